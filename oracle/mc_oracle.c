@@ -1,0 +1,850 @@
+/*
+ * ORACLE -- test infrastructure only.  Only the tests, the smoke check and
+ * the CPU-baseline leg of the benchmark may load this library.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * A plain, slow, single-threaded FP64 restatement of the Monte Carlo X-ray
+ * scatter forward projection of "Computational Scatter Correction for
+ * High-Resolution Flat-Panel CT Based on a Fast Monte Carlo Photon Transport
+ * Model" (arXiv 2201.13191), Sec. II-A and II-C:
+ *
+ *   - primary image by the deterministic line integral, eq. (Ip);
+ *   - photon histories from a binned polychromatic source (Sec. II-A, last
+ *     paragraph), free flight by a fixed-step ray march with a controllable
+ *     step (Sec. II-C.2), photoelectric absorption, Compton scattering
+ *     sampled by Kahn's method from eq. (KleinNishina) with S = 1, Rayleigh
+ *     scattering sampled by inversion on F^2 plus rejection on the Thomson
+ *     factor, eq. (Thomson);
+ *   - scatter scoring by the point-detector estimator eq. (Th) with the
+ *     scatter-toward-detector pdfs eqs. (pmueforIncoherent) and
+ *     (pmueforcoherent), split into N_split pseudo-particles aimed at
+ *     randomly selected pixels (Sec. II-A and II-C.1), optional Russian
+ *     roulette, summed per eq. (Is).
+ *
+ * Readings of the paper that it implements (all listed in the design notes):
+ * lengths in mm, energies in keV, eta(E) = E, images in expected detector
+ * energy per pixel per source photon emitted into 4 pi; step rule = equal
+ * subdivision of the clipped chord, nearest voxel at each step midpoint;
+ * cross-section tables linear in E between their 1 keV nodes; counter-based
+ * Philox4x32-10 random numbers (Salmon et al., SC'11) with a fixed draw order.
+ *
+ * Parity pins: see the -m "not gpu" tests (chord lengths, Beer-Lambert,
+ * chi-square tests of both samplers, pdf normalisation, energy conservation,
+ * single-scatter quadrature, NEE vs analog tally, Philox known answers).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ESTATE -2
+#define ORC_EIO -8
+#define ORC_MAXMAT 16
+#define ORC_MAXCOMP 8
+
+static const double PI = 3.14159265358979323846;
+
+typedef struct {
+  /* tables */
+  int have_tables, n_mat, n_E;
+  double E0, dE, r0, mec2, hc, NA, cF, Kpe;
+  double density[ORC_MAXMAT];
+  int n_comp[ORC_MAXMAT];
+  double comp[ORC_MAXMAT][ORC_MAXCOMP][3]; /* Z, w (mol/g), b (A^2) */
+  double *mu_pe, *mu_in, *mu_co, *icoh;    /* [n_mat][n_E] */
+  /* volume */
+  int have_volume, nx, ny, nz;
+  double dx, dy, dz;
+  uint8_t *mat;
+  double *rho;
+  /* spectrum */
+  int have_spectrum, n_bins;
+  double *S, *Ebin;
+  /* geometry */
+  int have_geometry, nu, nv;
+  double sod, sdd, pu, pv;
+  /* options */
+  int n_split, max_order;
+  double rr_threshold, eps_face;
+} orc_ctx;
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from the published description (Salmon, Moraes, Dror,
+ * Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of
+ * two 32x32->64 multiplies with a Weyl key schedule. */
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Per-history random stream: key = seed, counter = (block, angle, h_lo, h_hi).
+ * Values are consumed four per block, in order. */
+typedef struct {
+  uint32_t key[2], ctr[4], buf[4];
+  int idx;
+  uint64_t draws;
+} rng_t;
+
+static void rng_init(rng_t *g, uint64_t h, uint32_t angle_index, uint64_t seed) {
+  g->key[0] = (uint32_t)seed;
+  g->key[1] = (uint32_t)(seed >> 32);
+  g->ctr[0] = 0;
+  g->ctr[1] = angle_index;
+  g->ctr[2] = (uint32_t)h;
+  g->ctr[3] = (uint32_t)(h >> 32);
+  g->idx = 4;
+  g->draws = 0;
+}
+static uint32_t rng_next(rng_t *g) {
+  if (g->idx == 4) {
+    orc_philox(g->ctr, g->key, g->buf);
+    g->ctr[0] += 1;
+    g->idx = 0;
+  }
+  g->draws++;
+  return g->buf[g->idx++];
+}
+/* Skip to the start of the next block of four. */
+static void rng_align(rng_t *g) { g->idx = 4; }
+/* Uniform on (0,1): the top 23 bits plus one half, scaled by 2^-23; exact in FP32. */
+static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+static double rng_u(rng_t *g) { return u01(rng_next(g)); }
+
+/* ------------------------------------------------------------------ */
+/* context */
+int orc_create(orc_ctx **out) {
+  orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  if (!c) return ORC_EINVAL;
+  c->n_split = 10;
+  c->max_order = 64;
+  c->rr_threshold = 0.0;
+  c->eps_face = 2e-4;
+  *out = c;
+  return ORC_OK;
+}
+void orc_destroy(orc_ctx *c) {
+  if (!c) return;
+  free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh);
+  free(c->mat); free(c->rho); free(c->S); free(c->Ebin);
+  free(c);
+}
+
+int orc_load_tables(orc_ctx *c, const char *path) {
+  FILE *f = fopen(path, "rb");
+  if (!f) return ORC_EIO;
+  char magic[8];
+  int32_t hdr[4];
+  double e[2], k[6];
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "MCXTAB01", 8) != 0 || fread(hdr, 4, 4, f) != 4 ||
+      fread(e, 8, 2, f) != 2 || fread(k, 8, 6, f) != 6) {
+    fclose(f);
+    return ORC_EIO;
+  }
+  int n_mat = hdr[1], n_E = hdr[2], maxc = hdr[3];
+  if (hdr[0] != 1 || n_mat < 1 || n_mat > ORC_MAXMAT || n_E < 2 || maxc != ORC_MAXCOMP) {
+    fclose(f);
+    return ORC_EIO;
+  }
+  c->n_mat = n_mat; c->n_E = n_E; c->E0 = e[0]; c->dE = e[1];
+  c->r0 = k[0]; c->mec2 = k[1]; c->hc = k[2]; c->NA = k[3]; c->cF = k[4]; c->Kpe = k[5];
+  for (int m = 0; m < n_mat; ++m) {
+    char name[16];
+    double dens;
+    int32_t nc[2];
+    double buf[ORC_MAXCOMP * 3];
+    if (fread(name, 1, 16, f) != 16 || fread(&dens, 8, 1, f) != 1 || fread(nc, 4, 2, f) != 2 ||
+        fread(buf, 8, ORC_MAXCOMP * 3, f) != ORC_MAXCOMP * 3 || nc[0] < 1 || nc[0] > ORC_MAXCOMP) {
+      fclose(f);
+      return ORC_EIO;
+    }
+    c->density[m] = dens;
+    c->n_comp[m] = nc[0];
+    for (int i = 0; i < ORC_MAXCOMP; ++i)
+      for (int j = 0; j < 3; ++j) c->comp[m][i][j] = buf[i * 3 + j];
+  }
+  size_t n = (size_t)n_mat * n_E;
+  free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh);
+  c->mu_pe = malloc(n * 8); c->mu_in = malloc(n * 8); c->mu_co = malloc(n * 8); c->icoh = malloc(n * 8);
+  if (fread(c->mu_pe, 8, n, f) != n || fread(c->mu_in, 8, n, f) != n || fread(c->mu_co, 8, n, f) != n ||
+      fread(c->icoh, 8, n, f) != n) {
+    fclose(f);
+    return ORC_EIO;
+  }
+  fclose(f);
+  c->have_tables = 1;
+  return ORC_OK;
+}
+
+int orc_load_volume(orc_ctx *c, const uint8_t *mat, const uint16_t *rho16, int nx, int ny, int nz, double dx,
+                    double dy, double dz) {
+  if (!c->have_tables) return ORC_ESTATE;
+  if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0)) return ORC_EINVAL;
+  size_t n = (size_t)nx * ny * nz;
+  uint8_t *m = malloc(n);
+  double *r = malloc(n * 8);
+  for (size_t i = 0; i < n; ++i) {
+    if (mat[i] >= c->n_mat) {
+      free(m); free(r);
+      return ORC_EINVAL;
+    }
+    m[i] = mat[i];
+    /* IEEE binary16 -> double, exactly */
+    uint16_t hbits = rho16[i];
+    int s = hbits >> 15, ex = (hbits >> 10) & 31, fr = hbits & 1023;
+    double v;
+    if (ex == 0) v = ldexp((double)fr, -24);
+    else if (ex == 31) v = NAN;
+    else v = ldexp((double)(fr | 1024), ex - 25);
+    if (s) v = -v;
+    if (!(v >= 0.0) || isinf(v)) {
+      free(m); free(r);
+      return ORC_EINVAL;
+    }
+    r[i] = v;
+  }
+  free(c->mat); free(c->rho);
+  c->mat = m; c->rho = r;
+  c->nx = nx; c->ny = ny; c->nz = nz; c->dx = dx; c->dy = dy; c->dz = dz;
+  c->have_volume = 1;
+  return ORC_OK;
+}
+
+int orc_set_spectrum(orc_ctx *c, const double *w, const float *E, int n) {
+  if (!c->have_tables) return ORC_ESTATE;
+  if (n < 1) return ORC_EINVAL;
+  double sum = 0;
+  double Emax = c->E0 + c->dE * (c->n_E - 1);
+  for (int i = 0; i < n; ++i) {
+    if (!(w[i] >= 0.0) || !((double)E[i] >= c->E0) || !((double)E[i] <= Emax)) return ORC_EINVAL;
+    sum += w[i];
+  }
+  if (!(sum > 0)) return ORC_EINVAL;
+  free(c->S); free(c->Ebin);
+  c->S = malloc(n * 8); c->Ebin = malloc(n * 8);
+  for (int i = 0; i < n; ++i) {
+    c->S[i] = w[i] / sum;
+    c->Ebin[i] = (double)E[i];
+  }
+  c->n_bins = n;
+  c->have_spectrum = 1;
+  return ORC_OK;
+}
+
+int orc_set_geometry(orc_ctx *c, double sod, double sdd, int nu, int nv, double pu, double pv) {
+  if (!(sod > 0) || !(sdd > sod) || nu < 1 || nv < 1 || !(pu > 0) || !(pv > 0)) return ORC_EINVAL;
+  c->sod = sod; c->sdd = sdd; c->nu = nu; c->nv = nv; c->pu = pu; c->pv = pv;
+  c->have_geometry = 1;
+  return ORC_OK;
+}
+
+int orc_set_options(orc_ctx *c, int n_split, double rr_threshold, int max_order, double eps_face) {
+  if (n_split < 1 || max_order < 1 || rr_threshold < 0) return ORC_EINVAL;
+  c->n_split = n_split;
+  c->rr_threshold = rr_threshold;
+  c->max_order = max_order;
+  if (eps_face > 0) c->eps_face = eps_face;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* tables: linear in E between nodes */
+static void interp_idx(const orc_ctx *c, double E, int *i, double *f) {
+  double x = (E - c->E0) / c->dE;
+  int k = (int)floor(x);
+  if (k < 0) k = 0;
+  if (k > c->n_E - 2) k = c->n_E - 2;
+  *i = k;
+  *f = x - k;
+}
+static double tab(const orc_ctx *c, const double *a, int m, double E) {
+  int i;
+  double f;
+  interp_idx(c, E, &i, &f);
+  const double *row = a + (size_t)m * c->n_E;
+  return row[i] + f * (row[i + 1] - row[i]);
+}
+/* total mass attenuation, cm^2/g */
+static double mu_rho_tot(const orc_ctx *c, int m, double E) {
+  return tab(c, c->mu_pe, m, E) + tab(c, c->mu_in, m, E) + tab(c, c->mu_co, m, E);
+}
+
+/* Klein-Nishina total cross section per electron divided by pi r0^2
+ * (closed form of int_{-1}^{1} (a'/a)^2 (a'/a + a/a' - sin^2) dmu), with
+ * its Taylor series where the closed form cancels. */
+double orc_kn_norm(double E, double mec2) {
+  double k = E / mec2;
+  if (k < 1e-3) {
+    /* 8/3 (1 - 2k + 26/5 k^2 - 133/10 k^3 + 1144/35 k^4) */
+    return 8.0 / 3.0 * (1.0 - 2.0 * k + 5.2 * k * k - 13.3 * k * k * k + 1144.0 / 35.0 * k * k * k * k);
+  }
+  double l = log1p(2.0 * k);
+  double a = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / (1.0 + 2.0 * k) - l / k);
+  double b = l / (2.0 * k);
+  double d = (1.0 + 3.0 * k) / ((1.0 + 2.0 * k) * (1.0 + 2.0 * k));
+  return 2.0 * (a + b - d);
+}
+
+/* Molecular F^2 = sum_i w_i Z_i^2 / (1 + b_i x^2)^4 at x^2 = u (A^-2). */
+static double ff2(const orc_ctx *c, int m, double u) {
+  double s = 0;
+  for (int i = 0; i < c->n_comp[m]; ++i) {
+    double Z = c->comp[m][i][0], w = c->comp[m][i][1], b = c->comp[m][i][2];
+    double q = 1.0 + b * u;
+    double q2 = q * q;
+    s += w * Z * Z / (q2 * q2);
+  }
+  return s;
+}
+
+/* Scatter-toward-detector pdf over lambda in [-1, 1] (integrates to one):
+ * type 1 Compton, eq. (pmueforIncoherent) with S = 1, normalised by the KN total;
+ * type 2 Rayleigh, eq. (pmueforcoherent), normalised by the tabulated I_coh(E).
+ * Returns p and, for Compton, the scattered energy in *Eout. */
+double orc_nee_pdf(const orc_ctx *c, int type, int m, double E, double lam, double *Eout) {
+  if (type == 1) {
+    double a = E / c->mec2;
+    double ratio = 1.0 / (1.0 + a * (1.0 - lam));
+    if (Eout) *Eout = E * ratio;
+    return ratio * ratio * (ratio + 1.0 / ratio - 1.0 + lam * lam) / orc_kn_norm(E, c->mec2);
+  }
+  if (Eout) *Eout = E;
+  double K = (E / c->hc) * (E / c->hc);
+  double u = 0.5 * K * (1.0 - lam);
+  return (1.0 + lam * lam) * ff2(c, m, u) / tab(c, c->icoh, m, E);
+}
+
+/* Kahn's rejection method for the Klein-Nishina distribution (S = 1).
+ * r = E/E' in [1, 1 + 2a].  Returns cos(theta); *ratio = r. */
+static double sample_compton(rng_t *g, double E, double mec2, double *ratio, int *fail) {
+  double a = E / mec2;
+  for (int it = 0; it < 100000; ++it) {
+    double u1 = rng_u(g), u2 = rng_u(g), u3 = rng_u(g);
+    double r;
+    int acc;
+    if (u1 <= (1.0 + 2.0 * a) / (9.0 + 2.0 * a)) {
+      r = 1.0 + 2.0 * a * u2;
+      acc = u3 <= 4.0 * (1.0 / r - 1.0 / (r * r));
+    } else {
+      r = (1.0 + 2.0 * a) / (1.0 + 2.0 * a * u2);
+      double mu = 1.0 - (r - 1.0) / a;
+      acc = u3 <= 0.5 * (mu * mu + 1.0 / r);
+    }
+    if (acc) {
+      *ratio = r;
+      return 1.0 - (r - 1.0) / a;
+    }
+  }
+  *fail = 1;
+  *ratio = 1.0;
+  return 1.0;
+}
+
+/* Rayleigh: pick a form-factor component with probability proportional to
+ * w_i Z_i^2 G_i(K), invert u = x^2 on (1 + b_i u)^-4 over [0, K], take
+ * mu = 1 - 2u/K and accept with probability (1 + mu^2)/2. */
+static double sample_rayleigh(const orc_ctx *c, rng_t *g, int m, double E, int *fail) {
+  double K = (E / c->hc) * (E / c->hc);
+  double G[ORC_MAXCOMP], tot = 0;
+  int nc = c->n_comp[m];
+  for (int i = 0; i < nc; ++i) {
+    double Z = c->comp[m][i][0], w = c->comp[m][i][1], b = c->comp[m][i][2];
+    double T = 1.0 + b * K;
+    G[i] = w * Z * Z * (1.0 - 1.0 / (T * T * T)) / (3.0 * b);
+    tot += G[i];
+  }
+  for (int it = 0; it < 100000; ++it) {
+    double u1 = rng_u(g), u2 = rng_u(g), u3 = rng_u(g);
+    int i = 0;
+    double acc = G[0];
+    while (i < nc - 1 && !(u1 * tot < acc)) {
+      ++i;
+      acc += G[i];
+    }
+    double b = c->comp[m][i][2];
+    double T = 1.0 + b * K;
+    double q = 1.0 - u2 * (1.0 - 1.0 / (T * T * T));
+    double u = (pow(q, -1.0 / 3.0) - 1.0) / b;
+    double mu = 1.0 - 2.0 * u / K;
+    if (mu < -1.0) mu = -1.0;
+    if (u3 <= 0.5 * (1.0 + mu * mu)) return mu;
+  }
+  *fail = 1;
+  return 1.0;
+}
+
+/* Rotate unit vector w by polar cosine ct and azimuth phi. */
+static void rotate(double w[3], double ct, double phi) {
+  double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  double cp = cos(phi), sp = sin(phi);
+  double x = w[0], y = w[1], z = w[2], nx, ny, nz;
+  if (fabs(z) > 0.99999) {
+    nx = st * cp;
+    ny = st * sp;
+    nz = (z > 0 ? ct : -ct);
+  } else {
+    double s = sqrt(1.0 - z * z);
+    nx = x * ct + st * (x * z * cp - y * sp) / s;
+    ny = y * ct + st * (y * z * cp + x * sp) / s;
+    nz = z * ct - st * s * cp;
+  }
+  double n = sqrt(nx * nx + ny * ny + nz * nz);
+  w[0] = nx / n; w[1] = ny / n; w[2] = nz / n;
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry */
+typedef struct {
+  double s[3], c[3], eu[3], ev[3], n[3];
+} pose_t;
+static void pose(const orc_ctx *c, double beta, pose_t *p) {
+  double cb = cos(beta), sb = sin(beta);
+  p->s[0] = c->sod * cb; p->s[1] = c->sod * sb; p->s[2] = 0;
+  p->c[0] = (c->sod - c->sdd) * cb; p->c[1] = (c->sod - c->sdd) * sb; p->c[2] = 0;
+  p->eu[0] = -sb; p->eu[1] = cb; p->eu[2] = 0;
+  p->ev[0] = 0; p->ev[1] = 0; p->ev[2] = 1;
+  p->n[0] = cb; p->n[1] = sb; p->n[2] = 0;
+}
+/* Detector point at continuous pixel coordinates (a, b), pixel (i, j) spanning [i, i+1) x [j, j+1). */
+static void det_point(const orc_ctx *c, const pose_t *p, double a, double b, double out[3]) {
+  double ou = (a - 0.5 * c->nu) * c->pu, ov = (b - 0.5 * c->nv) * c->pv;
+  for (int k = 0; k < 3; ++k) out[k] = p->c[k] + ou * p->eu[k] + ov * p->ev[k];
+}
+
+/* Slab clip of p0 + t w, t in [t0, t1], to the volume box. */
+static int clip_box(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double *ta,
+                    double *tb) {
+  double half[3] = {0.5 * c->nx * c->dx, 0.5 * c->ny * c->dy, 0.5 * c->nz * c->dz};
+  double a = t0, b = t1;
+  for (int k = 0; k < 3; ++k) {
+    if (w[k] == 0.0) {
+      if (p0[k] < -half[k] || p0[k] > half[k]) return 0;
+    } else {
+      double u = (-half[k] - p0[k]) / w[k], v = (half[k] - p0[k]) / w[k];
+      if (u > v) { double t = u; u = v; v = t; }
+      if (u > a) a = u;
+      if (v < b) b = v;
+    }
+  }
+  *ta = a;
+  *tb = b;
+  return b > a;
+}
+
+static size_t voxel_of(const orc_ctx *c, const double p[3], int ijk[3]) {
+  double lo[3] = {-0.5 * c->nx * c->dx, -0.5 * c->ny * c->dy, -0.5 * c->nz * c->dz};
+  double d[3] = {c->dx, c->dy, c->dz};
+  int n[3] = {c->nx, c->ny, c->nz};
+  for (int k = 0; k < 3; ++k) {
+    int i = (int)floor((p[k] - lo[k]) / d[k]);
+    if (i < 0) i = 0;
+    if (i > n[k] - 1) i = n[k] - 1;
+    ijk[k] = i;
+  }
+  return ((size_t)ijk[2] * c->ny + ijk[1]) * c->nx + ijk[0];
+}
+
+/* Fixed-step march (Sec. II-C.2): the clipped chord [ta, tb] is cut into
+ * n = ceil(L/step) equal steps of length h = L/n; each step takes the
+ * material and density of the voxel holding its midpoint.  Accumulates
+ * rho*h per material into rhoL (g/cm^3 * mm).  If bound != NULL, adds for
+ * every midpoint within eps_face*voxel of a face whose neighbour differs the
+ * largest possible change of rho*mu_rho*h at energy Eb (an ambiguity bound for
+ * FP32 re-evaluation); sets *namb if L/step is within 1e-5 of an integer.
+ * Returns the number of steps. */
+static long march_rhoL(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
+                       double *rhoL, double *bound, double Eb, int *namb) {
+  double ta, tb;
+  if (!clip_box(c, p0, w, t0, t1, &ta, &tb)) return 0;
+  double L = tb - ta;
+  double q = L / step;
+  long n = (long)ceil(q);
+  if (n < 1) n = 1;
+  if (namb) {
+    double fr = q - floor(q + 0.5);
+    if (fabs(fr) < 1e-5 * (q > 1 ? q : 1)) *namb = 1;
+  }
+  double h = L / n;
+  double lo[3] = {-0.5 * c->nx * c->dx, -0.5 * c->ny * c->dy, -0.5 * c->nz * c->dz};
+  double dv[3] = {c->dx, c->dy, c->dz};
+  int nn[3] = {c->nx, c->ny, c->nz};
+  for (long k = 0; k < n; ++k) {
+    double t = ta + (k + 0.5) * h;
+    double p[3] = {p0[0] + t * w[0], p0[1] + t * w[1], p0[2] + t * w[2]};
+    int ijk[3];
+    size_t v = voxel_of(c, p, ijk);
+    rhoL[c->mat[v]] += c->rho[v] * h;
+    if (bound) {
+      double mu_here = c->rho[v] * mu_rho_tot(c, c->mat[v], Eb) * 0.1;
+      for (int a = 0; a < 3; ++a) {
+        double x = (p[a] - lo[a]) / dv[a];
+        double fr = x - floor(x);
+        int nb = -1;
+        if (fr < c->eps_face) nb = ijk[a] - 1;
+        else if (fr > 1.0 - c->eps_face) nb = ijk[a] + 1;
+        /* a neighbour index equal to the clamped index itself means the midpoint is at the box face */
+        if (nb >= 0 && nb < nn[a] && nb != ijk[a]) {
+          int j2[3] = {ijk[0], ijk[1], ijk[2]};
+          j2[a] = nb;
+          size_t v2 = ((size_t)j2[2] * c->ny + j2[1]) * c->nx + j2[0];
+          if (c->mat[v2] != c->mat[v] || c->rho[v2] != c->rho[v]) {
+            double mu2 = c->rho[v2] * mu_rho_tot(c, c->mat[v2], Eb) * 0.1;
+            *bound += fabs(mu2 - mu_here) * h;
+          }
+        }
+      }
+    }
+  }
+  return n;
+}
+
+/* Optical depth tau at energy E along the march (mm^-1 * mm). */
+static double march_tau(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
+                        double E, long *nsteps) {
+  double rhoL[ORC_MAXMAT] = {0};
+  long n = march_rhoL(c, p0, w, t0, t1, step, rhoL, NULL, 0, NULL);
+  if (nsteps) *nsteps += n;
+  double tau = 0;
+  for (int m = 0; m < c->n_mat; ++m)
+    if (rhoL[m] != 0) tau += mu_rho_tot(c, m, E) * 0.1 * rhoL[m];
+  return tau;
+}
+
+/* Exported march for tests: tau at energy E and per-material rho*L. */
+int orc_march(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step, double E,
+              double *tau, double *rhoL_out, double *bound, long *nsteps) {
+  if (!c->have_volume) return ORC_ESTATE;
+  double rhoL[ORC_MAXMAT] = {0};
+  double b = 0;
+  int namb = 0;
+  long n = march_rhoL(c, p0, w, t0, t1, step, rhoL, &b, E, &namb);
+  double t = 0;
+  for (int m = 0; m < c->n_mat; ++m) {
+    if (rhoL[m] != 0) t += mu_rho_tot(c, m, E) * 0.1 * rhoL[m];
+    if (rhoL_out) rhoL_out[m] = rhoL[m];
+  }
+  *tau = t;
+  if (bound) *bound = namb ? INFINITY : b;
+  if (nsteps) *nsteps = n;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Primary image, eq. (Ip), one angle.  Ip[j*nu + i] in keV per pixel per source
+ * photon into 4 pi; bound[] = ambiguity bound in optical depth (INFINITY when
+ * the step count itself is ambiguous). */
+int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *bound) {
+  if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
+  if (!(step > 0)) return ORC_EINVAL;
+  pose_t P;
+  pose(c, beta, &P);
+  double Emin = 1e30;
+  for (int n = 0; n < c->n_bins; ++n)
+    if (c->S[n] > 0 && c->Ebin[n] < Emin) Emin = c->Ebin[n];
+  for (int j = 0; j < c->nv; ++j) {
+    for (int i = 0; i < c->nu; ++i) {
+      double X[3];
+      det_point(c, &P, i + 0.5, j + 0.5, X);
+      double D[3] = {X[0] - P.s[0], X[1] - P.s[1], X[2] - P.s[2]};
+      double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      double w[3] = {D[0] / d, D[1] / d, D[2] / d};
+      double rhoL[ORC_MAXMAT] = {0};
+      double b = 0;
+      int namb = 0;
+      march_rhoL(c, P.s, w, 0.0, d, step, rhoL, &b, Emin, &namb);
+      double sum = 0;
+      for (int n = 0; n < c->n_bins; ++n) {
+        if (c->S[n] == 0) continue;
+        double tau = 0;
+        for (int m = 0; m < c->n_mat; ++m)
+          if (rhoL[m] != 0) tau += mu_rho_tot(c, m, c->Ebin[n]) * 0.1 * rhoL[m];
+        sum += c->S[n] * c->Ebin[n] * exp(-tau);
+      }
+      double cosg = c->sdd / d;
+      Ip[(size_t)j * c->nu + i] = sum * c->pu * c->pv * cosg / (4.0 * PI * d * d);
+      if (bound) bound[(size_t)j * c->nu + i] = namb ? INFINITY : b;
+    }
+  }
+  return ORC_OK;
+}
+
+/* Stratified photon counts per energy bin: M_n = max(1, floor(N S_n)) for
+ * S_n > 0, the remainder handed out one by one by largest fractional part
+ * (ties to the lower index) among bins not raised to one. */
+int orc_stratify(int n_bins, const double *S, uint64_t N, uint64_t *M) {
+  uint64_t sum = 0;
+  int *elig = malloc(n_bins * sizeof(int));
+  double *fr = malloc(n_bins * 8);
+  for (int n = 0; n < n_bins; ++n) {
+    double x = (double)N * S[n];
+    double fl = floor(x);
+    elig[n] = 0;
+    fr[n] = 0;
+    if (S[n] <= 0) {
+      M[n] = 0;
+    } else if (fl < 1.0) {
+      M[n] = 1;
+    } else {
+      M[n] = (uint64_t)fl;
+      elig[n] = 1;
+      fr[n] = x - fl;
+    }
+    sum += M[n];
+  }
+  if (sum > N) {
+    free(elig); free(fr);
+    return ORC_EINVAL;
+  }
+  uint64_t rem = N - sum;
+  while (rem > 0) {
+    int best = -1;
+    for (int n = 0; n < n_bins; ++n)
+      if (elig[n] == 1 && (best < 0 || fr[n] > fr[best])) best = n;
+    if (best < 0) break;
+    M[best] += 1;
+    elig[best] = 2;
+    --rem;
+  }
+  free(elig); free(fr);
+  return rem == 0 ? ORC_OK : ORC_EINVAL;
+}
+
+/* Statistics slots */
+enum {
+  ST_HIST = 0, ST_FLIGHT_STEPS, ST_NEE_STEPS, ST_NEE_RAYS, ST_PHOTO, ST_COMPTON, ST_RAYLEIGH, ST_ESCAPE,
+  ST_MAX_EERR, ST_LIMIT, ST_SAMPLER_FAIL, ST_E_SOURCE, ST_E_DEPOSIT, ST_E_ESCAPE, ST_RR_KILLED, ST_N
+};
+
+/* Scatter image by eq. (Is): histories h in [h_begin, h_end) of an N-photon
+ * run at angle beta (angle_index keys the random counter).
+ *   Is[P]          sum of NEE scores (keV per pixel per source photon);
+ *   Is_order[3][P] the same split by scatter order 1, 2, >=3 (nullable);
+ *   analog[P]      detector hits of escaping scattered photons (nullable);
+ *   analog0[P]     detector hits of unscattered photons (nullable);
+ *   stats[ST_N]    counters (see enum). */
+int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N, uint64_t h_begin, uint64_t h_end,
+                double step, uint64_t seed, double *Is, double *Is_order, double *analog, double *analog0,
+                double *stats) {
+  if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
+  if (!(step > 0) || h_end > N || h_begin > h_end) return ORC_EINVAL;
+  /* the volume must lie between source and detector */
+  double rmax = 0.5 * sqrt(pow(c->nx * c->dx, 2) + pow(c->ny * c->dy, 2));
+  if (!(rmax < c->sod) || !(rmax < c->sdd - c->sod)) return ORC_EINVAL;
+  uint64_t *M = malloc(c->n_bins * sizeof(uint64_t));
+  uint64_t *pre = malloc((c->n_bins + 1) * sizeof(uint64_t));
+  if (orc_stratify(c->n_bins, c->S, N, M) != ORC_OK) {
+    free(M); free(pre);
+    return ORC_EINVAL;
+  }
+  pre[0] = 0;
+  for (int n = 0; n < c->n_bins; ++n) pre[n + 1] = pre[n] + M[n];
+  pose_t P;
+  pose(c, beta, &P);
+  const size_t npix = (size_t)c->nu * c->nv;
+  const double A_det = c->nu * c->pu * c->nv * c->pv;
+  const double A_px = c->pu * c->pv;
+  double st[ST_N] = {0};
+  long nsteps = 0;
+  for (uint64_t h = h_begin; h < h_end; ++h) {
+    int bin = 0;
+    while (bin < c->n_bins - 1 && !(h < pre[bin + 1])) ++bin;
+    double E = c->Ebin[bin];
+    rng_t g;
+    rng_init(&g, h, angle_index, seed);
+    /* source: a uniform point on the detector rectangle, weighted by the solid-angle Jacobian */
+    double ua = rng_u(&g), ub = rng_u(&g);
+    double Q[3];
+    det_point(c, &P, ua * c->nu, ub * c->nv, Q);
+    double D[3] = {Q[0] - P.s[0], Q[1] - P.s[1], Q[2] - P.s[2]};
+    double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    double w[3] = {D[0] / d, D[1] / d, D[2] / d};
+    double W = c->S[bin] / (double)M[bin] * A_det * (c->sdd / d) / (4.0 * PI * d * d);
+    double x[3] = {P.s[0], P.s[1], P.s[2]};
+    double e_src = E * W, e_dep = 0, e_esc = 0;
+    int order = 0;
+    st[ST_HIST] += 1;
+    for (;;) {
+      /* free flight: march until the accumulated optical depth reaches -ln u */
+      double tau_star = -log(rng_u(&g));
+      double ta, tb;
+      int hit = 0;
+      double tint = 0;
+      int mint = 0;
+      if (clip_box(c, x, w, 0.0, INFINITY, &ta, &tb)) {
+        double L = tb - ta;
+        long n = (long)ceil(L / step);
+        if (n < 1) n = 1;
+        double hh = L / n, tau = 0;
+        for (long k = 0; k < n; ++k) {
+          double t = ta + (k + 0.5) * hh;
+          double p[3] = {x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]};
+          int ijk[3];
+          size_t v = voxel_of(c, p, ijk);
+          double mu = c->rho[v] * mu_rho_tot(c, c->mat[v], E) * 0.1;
+          st[ST_FLIGHT_STEPS] += 1;
+          if (tau + mu * hh >= tau_star) {
+            tint = ta + k * hh + (tau_star - tau) / mu;
+            mint = c->mat[v];
+            hit = 1;
+            break;
+          }
+          tau += mu * hh;
+        }
+      }
+      if (!hit) {
+        /* escape; the analog tally records where it meets the detector */
+        e_esc += E * W;
+        st[ST_ESCAPE] += 1;
+        double wn = w[0] * P.n[0] + w[1] * P.n[1] + w[2] * P.n[2];
+        double *img = order == 0 ? analog0 : analog;
+        if (img && wn < 0) {
+          double cx[3] = {P.c[0] - x[0], P.c[1] - x[1], P.c[2] - x[2]};
+          double t = (cx[0] * P.n[0] + cx[1] * P.n[1] + cx[2] * P.n[2]) / wn;
+          if (t > 0) {
+            double y[3] = {x[0] + t * w[0] - P.c[0], x[1] + t * w[1] - P.c[1], x[2] + t * w[2] - P.c[2]};
+            double a = (y[0] * P.eu[0] + y[1] * P.eu[1] + y[2] * P.eu[2]) / c->pu + 0.5 * c->nu;
+            double b = (y[0] * P.ev[0] + y[1] * P.ev[1] + y[2] * P.ev[2]) / c->pv + 0.5 * c->nv;
+            if (a >= 0 && a < c->nu && b >= 0 && b < c->nv) img[(size_t)floor(b) * c->nu + (size_t)floor(a)] += E * W;
+          }
+        }
+        break;
+      }
+      for (int k = 0; k < 3; ++k) x[k] += tint * w[k];
+      /* interaction type */
+      double pe = tab(c, c->mu_pe, mint, E), in = tab(c, c->mu_in, mint, E), co = tab(c, c->mu_co, mint, E);
+      double ut = rng_u(&g) * (pe + in + co);
+      int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
+      if (type == 0) {
+        st[ST_PHOTO] += 1;
+        e_dep += E * W;
+        break;
+      }
+      st[type == 1 ? ST_COMPTON : ST_RAYLEIGH] += 1;
+      /* point-detector scoring, split into n_split pseudo-particles, eq. (Th) */
+      rng_align(&g);
+      for (int s = 0; s < c->n_split; ++s) {
+        uint32_t r = rng_next(&g);
+        double va = rng_u(&g), vb = rng_u(&g), vr = rng_u(&g);
+        uint64_t pix = ((uint64_t)r * (uint64_t)npix) >> 32;
+        int pi = (int)(pix % c->nu), pj = (int)(pix / c->nu);
+        double Pp[3];
+        det_point(c, &P, pi + va, pj + vb, Pp);
+        double DD[3] = {Pp[0] - x[0], Pp[1] - x[1], Pp[2] - x[2]};
+        double dd = sqrt(DD[0] * DD[0] + DD[1] * DD[1] + DD[2] * DD[2]);
+        double dir[3] = {DD[0] / dd, DD[1] / dd, DD[2] / dd};
+        double lam = w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2];
+        double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
+        double Ep;
+        double p = orc_nee_pdf(c, type, mint, E, lam, &Ep);
+        double x0 = W * Ep * p * A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
+        st[ST_NEE_RAYS] += 1;
+        if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
+          if (vr >= x0 / c->rr_threshold) {
+            st[ST_RR_KILLED] += 1;
+            continue;
+          }
+          x0 = c->rr_threshold;
+        }
+        long ns = 0;
+        double tp = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
+        st[ST_NEE_STEPS] += ns;
+        double sc = x0 * exp(-tp);
+        Is[pix] += sc;
+        if (Is_order) Is_order[(size_t)(order < 2 ? order : 2) * npix + pix] += sc;
+      }
+      /* new direction */
+      int fail = 0;
+      double ct, Enew = E;
+      if (type == 1) {
+        double rr;
+        ct = sample_compton(&g, E, c->mec2, &rr, &fail);
+        Enew = E / rr;
+      } else {
+        ct = sample_rayleigh(c, &g, mint, E, &fail);
+      }
+      double phi = 2.0 * PI * rng_u(&g);
+      if (fail) st[ST_SAMPLER_FAIL] += 1;
+      rotate(w, ct, phi);
+      e_dep += (E - Enew) * W;
+      E = Enew;
+      order += 1;
+      if (E < 1.0) {
+        e_dep += E * W;
+        break;
+      }
+      if (order >= c->max_order) {
+        e_dep += E * W;
+        st[ST_LIMIT] += 1;
+        break;
+      }
+    }
+    double err = fabs(e_src - e_dep - e_esc) / e_src;
+    if (err > st[ST_MAX_EERR]) st[ST_MAX_EERR] = err;
+    st[ST_E_SOURCE] += e_src;
+    st[ST_E_DEPOSIT] += e_dep;
+    st[ST_E_ESCAPE] += e_esc;
+  }
+  (void)nsteps;
+  if (stats)
+    for (int k = 0; k < ST_N; ++k) stats[k] += st[k];
+  free(M); free(pre);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampler access for the chi-square tests: n independent draws, stream h = i. */
+int orc_sample_compton(double E, double mec2, uint64_t n, uint64_t seed, double *cos_out, double *ratio_out) {
+  for (uint64_t i = 0; i < n; ++i) {
+    rng_t g;
+    rng_init(&g, i, 0, seed);
+    int fail = 0;
+    double r;
+    cos_out[i] = sample_compton(&g, E, mec2, &r, &fail);
+    if (ratio_out) ratio_out[i] = r;
+    if (fail) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+int orc_sample_rayleigh(const orc_ctx *c, int m, double E, uint64_t n, uint64_t seed, double *cos_out) {
+  if (!c->have_tables || m < 0 || m >= c->n_mat) return ORC_ESTATE;
+  for (uint64_t i = 0; i < n; ++i) {
+    rng_t g;
+    rng_init(&g, i, 0, seed);
+    int fail = 0;
+    cos_out[i] = sample_rayleigh(c, &g, m, E, &fail);
+    if (fail) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+/* Uniforms of one history's stream, for cross-checking the generator. */
+int orc_stream(uint64_t h, uint32_t angle_index, uint64_t seed, int n, uint32_t *out) {
+  rng_t g;
+  rng_init(&g, h, angle_index, seed);
+  for (int i = 0; i < n; ++i) out[i] = rng_next(&g);
+  return ORC_OK;
+}
+
+double orc_table(const orc_ctx *c, int which, int m, double E) {
+  const double *a = which == 0 ? c->mu_pe : which == 1 ? c->mu_in : which == 2 ? c->mu_co : c->icoh;
+  return tab(c, a, m, E);
+}
