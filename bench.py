@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 Monte Carlo scatter forward projection.
+
+One step = one mc_project call over the whole path: the primary image
+(eq. Ip) and n_photons scatter histories scored on the panel (eq. Is) for one
+projection of the 256^3 / 512^2 / 1e8-photon polyenergetic workload (ell256:
+seeded ellipsoids of water, PMMA, aluminium and bone in air, 120 kVp Kramers
+spectrum with 2 mm Al, SOD/SDD 400/800 mm, 0.4 mm pixels, 0.25 mm step).
+Metric: photon histories/s, whole job.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU runs are replicas (one independent projection per rank, no
+collective on the data path): value = histories of all ranks / max time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon histories/s on 1 GB300; s/projection at <=2% scatter L2 error vs plain MC"
+UNIT = "histories/s"
+WORKLOAD = "ell256"
+FLOPS_PER_STEP = 10  # algorithmic FP32 operations per fixed-step march step
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--photons", type=float, default=None, help="override photons per step")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def device_id(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def oracle_rate(tp, wl, n_photons, budget_s):
+    """Oracle histories/s on a bounded sample of the workload (single thread)."""
+    import oracle
+
+    o = oracle.Oracle(tp)
+    o.setup(wl)
+    t0 = time.perf_counter()
+    o.primary(0.0, wl["step_mm"])
+    t_primary = time.perf_counter() - t0
+    n = 500
+    t0 = time.perf_counter()
+    o.scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n)
+    dt = time.perf_counter() - t0
+    n2 = int(max(500, min(5e6, n * (budget_s - t_primary) / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    o.scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n2)
+    t_hist = (time.perf_counter() - t0) / n2
+    rate = n_photons / (t_primary + n_photons * t_hist)
+    sample = (f"oracle, 1 thread: primary image once ({t_primary:.2f} s) + histories 0..{n2} of the "
+              f"{int(n_photons)}-photon run ({t_hist * n2:.1f} s), extrapolated to one full projection")
+    return rate, sample, t_primary, t_hist
+
+
+def make_inputs(tables_dir, photons):
+    from mc_inputs import default_table_path, make_workload, read_tables
+
+    tp = default_table_path("full", tables_dir)
+    wl = make_workload(WORKLOAD, read_tables(tp))
+    if photons:
+        wl["n_photons"] = int(photons)
+    return tp, wl
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    tdir = tempfile.mkdtemp(prefix="mcbench")
+    tp, wl = make_inputs(tdir, args.photons)
+    import oracle
+
+    o = oracle.Oracle(tp)
+    o.setup(wl)
+    N = wl["n_photons"]
+    # size each step to ~ (budget / (K + W)) seconds
+    per_step = max(2.0, min(20.0, 150.0 / (args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    o.scatter(0.0, N, wl["step_mm"], wl["seed"], 0, 300)
+    t_h = (time.perf_counter() - t0) / 300
+    n = int(max(300, per_step / max(t_h, 1e-7)))
+    for k in range(args.warmup):
+        o.scatter(0.0, N, wl["step_mm"], wl["seed"], k * n, (k + 1) * n)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        h0 = (args.warmup + k) * n
+        o.scatter(0.0, N, wl["step_mm"], wl["seed"], h0, h0 + n)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "volume": "256^3 x 0.5 mm", "detector": "512^2 x 0.4 mm",
+                   "photons_per_projection": N, "step_mm": wl["step_mm"], "n_split": 10,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} scatter histories of the {N}-photon run per step, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    tdir = tempfile.mkdtemp(prefix=f"mcbench{rank}")
+    tp, wl = make_inputs(tdir, args.photons)
+    N = wl["n_photons"]
+    seed = wl["seed"] + 1000 * rank
+    ctx = mcx.Context(local)
+    ctx.load_tables(tp)
+    ctx.setup(wl)
+    stream = torch.cuda.current_stream()
+    out = {"primary": ctx.empty_images(1), "scatter": ctx.empty_images(1)}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(k):
+        return ctx.project([0.0], N, wl["step_mm"], seed + k, out=out, stream=stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(device_id(torch, local))
+    clocks.start()
+    t_kernel, steps_per, stats = [], [], None
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        flush.zero_()  # inputs fit in L2: evict them between steps
+        step(args.warmup + k)
+        stats = ctx.last_stats()
+        t_kernel.append(stats["transport_ms"])
+        steps_per.append(stats["flight_steps"] + stats["nee_steps"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    el_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([el_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * N * args.steps / (el_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: volume upload from pinned
+    # host memory, projection, read-back of both images
+    vol = wl["volume"]
+    h_mat = torch.from_numpy(vol["mat"]).pin_memory()
+    h_rho = torch.from_numpy(vol["rho"].view(np.int16)).pin_memory()
+    h_out = torch.empty((2, 1, ctx.nv, ctx.nu), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ctx.load_volume(h_mat, h_rho, vol["spacing"], stream=stream)
+        ctx.project([0.0], N, wl["step_mm"], seed + 100 + k, out=out, stream=stream)
+        h_out[0].copy_(out["primary"], non_blocking=True)
+        h_out[1].copy_(out["scatter"], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * N * e2e_steps / e2e_s
+    h2d = vol["mat"].nbytes + vol["rho"].nbytes + 4 + len(wl["weights"]) * 12
+    d2h = 2 * ctx.nu * ctx.nv * 4
+
+    # roofline of the dominant kernel (transport): FP32 issue
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    mean_ms = float(np.mean(t_kernel))
+    achieved = FLOPS_PER_STEP * float(np.mean(steps_per)) / (mean_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
+            "kernel": "k_transport", "steps_per_launch": float(np.mean(steps_per)),
+            "kernel_ms": mean_ms, "steps_per_s": float(np.mean(steps_per)) / (mean_ms / 1e3),
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, _, _ = oracle_rate(tp, wl, N, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ellipsoid phantom, Kramers spectrum)",
+            "config": {"workload": WORKLOAD, "volume": "256^3 x 0.5 mm uint8 material + fp16 density",
+                       "detector": "512^2 x 0.4 mm", "photons_per_projection": N, "step_mm": wl["step_mm"],
+                       "n_split": 10, "spectrum": "120 kVp, 111 bins", "l2_flush": True,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "s_per_projection": el_ms / 1e3 / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * mc.h -- C ABI of the GB300 Monte Carlo X-ray scatter forward projection.
+ *
+ * Method: "Computational Scatter Correction for High-Resolution Flat-Panel CT
+ * Based on a Fast Monte Carlo Photon Transport Model" (arXiv 2201.13191),
+ * Sec. II-A (photon transport model, eqs. KleinNishina, Thomson, Th,
+ * pmueforIncoherent, pmueforcoherent, Is, Ip), Sec. II-C (variance
+ * reduction, controllable ray-tracing step, dual interpolation, smoothing)
+ * and Sec. II-E (iterative correction, eq. Correction).
+ *
+ * Conventions shared by every entry point
+ *   - lengths in mm, energies in keV, angles in radians;
+ *   - the volume is centred on the isocentre, stored [nz][ny][nx] with x
+ *     fastest; the source turns about z: s(b) = SOD (cos b, sin b, 0); the
+ *     flat panel is centred on (SOD - SDD)(cos b, sin b, 0) with axes
+ *     e_u = (-sin b, cos b, 0), e_v = (0, 0, 1); images are [nv][nu] row
+ *     major, pixel (i, j) centred at (i - (nu-1)/2) pu e_u + (j - (nv-1)/2) pv e_v
+ *     from the panel centre;
+ *   - detector response eta(E) = E (energy integrating); both images are the
+ *     expected detector energy per pixel per source photon emitted into 4 pi
+ *     (keV), the source being collimated to the detector pyramid;
+ *   - device pointers belong to the caller, who keeps ownership; the library
+ *     copies what it needs at load time and owns only its internal buffers;
+ *   - every call returns MC_OK or a negative status; mc_last_error() gives
+ *     detail.  No C++ exception crosses the ABI.  A context is not thread
+ *     safe: use one context per host thread.  All GPU work is enqueued on the
+ *     caller's stream (a cudaStream_t passed as void*, NULL = legacy default).
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_ERR_INVALID_ARG -1 /* argument out of range or inconsistent */
+#define MC_ERR_STATE -2       /* call made before the data it needs was loaded */
+#define MC_ERR_CUDA -3        /* a CUDA runtime call failed */
+#define MC_ERR_OOM -4         /* device allocation failed */
+#define MC_ERR_TIMEOUT -5     /* a bounded device wait gave up */
+#define MC_ERR_LIMIT -6       /* a history hit the scatter-order or sampler cap; outputs valid */
+#define MC_ERR_INTERNAL -7    /* a device-side consistency check failed */
+#define MC_ERR_IO -8          /* table file missing or malformed */
+
+#define MC_MAX_MATERIALS 8
+#define MC_MAX_BINS 512
+
+typedef struct mc_ctx mc_ctx;
+
+/* Tally modes for the scatter image (Sec. II-A, eq. Is). */
+#define MC_TALLY_AUTO 0   /* shared-memory histogram when the image fits, else global */
+#define MC_TALLY_GLOBAL 1 /* every pseudo-particle adds straight into the FP64 image */
+#define MC_TALLY_SHARED 2 /* per-block FP32 shared-memory image, flushed into FP64 */
+
+typedef struct mc_options {
+  int n_split;           /* pseudo-particles per scatter interaction (Sec. II-C.1), default 10 */
+  float rr_threshold;    /* Russian roulette on the pseudo-particle weight x0 (Sec. II-C.1); 0 = off */
+  int max_scatter_order; /* a history ends after this many scatters (energy deposited), default 64 */
+  int n_batches;         /* >1: histories h mod n_batches form batches for scatter_var_out */
+  int block_size;        /* transport threads per block; 0 = default (256) */
+  int blocks_per_sm;     /* persistent grid = SMs x blocks_per_sm; 0 = default (occupancy) */
+  int tally_mode;        /* MC_TALLY_* */
+  int sg_window;         /* Savitzky-Golay window (odd, >= order + 2), default 9 (Sec. II-C.4) */
+  int sg_order;          /* Savitzky-Golay polynomial order, default 3 (Sec. II-C.4) */
+  float cubic_a;         /* Keys cubic parameter of the spatial up-sampling, default -0.5 (Sec. II-C.3) */
+  int denoise_mode;      /* 0 = Savitzky-Golay, 2 = none */
+} mc_options;
+
+/* Fill *opt with the defaults listed above. */
+void mc_default_options(mc_options *opt);
+
+/* Create a context on CUDA device `cuda_device`; opt may be NULL (defaults).
+ * *out receives the context.  Errors: INVALID_ARG (bad option), CUDA. */
+int mc_create(mc_ctx **out, int cuda_device, const mc_options *opt);
+/* Free the context and every device buffer it owns (after a device sync). */
+void mc_destroy(mc_ctx *ctx);
+/* Replace the options (validated as in mc_create). */
+int mc_set_options(mc_ctx *ctx, const mc_options *opt);
+/* Detail of the last failing call on this context (never NULL). */
+const char *mc_last_error(const mc_ctx *ctx);
+
+/* Load the per-material cross-section tables (1 keV nodes; format described
+ * in mc_inputs/tables.py): mu_pe, mu_incoh, mu_coh in cm^2/g and the Rayleigh
+ * pdf normalisation I_coh(E), plus each material's form-factor components.
+ * These stand in for the Hubbell data of Sec. II-A.  Values between nodes are
+ * linear in E.  Errors: IO (missing/malformed file), INVALID_ARG (more than
+ * MC_MAX_MATERIALS materials), CUDA/OOM. */
+int mc_load_tables(mc_ctx *ctx, const char *path);
+
+/* Load the voxelised object (Sec. II-A last paragraph; Sec. II-E: segmented
+ * materials converted to densities): mat[nz][ny][nx] material ids (uint8,
+ * each < n_materials), rho_fp16[nz][ny][nx] densities in g/cm^3 as IEEE
+ * binary16 bit patterns (finite, >= 0), voxel size dx, dy, dz in mm.  The
+ * arrays are host memory (is_device_ptr = 0) or device memory (1); they are
+ * copied (on `stream`) and the caller keeps ownership.  Errors: STATE (no
+ * tables), INVALID_ARG (sizes, ids, densities), CUDA/OOM. */
+int mc_load_volume(mc_ctx *ctx, const uint8_t *mat, const uint16_t *rho_fp16, int nx, int ny, int nz, float dx,
+                   float dy, float dz, int is_device_ptr, void *stream);
+
+/* Polychromatic source as discrete bins (Sec. II-A, eq. Is: N bins, M photons
+ * per bin): host arrays weights[n] >= 0 (normalised here to sum 1) and
+ * energies_keV[n] inside the table range; 1 <= n <= MC_MAX_BINS.  Photons are
+ * stratified over bins: M_n = max(1, floor(N S_n)) for S_n > 0 plus the
+ * remainder by largest fractional part.  Errors: STATE (no tables), INVALID_ARG. */
+int mc_set_spectrum(mc_ctx *ctx, const double *weights, const float *energies_keV, int n_bins);
+
+/* Cone-beam geometry: source-isocentre sod, source-detector sdd (mm), flat
+ * panel of nu x nv pixels of pu x pv mm.  The volume must lie strictly
+ * between source and panel (checked at projection time).  Errors: INVALID_ARG. */
+int mc_set_geometry(mc_ctx *ctx, float sod, float sdd, int nu, int nv, float pu, float pv);
+
+/* Forward projection at n_angles source angles (host array angles_rad), all in
+ * one launch per kernel (Sec. II-B projection parallelism).
+ *   primary_out  device [n_angles][nv][nu] FP32: eq. (Ip), deterministic line
+ *                integral sampled at pixel centres with the fixed-step march;
+ *   scatter_out  device [n_angles][nv][nu] FP32: eq. (Is), n_photons histories
+ *                per angle, point-detector scoring (eq. Th) split n_split ways;
+ *   scatter_var_out (nullable) device, same shape: variance of scatter_out
+ *                from n_batches >= 2 batches.
+ * Either image pointer may be NULL to skip that image.  step_mm is the
+ * controllable ray-tracing step (Sec. II-C.2): each chord is cut into
+ * ceil(L/step) equal steps sampled at their midpoints.  Histories are keyed by
+ * (seed, angle index, history index) through Philox4x32-10, so results are
+ * deterministic up to the order of the FP64 tally sums.  The call returns once
+ * the work is enqueued and its status read back (it synchronises `stream`).
+ * Errors: STATE, INVALID_ARG, CUDA/OOM, LIMIT (outputs still valid), INTERNAL. */
+int mc_project(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm, uint64_t seed,
+               float *primary_out, float *scatter_out, float *scatter_var_out, void *stream);
+
+/* As mc_project's scatter image, restricted to histories
+ * [h_begin, h_begin + h_count) of an n_photons run: the same histories, the
+ * same random numbers and the same weights as in the full run, so any
+ * subset can be checked history for history.  scatter_out is FP32
+ * [n_angles][nv][nu] on the device.  Errors as mc_project. */
+int mc_project_histories(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, uint64_t h_begin,
+                         uint64_t h_count, float step_mm, uint64_t seed, float *scatter_out, void *stream);
+
+/* Counters of the last projection (double[n], n <= MC_STAT_N): histories,
+ * flight steps, pseudo-particle steps, pseudo-particles, photoelectric,
+ * Compton, Rayleigh, escapes, limit hits, sampler failures, transport kernel
+ * milliseconds, primary kernel milliseconds. */
+#define MC_STAT_N 12
+int mc_last_stats(const mc_ctx *ctx, double *out, int n);
+
+/* Smoothing and dual interpolation of simulated scatter (Sec. II-C.3, II-C.4):
+ *   1. Savitzky-Golay smoothing of each input image, separable, polynomial
+ *      order opt.sg_order over opt.sg_window points per axis, edges fitted by
+ *      the same least-squares polynomial over the first/last window
+ *      (denoise_mode 0; mode 2 skips it);
+ *   2. linear interpolation in angle, periodic in 2 pi, from the n_in sorted
+ *      simulated angles in_angles (host, radians) to out_angles (host);
+ *   3. separable Keys cubic up-sampling (parameter opt.cubic_a) from nv x nu
+ *      to NV x NU with half-pixel centre alignment and clamped edges.
+ * in: device FP32 [n_in][nv][nu]; out: device FP32 [n_out][NV][NU].
+ * Values are interpolated as given (no pixel-area rescaling).
+ * Errors: INVALID_ARG (sizes, window, unsorted angles), CUDA/OOM. */
+int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_angles, int nu, int nv, float *out,
+                       int n_out, const float *out_angles, int NU, int NV, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

@@ -549,8 +549,13 @@ int orc_march(const orc_ctx *c, const double p0[3], const double w[3], double t0
 
 /* ------------------------------------------------------------------ */
 /* Primary image, eq. (Ip), one angle.  Ip[j*nu + i] in keV per pixel per source
- * photon into 4 pi; bound[] = ambiguity bound in optical depth (INFINITY when
- * the step count itself is ambiguous). */
+ * photon into 4 pi.  bound[] (nullable) is the relative change of Ip that a
+ * re-evaluation in FP32 may legitimately produce: midpoints within eps_face of
+ * a face between different voxels may fall on either side (their largest
+ * optical-depth change, weighted over the spectrum), and the chord length
+ * itself carries an FP32 rounding of a few units in the last place of the
+ * larger ray parameter; INFINITY when the step count ceil(L/step) itself is
+ * ambiguous. */
 int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *bound) {
   if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
   if (!(step > 0)) return ORC_EINVAL;
@@ -559,6 +564,7 @@ int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *
   double Emin = 1e30;
   for (int n = 0; n < c->n_bins; ++n)
     if (c->S[n] > 0 && c->Ebin[n] < Emin) Emin = c->Ebin[n];
+  double *tau_n = malloc(c->n_bins * 8);
   for (int j = 0; j < c->nv; ++j) {
     for (int i = 0; i < c->nu; ++i) {
       double X[3];
@@ -570,19 +576,32 @@ int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *
       double b = 0;
       int namb = 0;
       march_rhoL(c, P.s, w, 0.0, d, step, rhoL, &b, Emin, &namb);
-      double sum = 0;
+      double sum = 0, wt = 0, wtau = 0;
       for (int n = 0; n < c->n_bins; ++n) {
+        tau_n[n] = 0;
         if (c->S[n] == 0) continue;
         double tau = 0;
         for (int m = 0; m < c->n_mat; ++m)
           if (rhoL[m] != 0) tau += mu_rho_tot(c, m, c->Ebin[n]) * 0.1 * rhoL[m];
-        sum += c->S[n] * c->Ebin[n] * exp(-tau);
+        double e = c->S[n] * c->Ebin[n] * exp(-tau);
+        sum += e;
+        wt += e;
+        wtau += e * tau;
       }
       double cosg = c->sdd / d;
       Ip[(size_t)j * c->nu + i] = sum * c->pu * c->pv * cosg / (4.0 * PI * d * d);
-      if (bound) bound[(size_t)j * c->nu + i] = namb ? INFINITY : b;
+      if (bound) {
+        double ta, tb, chord = 0;
+        if (clip_box(c, P.s, w, 0.0, d, &ta, &tb)) {
+          double L = tb - ta, tmax = fmax(fabs(ta), fabs(tb));
+          /* four FP32 units in the last place of the larger parameter */
+          chord = (wt > 0 ? wtau / wt : 0) * 4.0 * ldexp(1.0, ilogb(tmax) - 23) / L;
+        }
+        bound[(size_t)j * c->nu + i] = namb ? INFINITY : b + chord;
+      }
     }
   }
+  free(tau_n);
   return ORC_OK;
 }
 

@@ -1,0 +1,243 @@
+"""ctypes binding of include/mc.h: same entry points, argument marshalling only.
+
+Device buffers are torch tensors on the context's CUDA device; streams are
+torch streams (their raw cudaStream_t handles are passed through).  Host
+arrays (angles, spectrum) are numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import OUT as _LIB_PATH
+
+MC_OK = 0
+_ERRORS = {
+    -1: "MC_ERR_INVALID_ARG",
+    -2: "MC_ERR_STATE",
+    -3: "MC_ERR_CUDA",
+    -4: "MC_ERR_OOM",
+    -5: "MC_ERR_TIMEOUT",
+    -6: "MC_ERR_LIMIT",
+    -7: "MC_ERR_INTERNAL",
+    -8: "MC_ERR_IO",
+}
+STAT_NAMES = [
+    "histories", "flight_steps", "nee_steps", "nee_rays", "photo", "compton", "rayleigh", "escape", "limit",
+    "sampler_fail", "transport_ms", "primary_ms",
+]
+EXPORTED = [
+    "mc_default_options", "mc_create", "mc_destroy", "mc_set_options", "mc_last_error", "mc_load_tables",
+    "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
+    "mc_last_stats", "mc_smooth_upsample",
+]
+
+
+class MCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("n_split", C.c_int),
+        ("rr_threshold", C.c_float),
+        ("max_scatter_order", C.c_int),
+        ("n_batches", C.c_int),
+        ("block_size", C.c_int),
+        ("blocks_per_sm", C.c_int),
+        ("tally_mode", C.c_int),
+        ("sg_window", C.c_int),
+        ("sg_order", C.c_int),
+        ("cubic_a", C.c_float),
+        ("denoise_mode", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def library():
+    """Load libmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise OSError(f"{_LIB_PATH} is missing: build it with paper_2201_13191_gb300.build()")
+        L = C.CDLL(_LIB_PATH)
+        P, i, f, u64, vp = C.c_void_p, C.c_int, C.c_float, C.c_uint64, C.c_void_p
+        L.mc_default_options.argtypes = [C.POINTER(Options)]
+        L.mc_default_options.restype = None
+        L.mc_create.argtypes = [C.POINTER(P), i, C.POINTER(Options)]
+        L.mc_destroy.argtypes = [P]
+        L.mc_destroy.restype = None
+        L.mc_set_options.argtypes = [P, C.POINTER(Options)]
+        L.mc_last_error.argtypes = [P]
+        L.mc_last_error.restype = C.c_char_p
+        L.mc_load_tables.argtypes = [P, C.c_char_p]
+        L.mc_load_volume.argtypes = [P, vp, vp, i, i, i, f, f, f, i, vp]
+        L.mc_set_spectrum.argtypes = [P, vp, vp, i]
+        L.mc_set_geometry.argtypes = [P, f, f, i, i, f, f]
+        L.mc_project.argtypes = [P, vp, i, u64, f, u64, vp, vp, vp, vp]
+        L.mc_project_histories.argtypes = [P, vp, i, u64, u64, u64, f, u64, vp, vp]
+        L.mc_last_stats.argtypes = [P, C.POINTER(C.c_double), i]
+        L.mc_smooth_upsample.argtypes = [P, vp, i, vp, i, i, vp, i, vp, i, i, vp]
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _t_ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One mc_ctx on a CUDA device.  Method names follow the C entry points."""
+
+    def __init__(self, device=0, **options):
+        import torch
+
+        self.torch = torch
+        self.L = library()
+        self.device = torch.device("cuda", device)
+        opt = Options()
+        self.L.mc_default_options(C.byref(opt))
+        for k, v in options.items():
+            setattr(opt, k, v)
+        self.opt = opt
+        self.h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.L.mc_create(C.byref(self.h), device, C.byref(opt))
+        if rc != MC_OK:
+            raise MCError(rc, "mc_create failed")
+        self.nu = self.nv = 0
+
+    def _check(self, rc, allow_limit=False):
+        if rc == MC_OK or (allow_limit and rc == -6):
+            return rc
+        raise MCError(rc, self.L.mc_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.L.mc_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            setattr(self.opt, k, v)
+        self._check(self.L.mc_set_options(self.h, C.byref(self.opt)))
+
+    def load_tables(self, path):
+        self._check(self.L.mc_load_tables(self.h, str(path).encode()))
+
+    def load_volume(self, mat, rho_fp16, spacing, stream=None):
+        """mat: uint8 [nz][ny][nx]; rho_fp16: uint16 (binary16 bits) or float16, numpy (host) or torch (host/device)."""
+        torch = self.torch
+        if isinstance(mat, np.ndarray):
+            mat = np.ascontiguousarray(mat, dtype=np.uint8)
+            rho = np.ascontiguousarray(rho_fp16).view(np.uint16)
+            nz, ny, nx = mat.shape
+            pm, pr, dev = _np_ptr(mat), _np_ptr(rho), 0
+        else:
+            mat = mat.contiguous()
+            rho = rho_fp16.contiguous()
+            nz, ny, nx = mat.shape
+            pm, pr, dev = _t_ptr(mat), _t_ptr(rho), int(mat.is_cuda)
+        dx, dy, dz = spacing
+        self._check(
+            self.L.mc_load_volume(self.h, pm, pr, nx, ny, nz, dx, dy, dz, dev, _stream_handle(stream))
+        )
+        self._keep = (mat, rho)
+
+    def set_spectrum(self, energies, weights):
+        E = np.ascontiguousarray(energies, dtype=np.float32)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        self._check(self.L.mc_set_spectrum(self.h, _np_ptr(w), _np_ptr(E), len(E)))
+
+    def set_geometry(self, sod, sdd, nu, nv, pu, pv):
+        self.nu, self.nv = nu, nv
+        self._check(self.L.mc_set_geometry(self.h, sod, sdd, nu, nv, pu, pv))
+
+    def setup(self, wl):
+        v = wl["volume"]
+        self.load_volume(v["mat"], v["rho"], v["spacing"])
+        self.set_spectrum(wl["energies"], wl["weights"])
+        self.set_geometry(**wl["geometry"])
+
+    def empty_images(self, n_angles):
+        return self.torch.empty((n_angles, self.nv, self.nu), dtype=self.torch.float32, device=self.device)
+
+    def project(self, angles, n_photons, step_mm, seed, primary=True, scatter=True, variance=False, out=None,
+                stream=None, allow_limit=False):
+        """Returns dict(primary=, scatter=, variance=) of [n_angles][nv][nu] FP32 device tensors."""
+        a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
+        out = dict(out or {})
+        if primary and out.get("primary") is None:
+            out["primary"] = self.empty_images(len(a))
+        if scatter and out.get("scatter") is None:
+            out["scatter"] = self.empty_images(len(a))
+        if variance and out.get("variance") is None:
+            out["variance"] = self.empty_images(len(a))
+        rc = self.L.mc_project(
+            self.h, _np_ptr(a), len(a), int(n_photons), float(step_mm), int(seed),
+            _t_ptr(out.get("primary") if primary else None), _t_ptr(out.get("scatter") if scatter else None),
+            _t_ptr(out.get("variance") if variance else None), _stream_handle(stream),
+        )
+        self._check(rc, allow_limit)
+        return out
+
+    def project_histories(self, angles, n_photons, h_begin, h_count, step_mm, seed, out=None, stream=None):
+        a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
+        if out is None:
+            out = self.empty_images(len(a))
+        rc = self.L.mc_project_histories(
+            self.h, _np_ptr(a), len(a), int(n_photons), int(h_begin), int(h_count), float(step_mm), int(seed),
+            _t_ptr(out), _stream_handle(stream),
+        )
+        self._check(rc)
+        return out
+
+    def last_stats(self):
+        buf = (C.c_double * len(STAT_NAMES))()
+        self._check(self.L.mc_last_stats(self.h, buf, len(STAT_NAMES)))
+        return dict(zip(STAT_NAMES, list(buf)))
+
+    def smooth_upsample(self, images, in_angles, out_angles, NU, NV, out=None, stream=None):
+        torch = self.torch
+        images = images.contiguous()
+        n_in, nv, nu = images.shape
+        ia = np.ascontiguousarray(np.atleast_1d(in_angles), dtype=np.float32)
+        oa = np.ascontiguousarray(np.atleast_1d(out_angles), dtype=np.float32)
+        if out is None:
+            out = torch.empty((len(oa), NV, NU), dtype=torch.float32, device=images.device)
+        self._check(
+            self.L.mc_smooth_upsample(
+                self.h, _t_ptr(images), n_in, _np_ptr(ia), nu, nv, _t_ptr(out), len(oa), _np_ptr(oa), NU, NV,
+                _stream_handle(stream),
+            )
+        )
+        return out

@@ -1,0 +1,138 @@
+// Primary image, eq. (Ip) of arXiv 2201.13191 Sec. II-A: for every pixel the
+// ray from the source to the pixel centre is marched with the fixed step
+// (Sec. II-C.2); the per-material column masses rho*L are summed exactly in
+// 64-bit fixed point (each FP16 density is an integer multiple of 2^-24), and
+// the spectrum sum S(E) eta(E) exp(-mu(E) L) runs over the energy bins.
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "mc_device.cuh"
+
+namespace mcx {
+namespace {
+
+constexpr float kPi = 3.14159265358979f;
+
+// FP16 bit pattern -> value * 2^24 as an exact integer (finite, non-negative inputs).
+__device__ __forceinline__ unsigned long long fp16_fixed24(uint16_t b) {
+  const uint32_t e = (b >> 10) & 31u, f = b & 1023u;
+  return e == 0 ? (unsigned long long)f : ((unsigned long long)(f | 1024u) << (e - 1));
+}
+
+__global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
+  extern __shared__ float s_mub[];  // [n_bins][n_mat]: 0.1 * mu/rho at each bin energy
+  const int nm = P.tab.n_mat, nb = P.spec.n_bins, ns = P.tab.n_stage;
+  for (int q = threadIdx.x; q < nb * nm; q += blockDim.x) {
+    const int n = q / nm, m = q % nm;
+    const float E = P.spec.energy[n];
+    const float x = (E - P.tab.E0) * P.tab.inv_dE;
+    const int i = max(0, min(__float2int_rd(x), ns - 2));
+    const float f = x - (float)i;
+    const float2 v = P.tab.blob[(TAB_TOT * nm + m) * ns + i];
+    s_mub[q] = 0.1f * fmaf(f, v.y, v.x);
+  }
+  __syncthreads();
+  const GeomView& G = P.geo;
+  const VolumeView& V = P.vol;
+  const int npix = G.nu * G.nv;
+  const int a = blockIdx.y;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int i = pix % G.nu, j = pix / G.nu;
+  const Pose ps = make_pose(G, __ldg(P.angles + a));
+  const float3 X = det_point(G, ps, (float)i + 0.5f, (float)j + 0.5f);
+  const float3 D = sub3(X, ps.s);
+  const float d = sqrtf(dot3(D, D));
+  const float3 w = make_float3(D.x / d, D.y / d, D.z / d);
+  unsigned long long acc[kMaxMat];
+#pragma unroll
+  for (int m = 0; m < kMaxMat; ++m) acc[m] = 0ull;
+  float ta, tb, h = 0.f;
+  if (clip_box(V, ps.s, w, 0.f, d, ta, tb)) {
+    const float L = tb - ta;
+    const int n = step_count(L, P.step);
+    h = L / (float)n;
+    VoxRay r;
+    r.set(V, ps.s, w);
+    const uint16_t* rho = reinterpret_cast<const uint16_t*>(V.rho);
+    int cur = __ldg(V.mat + r.voxel(V, fmaf(0.5f, h, ta)));
+    unsigned long long run = 0ull;
+    for (int k = 0; k < n; ++k) {
+      const int v = r.voxel(V, fmaf((float)k + 0.5f, h, ta));
+      const int m = __ldg(V.mat + v);
+      if (m != cur) {
+#pragma unroll
+        for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+        cur = m;
+        run = 0ull;
+      }
+      run += fp16_fixed24(__ldg(rho + v));
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+  }
+  float rl[kMaxMat];
+#pragma unroll
+  for (int m = 0; m < kMaxMat; ++m) rl[m] = (float)acc[m] * 5.9604644775390625e-08f * h;  // 2^-24
+  float sum = 0.f;
+  for (int n = 0; n < nb; ++n) {
+    const float S = __ldg(P.spec.sn + n);
+    if (S == 0.f) continue;
+    float tau = 0.f;
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m)
+      if (m < nm) tau = fmaf(s_mub[n * nm + m], rl[m], tau);
+    sum = fmaf(S * __ldg(P.spec.energy + n), expf(-tau), sum);
+  }
+  const float cosg = G.sdd / d;
+  P.out[(size_t)a * npix + pix] = sum * (G.pu * G.pv) * cosg / (4.f * kPi * d * d);
+}
+
+}  // namespace
+
+cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s) {
+  const int block = 256;
+  const int npix = p.geo.nu * p.geo.nv;
+  dim3 grid((npix + block - 1) / block, p.n_angles);
+  const int smem = p.spec.n_bins * p.tab.n_mat * 4;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_primary, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_primary<<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace mcx
+
+// Device-side validation of a volume given by device pointers: every material
+// id below n_mat and every density a finite, non-negative binary16.
+namespace mcx {
+namespace {
+__global__ void k_validate_volume(const uint8_t* __restrict__ mat, const uint16_t* __restrict__ rho, size_t n,
+                                  int n_mat, int* bad) {
+  int b = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint16_t h = rho[i];
+    b |= (mat[i] >= n_mat) | (((h & 0x8000u) != 0) & ((h & 0x7fffu) != 0)) | (((h >> 10) & 31u) == 31u);
+  }
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+}  // namespace
+
+cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size_t n, int n_mat, cudaStream_t s,
+                                   int* bad_host) {
+  int* d_bad = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d_bad, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_validate_volume<<<1024, 256, 0, s>>>(mat, rho, n, n_mat, d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad_host, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d_bad, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+}  // namespace mcx

@@ -1,0 +1,733 @@
+// C ABI of the GB300 Monte Carlo scatter forward projection (include/mc.h):
+// context, argument validation, table/volume/spectrum staging, launches.
+// Host code only marshals inputs and sequences kernels; every step of the
+// method runs in the kernels of k_transport.cu, k_primary.cu and k_post.cu.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mc_device.cuh"
+#include "mc_internal.h"
+
+using namespace mcx;
+
+struct mc_ctx {
+  int device = 0;
+  int sm_count = 0;
+  mc_options opt{};
+  std::string err;
+  // tables (host FP64 copies, file order)
+  bool have_tables = false;
+  int n_mat = 0, n_E = 0;
+  double E0 = 0, dE = 1, r0 = 0, mec2 = 0, hc = 0;
+  std::vector<double> pe, in, co, icoh;  // [n_mat][n_E]
+  int n_comp[kMaxMat] = {};
+  double comp[kMaxMat][kMaxComp][3] = {};
+  // staged FP32 blob (device)
+  float2* d_blob = nullptr;
+  int blob_bytes = 0, blob_stage = 0;
+  bool blob_dirty = true;
+  // volume
+  bool have_volume = false;
+  uint8_t* d_mat = nullptr;
+  __half* d_rho = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  float dx = 0, dy = 0, dz = 0;
+  // spectrum
+  bool have_spectrum = false;
+  std::vector<double> S;
+  std::vector<float> Ebin;
+  void* d_spec = nullptr;  // prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n]
+  size_t d_spec_cap = 0;
+  // geometry
+  bool have_geometry = false;
+  float sod = 0, sdd = 0, pu = 0, pv = 0;
+  int nu = 0, nv = 0;
+  // scratch
+  double* d_tally = nullptr;
+  size_t tally_cap = 0;
+  unsigned long long* d_stats = nullptr;
+  float* d_angles = nullptr;
+  int angles_cap = 0;
+  float* d_post = nullptr;  // post-processing scratch
+  size_t post_cap = 0;
+  double stats[MC_STAT_N] = {};
+  cudaEvent_t ev[4] = {};
+};
+
+namespace {
+
+int fail(mc_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(mc_ctx* c, cudaError_t e, const char* where) {
+  const int code = (e == cudaErrorMemoryAllocation) ? MC_ERR_OOM : MC_ERR_CUDA;
+  return fail(c, code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                           \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+template <class T>
+cudaError_t ensure(T*& p, size_t& cap, size_t n) {
+  if (n <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void**)&p, n * sizeof(T));
+  if (e == cudaSuccess) cap = n;
+  return e;
+}
+
+int validate_options(const mc_options* o, std::string& why) {
+  if (o->n_split < 1 || o->n_split > 4096) return why = "n_split must be in [1, 4096]", -1;
+  if (!(o->rr_threshold >= 0.f)) return why = "rr_threshold must be >= 0", -1;
+  if (o->max_scatter_order < 1) return why = "max_scatter_order must be >= 1", -1;
+  if (o->n_batches < 1 || o->n_batches > 1024) return why = "n_batches must be in [1, 1024]", -1;
+  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
+    return why = "block_size must be 0 or a multiple of 32 in [32, 256]", -1;
+  if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return why = "blocks_per_sm must be in [0, 64]", -1;
+  if (o->tally_mode < 0 || o->tally_mode > 2) return why = "tally_mode must be 0, 1 or 2", -1;
+  if (o->sg_order < 0 || o->sg_window < o->sg_order + 2 || o->sg_window % 2 == 0 || o->sg_window > 31)
+    return why = "sg_window must be odd, >= sg_order + 2 and <= 31", -1;
+  if (!(o->cubic_a < 0.f && o->cubic_a > -3.f)) return why = "cubic_a must be in (-3, 0)", -1;
+  if (o->denoise_mode != 0 && o->denoise_mode != 2) return why = "denoise_mode must be 0 or 2", -1;
+  return 0;
+}
+
+// Klein-Nishina total per electron / (pi r0^2), closed form with its series
+// where the closed form cancels.
+double kn_norm(double E, double mec2) {
+  const double k = E / mec2;
+  if (k < 1e-3) return 8.0 / 3.0 * (1.0 - 2.0 * k + 5.2 * k * k - 13.3 * k * k * k);
+  const double l = std::log1p(2.0 * k);
+  const double a = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / (1.0 + 2.0 * k) - l / k);
+  return 2.0 * (a + l / (2.0 * k) - (1.0 + 3.0 * k) / ((1.0 + 2.0 * k) * (1.0 + 2.0 * k)));
+}
+
+// Build and upload the FP32 shared-memory blob for the nodes the spectrum can reach.
+int stage_tables(mc_ctx* ctx) {
+  if (!ctx->blob_dirty && ctx->d_blob) return MC_OK;
+  double Emax = ctx->E0 + 1.0;
+  for (size_t n = 0; n < ctx->S.size(); ++n) Emax = std::max(Emax, (double)ctx->Ebin[n]);
+  int ns = (int)std::floor((Emax - ctx->E0) / ctx->dE) + 2;
+  ns = std::max(2, std::min(ns, ctx->n_E));
+  const int nm = ctx->n_mat;
+  const int bytes = tab_blob_bytes(nm, ns);
+  std::vector<unsigned char> blob(bytes, 0);
+  float2* tab = reinterpret_cast<float2*>(blob.data());
+  const std::vector<double>* src[kTabKinds] = {nullptr, &ctx->pe, &ctx->in, &ctx->co, &ctx->icoh};
+  for (int kind = 0; kind < kTabKinds; ++kind) {
+    for (int m = 0; m < nm; ++m) {
+      for (int i = 0; i < ns; ++i) {
+        auto val = [&](int j) {
+          const size_t q = (size_t)m * ctx->n_E + j;
+          if (kind == TAB_TOT) return ctx->pe[q] + ctx->in[q] + ctx->co[q];
+          return (*src[kind])[q];
+        };
+        const double v0 = val(i);
+        const double v1 = val(std::min(i + 1, ctx->n_E - 1));
+        tab[(kind * nm + m) * ns + i] = make_float2((float)v0, (float)(v1 - v0));
+      }
+    }
+  }
+  float2* jkn = reinterpret_cast<float2*>(blob.data() + tab_off_jkn(nm, ns));
+  for (int i = 0; i < ns; ++i) {
+    const double E = ctx->E0 + ctx->dE * i;
+    const double j0 = kn_norm(E, ctx->mec2), j1 = kn_norm(E + ctx->dE, ctx->mec2);
+    jkn[i] = make_float2((float)j0, (float)(j1 - j0));
+  }
+  float2* comp = reinterpret_cast<float2*>(blob.data() + tab_off_comp(nm, ns));
+  int* ncomp = reinterpret_cast<int*>(blob.data() + tab_off_ncomp(nm, ns));
+  for (int m = 0; m < nm; ++m) {
+    ncomp[m] = ctx->n_comp[m];
+    for (int i = 0; i < kMaxComp; ++i) {
+      const double Z = ctx->comp[m][i][0], w = ctx->comp[m][i][1], b = ctx->comp[m][i][2];
+      comp[m * kMaxComp + i] = i < ctx->n_comp[m] ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
+    }
+  }
+  if (ctx->d_blob) cudaFree(ctx->d_blob);
+  ctx->d_blob = nullptr;
+  CK(cudaMalloc((void**)&ctx->d_blob, bytes), "table blob allocation");
+  CK(cudaMemcpy(ctx->d_blob, blob.data(), bytes, cudaMemcpyHostToDevice), "table blob upload");
+  ctx->blob_bytes = bytes;
+  ctx->blob_stage = ns;
+  ctx->blob_dirty = false;
+  return MC_OK;
+}
+
+TableView table_view(const mc_ctx* c) {
+  TableView t;
+  t.blob = c->d_blob;
+  t.n_mat = c->n_mat;
+  t.n_stage = c->blob_stage;
+  t.blob_bytes = c->blob_bytes;
+  t.E0 = (float)c->E0;
+  t.dE = (float)c->dE;
+  t.inv_dE = (float)(1.0 / c->dE);
+  t.mec2 = (float)c->mec2;
+  t.inv_hc = (float)(1.0 / c->hc);
+  return t;
+}
+
+VolumeView volume_view(const mc_ctx* c) {
+  VolumeView v;
+  v.mat = c->d_mat;
+  v.rho = c->d_rho;
+  v.nx = c->nx; v.ny = c->ny; v.nz = c->nz;
+  v.dx = c->dx; v.dy = c->dy; v.dz = c->dz;
+  v.inv_dx = 1.f / c->dx; v.inv_dy = 1.f / c->dy; v.inv_dz = 1.f / c->dz;
+  v.hx = 0.5f * c->nx * c->dx; v.hy = 0.5f * c->ny * c->dy; v.hz = 0.5f * c->nz * c->dz;
+  return v;
+}
+
+GeomView geom_view(const mc_ctx* c) {
+  GeomView g;
+  g.sod = c->sod; g.sdd = c->sdd; g.pu = c->pu; g.pv = c->pv; g.nu = c->nu; g.nv = c->nv;
+  return g;
+}
+
+// Stratified counts (largest remainder, at least one photon per non-empty bin)
+// and the device spectrum block.
+int stage_spectrum(mc_ctx* ctx, uint64_t N, cudaStream_t s, SpectrumView& sv) {
+  const int n = (int)ctx->S.size();
+  std::vector<uint64_t> M(n, 0);
+  std::vector<int> elig(n, 0);
+  std::vector<double> fr(n, 0.0);
+  uint64_t sum = 0;
+  for (int i = 0; i < n; ++i) {
+    const double x = (double)N * ctx->S[i];
+    const double fl = std::floor(x);
+    if (ctx->S[i] <= 0) M[i] = 0;
+    else if (fl < 1.0) M[i] = 1;
+    else {
+      M[i] = (uint64_t)fl;
+      elig[i] = 1;
+      fr[i] = x - fl;
+    }
+    sum += M[i];
+  }
+  if (sum > N) return fail(ctx, MC_ERR_INVALID_ARG, "n_photons is smaller than the number of non-empty energy bins");
+  uint64_t rem = N - sum;
+  while (rem > 0) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (elig[i] == 1 && (best < 0 || fr[i] > fr[best])) best = i;
+    if (best < 0) break;
+    M[best] += 1;
+    elig[best] = 2;
+    --rem;
+  }
+  if (rem) return fail(ctx, MC_ERR_INTERNAL, "stratification did not place every photon");
+  const size_t bytes = (size_t)(n + 1) * 8 + (size_t)n * 12;
+  std::vector<unsigned char> host(bytes);
+  auto* pre = reinterpret_cast<unsigned long long*>(host.data());
+  float* en = reinterpret_cast<float*>(pre + n + 1);
+  float* wb = en + n;
+  float* sn = wb + n;
+  pre[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    pre[i + 1] = pre[i] + M[i];
+    en[i] = ctx->Ebin[i];
+    wb[i] = M[i] ? (float)(ctx->S[i] / (double)M[i]) : 0.f;
+    sn[i] = (float)ctx->S[i];
+  }
+  unsigned char* d = (unsigned char*)ctx->d_spec;
+  cudaError_t e = ensure(d, ctx->d_spec_cap, bytes);
+  ctx->d_spec = d;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum allocation");
+  e = cudaMemcpyAsync(ctx->d_spec, host.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum upload");
+  unsigned char* base = (unsigned char*)ctx->d_spec;
+  sv.prefix = reinterpret_cast<const unsigned long long*>(base);
+  sv.energy = reinterpret_cast<const float*>(base + (size_t)(n + 1) * 8);
+  sv.wbin = sv.energy + n;
+  sv.sn = sv.wbin + n;
+  sv.n_bins = n;
+  return MC_OK;
+}
+
+int check_ready(mc_ctx* ctx) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "tables not loaded");
+  if (!ctx->have_volume) return fail(ctx, MC_ERR_STATE, "volume not loaded");
+  if (!ctx->have_spectrum) return fail(ctx, MC_ERR_STATE, "spectrum not set");
+  if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
+  const double rmax = 0.5 * std::sqrt((double)ctx->nx * ctx->dx * ctx->nx * ctx->dx +
+                                      (double)ctx->ny * ctx->dy * ctx->ny * ctx->dy);
+  if (!(rmax < ctx->sod) || !(rmax < (double)ctx->sdd - ctx->sod))
+    return fail(ctx, MC_ERR_INVALID_ARG, "the volume must lie strictly between source and detector");
+  return MC_OK;
+}
+
+int upload_angles(mc_ctx* ctx, const float* angles, int n, cudaStream_t s) {
+  if (!angles || n < 1) return fail(ctx, MC_ERR_INVALID_ARG, "n_angles must be >= 1 with a host angle array");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(angles[i])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must be finite");
+  if (n > ctx->angles_cap) {
+    if (ctx->d_angles) cudaFree(ctx->d_angles);
+    ctx->d_angles = nullptr;
+    ctx->angles_cap = 0;
+    CK(cudaMalloc((void**)&ctx->d_angles, (size_t)n * 4), "angle allocation");
+    ctx->angles_cap = n;
+  }
+  CK(cudaMemcpyAsync(ctx->d_angles, angles, (size_t)n * 4, cudaMemcpyHostToDevice, s), "angle upload");
+  return MC_OK;
+}
+
+// Shared body of mc_project / mc_project_histories.
+int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uint64_t h_begin, uint64_t h_count,
+                 float step, uint64_t seed, float* primary_out, float* scatter_out, float* var_out, void* stream) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!(step > 0.f) || !std::isfinite(step)) return fail(ctx, MC_ERR_INVALID_ARG, "step_mm must be > 0");
+  {
+    // bound the steps of one march: the longest chord is the volume diagonal
+    const double diag = std::sqrt((double)ctx->nx * ctx->dx * ctx->nx * ctx->dx + (double)ctx->ny * ctx->dy * ctx->ny * ctx->dy +
+                                  (double)ctx->nz * ctx->dz * ctx->nz * ctx->dz);
+    if (diag / step > 4.0e6) return fail(ctx, MC_ERR_INVALID_ARG, "step_mm too small: more than 4e6 steps per chord");
+  }
+  if (N < 1) return fail(ctx, MC_ERR_INVALID_ARG, "n_photons must be >= 1");
+  if (h_begin > N || h_count > N - h_begin) return fail(ctx, MC_ERR_INVALID_ARG, "history range outside the run");
+  if (var_out && ctx->opt.n_batches < 2) return fail(ctx, MC_ERR_INVALID_ARG, "scatter_var_out needs n_batches >= 2");
+  const int nb_img = var_out ? ctx->opt.n_batches : 1;
+  rc = stage_tables(ctx);
+  if (rc) return rc;
+  SpectrumView sv;
+  rc = stage_spectrum(ctx, N, s, sv);
+  if (rc) return rc;
+  rc = upload_angles(ctx, angles, n_angles, s);
+  if (rc) return rc;
+  for (double& v : ctx->stats) v = 0;
+  const size_t img = (size_t)ctx->nu * ctx->nv * n_angles;
+  CK(cudaMemsetAsync(ctx->d_stats, 0, S_NSTAT * 8, s), "stats reset");
+  float ms_t = 0, ms_p = 0;
+  if (primary_out) {
+    PrimaryParams pp;
+    pp.tab = table_view(ctx);
+    pp.vol = volume_view(ctx);
+    pp.geo = geom_view(ctx);
+    pp.spec = sv;
+    pp.angles = ctx->d_angles;
+    pp.n_angles = n_angles;
+    pp.step = step;
+    pp.out = primary_out;
+    CK(cudaEventRecord(ctx->ev[2], s), "event");
+    CK(launch_primary(pp, s), "primary launch");
+    CK(cudaEventRecord(ctx->ev[3], s), "event");
+  }
+  if (scatter_out) {
+    CK(ensure(ctx->d_tally, ctx->tally_cap, img * nb_img), "tally allocation");
+    CK(cudaMemsetAsync(ctx->d_tally, 0, img * nb_img * sizeof(double), s), "tally reset");
+    TransportParams tp;
+    tp.tab = table_view(ctx);
+    tp.vol = volume_view(ctx);
+    tp.geo = geom_view(ctx);
+    tp.spec = sv;
+    tp.angles = ctx->d_angles;
+    tp.n_angles = n_angles;
+    tp.n_photons = N;
+    tp.h_begin = h_begin;
+    tp.h_count = h_count;
+    tp.step = step;
+    tp.seed = seed;
+    tp.n_split = ctx->opt.n_split;
+    tp.rr_threshold = ctx->opt.rr_threshold;
+    tp.max_order = ctx->opt.max_scatter_order;
+    tp.n_batches = nb_img;
+    tp.tally = ctx->d_tally;
+    tp.stats = ctx->d_stats;
+    const int block = ctx->opt.block_size ? ctx->opt.block_size : 256;
+    const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block);
+    int per_sm = ctx->opt.blocks_per_sm;
+    if (per_sm == 0) {
+      CK(transport_occupancy(block, smem, &per_sm), "occupancy query");
+      per_sm = std::max(1, per_sm);
+    }
+    const unsigned long long work = (unsigned long long)n_angles * h_count;
+    const unsigned long long need = (work + block - 1) / block;
+    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(need, (unsigned long long)ctx->sm_count * per_sm));
+    CK(cudaEventRecord(ctx->ev[0], s), "event");
+    if (work > 0) CK(launch_transport(tp, grid, block, s), "transport launch");
+    CK(cudaEventRecord(ctx->ev[1], s), "event");
+    CK(launch_finalize(ctx->d_tally, nb_img, img, scatter_out, var_out, s), "finalize launch");
+  }
+  unsigned long long st[S_NSTAT] = {};
+  CK(cudaMemcpyAsync(st, ctx->d_stats, S_NSTAT * 8, cudaMemcpyDeviceToHost, s), "stats readback");
+  CK(cudaStreamSynchronize(s), "stream synchronize");
+  if (scatter_out) CK(cudaEventElapsedTime(&ms_t, ctx->ev[0], ctx->ev[1]), "event time");
+  if (primary_out) CK(cudaEventElapsedTime(&ms_p, ctx->ev[2], ctx->ev[3]), "event time");
+  const int map[10] = {S_HIST, S_FLIGHT_STEPS, S_NEE_STEPS, S_NEE_RAYS, S_PHOTO, S_COMPTON, S_RAYLEIGH, S_ESCAPE, S_LIMIT, S_SAMPLER_FAIL};
+  for (int i = 0; i < 10; ++i) ctx->stats[i] = (double)st[map[i]];
+  ctx->stats[10] = ms_t;
+  ctx->stats[11] = ms_p;
+  if (st[S_INTERNAL]) return fail(ctx, MC_ERR_TIMEOUT, "a block gave up waiting for its table copy");
+  if (st[S_LIMIT] || st[S_SAMPLER_FAIL])
+    return fail(ctx, MC_ERR_LIMIT, "histories hit the scatter-order or sampler cap (outputs valid)");
+  return MC_OK;
+}
+
+// Savitzky-Golay hat matrix H = V (V^T V)^-1 V^T for window win, order k (FP64,
+// Gauss-Jordan on the (k+1)^2 normal matrix).
+void sg_hat(int win, int k, std::vector<float>& H) {
+  const int m = win / 2, q = k + 1;
+  std::vector<double> V(win * q), A(q * q, 0.0), Ai(q * q, 0.0);
+  for (int j = 0; j < win; ++j)
+    for (int c = 0; c < q; ++c) V[j * q + c] = std::pow((double)(j - m), c);
+  for (int r = 0; r < q; ++r)
+    for (int c = 0; c < q; ++c) {
+      double s = 0;
+      for (int j = 0; j < win; ++j) s += V[j * q + r] * V[j * q + c];
+      A[r * q + c] = s;
+    }
+  for (int r = 0; r < q; ++r) Ai[r * q + r] = 1.0;
+  for (int col = 0; col < q; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < q; ++r)
+      if (std::fabs(A[r * q + col]) > std::fabs(A[piv * q + col])) piv = r;
+    for (int c = 0; c < q; ++c) {
+      std::swap(A[col * q + c], A[piv * q + c]);
+      std::swap(Ai[col * q + c], Ai[piv * q + c]);
+    }
+    const double d = A[col * q + col];
+    for (int c = 0; c < q; ++c) {
+      A[col * q + c] /= d;
+      Ai[col * q + c] /= d;
+    }
+    for (int r = 0; r < q; ++r) {
+      if (r == col) continue;
+      const double f = A[r * q + col];
+      for (int c = 0; c < q; ++c) {
+        A[r * q + c] -= f * A[col * q + c];
+        Ai[r * q + c] -= f * Ai[col * q + c];
+      }
+    }
+  }
+  H.assign(win * win, 0.f);
+  for (int p = 0; p < win; ++p)
+    for (int j = 0; j < win; ++j) {
+      double s = 0;
+      for (int r = 0; r < q; ++r)
+        for (int c = 0; c < q; ++c) s += V[p * q + r] * Ai[r * q + c] * V[j * q + c];
+      H[p * win + j] = (float)s;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void mc_default_options(mc_options* o) {
+  if (!o) return;
+  o->n_split = 10;
+  o->rr_threshold = 0.f;
+  o->max_scatter_order = 64;
+  o->n_batches = 1;
+  o->block_size = 0;
+  o->blocks_per_sm = 0;
+  o->tally_mode = MC_TALLY_AUTO;
+  o->sg_window = 9;
+  o->sg_order = 3;
+  o->cubic_a = -0.5f;
+  o->denoise_mode = 0;
+}
+
+int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {
+  if (!out) return MC_ERR_INVALID_ARG;
+  *out = nullptr;
+  mc_ctx* ctx = new (std::nothrow) mc_ctx();
+  if (!ctx) return MC_ERR_OOM;
+  mc_default_options(&ctx->opt);
+  if (opt) {
+    std::string why;
+    if (validate_options(opt, why)) {
+      delete ctx;
+      return MC_ERR_INVALID_ARG;
+    }
+    ctx->opt = *opt;
+  }
+  ctx->device = cuda_device;
+  cudaError_t e = cudaSetDevice(cuda_device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cuda_device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_stats, S_NSTAT * 8);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e != cudaSuccess) {
+    mc_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA;
+  }
+  *out = ctx;
+  return MC_OK;
+}
+
+void mc_destroy(mc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->d_blob);
+  cudaFree(ctx->d_mat);
+  cudaFree(ctx->d_rho);
+  cudaFree(ctx->d_spec);
+  cudaFree(ctx->d_tally);
+  cudaFree(ctx->d_stats);
+  cudaFree(ctx->d_angles);
+  cudaFree(ctx->d_post);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int mc_set_options(mc_ctx* ctx, const mc_options* opt) {
+  if (!ctx || !opt) return MC_ERR_INVALID_ARG;
+  std::string why;
+  if (validate_options(opt, why)) return fail(ctx, MC_ERR_INVALID_ARG, why);
+  ctx->opt = *opt;
+  return MC_OK;
+}
+
+const char* mc_last_error(const mc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mc_load_tables(mc_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, MC_ERR_INVALID_ARG, "null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, MC_ERR_IO, std::string("cannot open table file ") + path);
+  char magic[8];
+  int32_t hdr[4];
+  double e2[2], k6[6];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MCXTAB01", 8) == 0 &&
+            std::fread(hdr, 4, 4, f) == 4 && std::fread(e2, 8, 2, f) == 2 && std::fread(k6, 8, 6, f) == 6;
+  if (!ok || hdr[0] != 1 || hdr[3] != kMaxComp || hdr[2] < 2) {
+    std::fclose(f);
+    return fail(ctx, MC_ERR_IO, "malformed table header");
+  }
+  if (hdr[1] < 1 || hdr[1] > kMaxMat) {
+    std::fclose(f);
+    return fail(ctx, MC_ERR_INVALID_ARG, "the table holds more materials than MC_MAX_MATERIALS");
+  }
+  const int nm = hdr[1], nE = hdr[2];
+  int ncomp[kMaxMat];
+  double comp[kMaxMat][kMaxComp][3];
+  for (int m = 0; m < nm; ++m) {
+    char name[16];
+    double dens;
+    int32_t nc[2];
+    double buf[kMaxComp * 3];
+    if (std::fread(name, 1, 16, f) != 16 || std::fread(&dens, 8, 1, f) != 1 || std::fread(nc, 4, 2, f) != 2 ||
+        std::fread(buf, 8, kMaxComp * 3, f) != (size_t)kMaxComp * 3 || nc[0] < 1 || nc[0] > kMaxComp) {
+      std::fclose(f);
+      return fail(ctx, MC_ERR_IO, "malformed material record");
+    }
+    ncomp[m] = nc[0];
+    for (int i = 0; i < kMaxComp; ++i)
+      for (int j = 0; j < 3; ++j) comp[m][i][j] = buf[i * 3 + j];
+    for (int i = 0; i < nc[0]; ++i)
+      if (!(comp[m][i][2] > 0)) {
+        std::fclose(f);
+        return fail(ctx, MC_ERR_IO, "form-factor width must be positive");
+      }
+  }
+  const size_t n = (size_t)nm * nE;
+  std::vector<double> a(n), b(n), c(n), d(n);
+  ok = std::fread(a.data(), 8, n, f) == n && std::fread(b.data(), 8, n, f) == n && std::fread(c.data(), 8, n, f) == n &&
+       std::fread(d.data(), 8, n, f) == n;
+  std::fclose(f);
+  if (!ok) return fail(ctx, MC_ERR_IO, "truncated table arrays");
+  ctx->n_mat = nm;
+  ctx->n_E = nE;
+  ctx->E0 = e2[0];
+  ctx->dE = e2[1];
+  ctx->r0 = k6[0];
+  ctx->mec2 = k6[1];
+  ctx->hc = k6[2];
+  ctx->pe.swap(a);
+  ctx->in.swap(b);
+  ctx->co.swap(c);
+  ctx->icoh.swap(d);
+  for (int m = 0; m < nm; ++m) {
+    ctx->n_comp[m] = ncomp[m];
+    std::memcpy(ctx->comp[m], comp[m], sizeof(comp[m]));
+  }
+  ctx->have_tables = true;
+  ctx->blob_dirty = true;
+  return MC_OK;
+}
+
+int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, int nx, int ny, int nz, float dx,
+                   float dy, float dz, int is_device_ptr, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "load tables before the volume");
+  if (!mat || !rho_fp16 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0))
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad volume arguments");
+  const size_t n = (size_t)nx * ny * nz;
+  if (n > (size_t)INT32_MAX) return fail(ctx, MC_ERR_INVALID_ARG, "volume larger than 2^31 voxels");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!is_device_ptr) {
+    // host data: validate here
+    for (size_t i = 0; i < n; ++i) {
+      if (mat[i] >= ctx->n_mat) return fail(ctx, MC_ERR_INVALID_ARG, "material id outside the table");
+      const uint16_t h = rho_fp16[i];
+      if ((h & 0x8000u) && (h & 0x7fffu)) return fail(ctx, MC_ERR_INVALID_ARG, "negative density");
+      if (((h >> 10) & 31u) == 31u) return fail(ctx, MC_ERR_INVALID_ARG, "non-finite density");
+    }
+  }
+  if (ctx->have_volume && (size_t)ctx->nx * ctx->ny * ctx->nz != n) {
+    cudaFree(ctx->d_mat);
+    cudaFree(ctx->d_rho);
+    ctx->d_mat = nullptr;
+    ctx->d_rho = nullptr;
+  }
+  ctx->have_volume = false;
+  if (!ctx->d_mat) CK(cudaMalloc((void**)&ctx->d_mat, n), "volume allocation");
+  if (!ctx->d_rho) CK(cudaMalloc((void**)&ctx->d_rho, n * 2), "volume allocation");
+  const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(ctx->d_mat, mat, n, kind, s), "volume copy");
+  CK(cudaMemcpyAsync(ctx->d_rho, rho_fp16, n * 2, kind, s), "volume copy");
+  if (is_device_ptr) {
+    // device data: validate on the device (max material id, finite non-negative densities)
+    int bad = 0;
+    cudaError_t e = validate_volume_device(ctx->d_mat, (const uint16_t*)ctx->d_rho, n, ctx->n_mat, s, &bad);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "volume validation");
+    if (bad) return fail(ctx, MC_ERR_INVALID_ARG, "volume holds an unknown material id or an invalid density");
+  }
+  ctx->nx = nx; ctx->ny = ny; ctx->nz = nz;
+  ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
+  ctx->have_volume = true;
+  return MC_OK;
+}
+
+int mc_set_spectrum(mc_ctx* ctx, const double* weights, const float* energies, int n) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "load tables before the spectrum");
+  if (!weights || !energies || n < 1 || n > MC_MAX_BINS) return fail(ctx, MC_ERR_INVALID_ARG, "bad spectrum size");
+  const double Emax = ctx->E0 + ctx->dE * (ctx->n_E - 1);
+  double sum = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!(weights[i] >= 0) || !std::isfinite(weights[i])) return fail(ctx, MC_ERR_INVALID_ARG, "weights must be >= 0");
+    if (!((double)energies[i] >= ctx->E0) || !((double)energies[i] <= Emax))
+      return fail(ctx, MC_ERR_INVALID_ARG, "energy outside the table range");
+    sum += weights[i];
+  }
+  if (!(sum > 0)) return fail(ctx, MC_ERR_INVALID_ARG, "weights sum to zero");
+  ctx->S.assign(n, 0.0);
+  ctx->Ebin.assign(energies, energies + n);
+  for (int i = 0; i < n; ++i) ctx->S[i] = weights[i] / sum;
+  ctx->have_spectrum = true;
+  ctx->blob_dirty = true;
+  return MC_OK;
+}
+
+int mc_set_geometry(mc_ctx* ctx, float sod, float sdd, int nu, int nv, float pu, float pv) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!(sod > 0) || !(sdd > sod) || nu < 1 || nv < 1 || !(pu > 0) || !(pv > 0) || (double)nu * nv > 1.0e9)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad geometry");
+  ctx->sod = sod; ctx->sdd = sdd; ctx->nu = nu; ctx->nv = nv; ctx->pu = pu; ctx->pv = pv;
+  ctx->have_geometry = true;
+  return MC_OK;
+}
+
+int mc_project(mc_ctx* ctx, const float* angles, int n_angles, uint64_t n_photons, float step_mm, uint64_t seed,
+               float* primary_out, float* scatter_out, float* scatter_var_out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!primary_out && !scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "no output requested");
+  if (scatter_var_out && !scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "variance needs scatter_out");
+  return project_impl(ctx, angles, n_angles, n_photons, 0, n_photons, step_mm, seed, primary_out, scatter_out,
+                      scatter_var_out, stream);
+}
+
+int mc_project_histories(mc_ctx* ctx, const float* angles, int n_angles, uint64_t n_photons, uint64_t h_begin,
+                         uint64_t h_count, float step_mm, uint64_t seed, float* scatter_out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "scatter_out is required");
+  return project_impl(ctx, angles, n_angles, n_photons, h_begin, h_count, step_mm, seed, nullptr, scatter_out,
+                      nullptr, stream);
+}
+
+int mc_last_stats(const mc_ctx* ctx, double* out, int n) {
+  if (!ctx || !out || n < 0 || n > MC_STAT_N) return MC_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) out[i] = ctx->stats[i];
+  return MC_OK;
+}
+
+int mc_smooth_upsample(mc_ctx* ctx, const float* in, int n_in, const float* in_angles, int nu, int nv, float* out,
+                       int n_out, const float* out_angles, int NU, int NV, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!in || !out || !in_angles || !out_angles || n_in < 1 || n_out < 1 || nu < 1 || nv < 1 || NU < 1 || NV < 1)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad smooth_upsample arguments");
+  const int win = ctx->opt.sg_window, ord = ctx->opt.sg_order;
+  const bool smooth = ctx->opt.denoise_mode == 0;
+  if (smooth && (nu < win || nv < win)) return fail(ctx, MC_ERR_INVALID_ARG, "image smaller than the smoothing window");
+  const double two_pi = 6.283185307179586;
+  for (int i = 0; i < n_in; ++i) {
+    if (!std::isfinite(in_angles[i])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must be finite");
+    if (i > 0 && !(in_angles[i] > in_angles[i - 1])) return fail(ctx, MC_ERR_INVALID_ARG, "in_angles must increase");
+  }
+  if (n_in > 1 && !((double)in_angles[n_in - 1] - in_angles[0] < two_pi))
+    return fail(ctx, MC_ERR_INVALID_ARG, "in_angles must span less than 2 pi");
+  // bracketing simulated angles for each requested angle (periodic in 2 pi)
+  std::vector<int> a0(n_out), a1(n_out);
+  std::vector<float> fa(n_out);
+  for (int o = 0; o < n_out; ++o) {
+    if (!std::isfinite(out_angles[o])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must be finite");
+    if (n_in == 1) {
+      a0[o] = a1[o] = 0;
+      fa[o] = 0.f;
+      continue;
+    }
+    double th = std::fmod((double)out_angles[o] - in_angles[0], two_pi);
+    if (th < 0) th += two_pi;
+    int k = n_in - 1;
+    for (int i = 0; i + 1 < n_in; ++i)
+      if (th < (double)in_angles[i + 1] - in_angles[0]) {
+        k = i;
+        break;
+      }
+    const double lo = (double)in_angles[k] - in_angles[0];
+    const double hi = (k + 1 < n_in) ? (double)in_angles[k + 1] - in_angles[0] : two_pi;
+    a0[o] = k;
+    a1[o] = (k + 1) % n_in;
+    fa[o] = (float)((th - lo) / (hi - lo));
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nimg = (size_t)n_in * nu * nv;
+  const size_t meta = (size_t)win * win + 3 * (size_t)n_out + 64;
+  CK(ensure(ctx->d_post, ctx->post_cap, 2 * nimg + meta), "post-processing allocation");
+  float* t0 = ctx->d_post;
+  float* t1 = t0 + nimg;
+  float* coef = t1 + nimg;
+  int* d_a0 = reinterpret_cast<int*>(coef + win * win);
+  int* d_a1 = d_a0 + n_out;
+  float* d_fa = reinterpret_cast<float*>(d_a1 + n_out);
+  std::vector<float> H;
+  sg_hat(win, ord, H);
+  std::vector<unsigned char> hostmeta((size_t)win * win * 4 + (size_t)n_out * 12);
+  std::memcpy(hostmeta.data(), H.data(), (size_t)win * win * 4);
+  std::memcpy(hostmeta.data() + (size_t)win * win * 4, a0.data(), (size_t)n_out * 4);
+  std::memcpy(hostmeta.data() + (size_t)win * win * 4 + (size_t)n_out * 4, a1.data(), (size_t)n_out * 4);
+  std::memcpy(hostmeta.data() + (size_t)win * win * 4 + (size_t)n_out * 8, fa.data(), (size_t)n_out * 4);
+  CK(cudaMemcpyAsync(coef, hostmeta.data(), hostmeta.size(), cudaMemcpyHostToDevice, s), "coefficient upload");
+  const float* src = in;
+  if (smooth) {
+    CK(launch_sg_rows(in, t0, n_in, nv, nu, coef, win, s), "smoothing launch");
+    CK(launch_sg_cols(t0, t1, n_in, nv, nu, coef, win, s), "smoothing launch");
+    src = t1;
+  }
+  CK(launch_lerp_upsample(src, nv, nu, out, n_out, NV, NU, d_a0, d_a1, d_fa, ctx->opt.cubic_a, s), "upsample launch");
+  CK(cudaStreamSynchronize(s), "stream synchronize");
+  return MC_OK;
+}
+
+}  // extern "C"

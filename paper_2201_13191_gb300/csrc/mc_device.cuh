@@ -1,0 +1,171 @@
+// Device helpers of the transport and primary kernels: counter-based random
+// numbers, cross-section table lookups, scanner geometry and the fixed-step
+// voxel march.  Everything here is FP32 (FP64 is used only for tallies).
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "mc_internal.h"
+
+namespace mcx {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32->64 products of the counter words with fixed multipliers, the high
+// halves xor-ed with the other counter words and the round key; the key is
+// bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// One history's stream: key = seed, counter = (block, angle, h_lo, h_hi);
+// the four words of each block are consumed in order.
+struct Rng {
+  uint2 key;
+  uint4 ctr;
+  uint4 buf;
+  int idx;
+  __device__ __forceinline__ void init(unsigned long long h, uint32_t angle, unsigned long long seed) {
+    key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    ctr = make_uint4(0u, angle, (uint32_t)h, (uint32_t)(h >> 32));
+    idx = 4;
+  }
+  __device__ __forceinline__ void refill() {
+    buf = philox4x32_10(ctr, key);
+    ctr.x += 1u;
+    idx = 0;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    if (idx == 4) refill();
+    const uint32_t v = idx == 0 ? buf.x : idx == 1 ? buf.y : idx == 2 ? buf.z : buf.w;
+    ++idx;
+    return v;
+  }
+  // Start of the next block of four.
+  __device__ __forceinline__ void align() { idx = 4; }
+  // Uniform on (0,1): ((x >> 9) + 1/2) 2^-23, exactly representable.
+  __device__ __forceinline__ float u() { return u01(next()); }
+  static __device__ __forceinline__ float u01(uint32_t x) {
+    return __fmul_rn((float)(x >> 9) + 0.5f, 1.1920928955078125e-07f);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Tables in shared memory: float2 (v_i, v_{i+1} - v_i) per node; linear in E.
+struct SmemTables {
+  const float2* tab;   // [kTabKinds][n_mat][n_stage]
+  const float2* jkn;   // [n_stage]
+  const float2* comp;  // [n_mat][kMaxComp]
+  const int* ncomp;    // [n_mat]
+  int n_mat, n_stage;
+  float E0, inv_dE, mec2, inv_hc;
+
+  __device__ __forceinline__ void locate(float E, int& i, float& f) const {
+    const float x = (E - E0) * inv_dE;
+    int k = __float2int_rd(x);
+    k = max(0, min(k, n_stage - 2));
+    i = k;
+    f = x - (float)k;
+  }
+  __device__ __forceinline__ float at(int kind, int m, int i, float f) const {
+    const float2 v = tab[(kind * n_mat + m) * n_stage + i];
+    return fmaf(f, v.y, v.x);
+  }
+  __device__ __forceinline__ float kn_norm(int i, float f) const {
+    const float2 v = jkn[i];
+    return fmaf(f, v.y, v.x);
+  }
+};
+
+// Byte offsets of the blob sections (all multiples of 8; total padded to 16).
+__host__ __device__ inline int tab_off_jkn(int n_mat, int n_stage) { return kTabKinds * n_mat * n_stage * 8; }
+__host__ __device__ inline int tab_off_comp(int n_mat, int n_stage) {
+  return tab_off_jkn(n_mat, n_stage) + n_stage * 8;
+}
+__host__ __device__ inline int tab_off_ncomp(int n_mat, int n_stage) {
+  return tab_off_comp(n_mat, n_stage) + n_mat * kMaxComp * 8;
+}
+__host__ __device__ inline int tab_blob_bytes(int n_mat, int n_stage) {
+  return (tab_off_ncomp(n_mat, n_stage) + n_mat * 4 + 15) & ~15;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of one angle (source on the circle of radius SOD about z).
+struct Pose {
+  float3 s, c, eu, n;  // source, panel centre, panel u axis, panel normal (toward source); e_v = z
+};
+__device__ __forceinline__ Pose make_pose(const GeomView& g, float beta) {
+  float sb, cb;
+  sincosf(beta, &sb, &cb);
+  Pose p;
+  p.s = make_float3(g.sod * cb, g.sod * sb, 0.f);
+  const float r = g.sod - g.sdd;
+  p.c = make_float3(r * cb, r * sb, 0.f);
+  p.eu = make_float3(-sb, cb, 0.f);
+  p.n = make_float3(cb, sb, 0.f);
+  return p;
+}
+// Panel point at continuous pixel coordinates (a, b); pixel (i, j) spans [i, i+1) x [j, j+1).
+__device__ __forceinline__ float3 det_point(const GeomView& g, const Pose& p, float a, float b) {
+  const float ou = (a - 0.5f * (float)g.nu) * g.pu;
+  const float ov = (b - 0.5f * (float)g.nv) * g.pv;
+  return make_float3(fmaf(ou, p.eu.x, p.c.x), fmaf(ou, p.eu.y, p.c.y), p.c.z + ov);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+
+// Slab clip of x + t w, t in [t0, t1], against the centred box of half extents h.
+__device__ __forceinline__ bool clip_box(const VolumeView& v, float3 x, float3 w, float t0, float t1, float& ta,
+                                         float& tb) {
+  float a = t0, b = t1;
+  const float px[3] = {x.x, x.y, x.z}, wx[3] = {w.x, w.y, w.z}, hx[3] = {v.hx, v.hy, v.hz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (wx[k] == 0.f) {
+      if (px[k] < -hx[k] || px[k] > hx[k]) return false;
+    } else {
+      float u = (-hx[k] - px[k]) / wx[k], q = (hx[k] - px[k]) / wx[k];
+      if (u > q) {
+        const float t = u;
+        u = q;
+        q = t;
+      }
+      a = fmaxf(a, u);
+      b = fminf(b, q);
+    }
+  }
+  ta = a;
+  tb = b;
+  return b > a;
+}
+
+// Ray in voxel units: v(t) = v0 + t vw, voxel = floor(v) clamped.
+struct VoxRay {
+  float3 v0, vw;
+  __device__ __forceinline__ void set(const VolumeView& vol, float3 x, float3 w) {
+    v0 = make_float3(fmaf(x.x, vol.inv_dx, 0.5f * (float)vol.nx), fmaf(x.y, vol.inv_dy, 0.5f * (float)vol.ny),
+                     fmaf(x.z, vol.inv_dz, 0.5f * (float)vol.nz));
+    vw = make_float3(w.x * vol.inv_dx, w.y * vol.inv_dy, w.z * vol.inv_dz);
+  }
+  __device__ __forceinline__ int voxel(const VolumeView& vol, float t) const {
+    const int ix = min(max(__float2int_rd(fmaf(t, vw.x, v0.x)), 0), vol.nx - 1);
+    const int iy = min(max(__float2int_rd(fmaf(t, vw.y, v0.y)), 0), vol.ny - 1);
+    const int iz = min(max(__float2int_rd(fmaf(t, vw.z, v0.z)), 0), vol.nz - 1);
+    return (iz * vol.ny + iy) * vol.nx + ix;
+  }
+};
+
+__device__ __forceinline__ int step_count(float L, float step) { return max(1, (int)ceilf(L / step)); }
+
+}  // namespace mcx

@@ -1,0 +1,107 @@
+// Internal interfaces of the GB300 library: parameter blocks passed by value to
+// the kernels and the launch wrappers each translation unit exports to the API.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mc.h"
+
+namespace mcx {
+
+constexpr int kMaxMat = MC_MAX_MATERIALS;
+constexpr int kMaxComp = 8;
+constexpr int kTabKinds = 5;  // tot, pe, incoh, coh, I_coh
+enum TabKind { TAB_TOT = 0, TAB_PE = 1, TAB_IN = 2, TAB_CO = 3, TAB_ICOH = 4 };
+
+// Statistic slots (uint64 counters on the device, doubles at the ABI).
+enum Stat {
+  S_HIST = 0, S_FLIGHT_STEPS, S_NEE_STEPS, S_NEE_RAYS, S_PHOTO, S_COMPTON, S_RAYLEIGH, S_ESCAPE,
+  S_LIMIT, S_SAMPLER_FAIL, S_INTERNAL, S_NSTAT
+};
+
+// Staged table blob (device global, copied per block into shared memory):
+//   float2 tab[kTabKinds][n_mat][n_stage]   (v_i, v_{i+1} - v_i)
+//   float2 jkn[n_stage]                      Klein-Nishina normalisation J(E)
+//   float2 comp[n_mat][kMaxComp]             (w Z^2, b) of the form factor
+//   int    ncomp[n_mat] (padded to 16 bytes)
+struct TableView {
+  const float2* blob;  // device
+  int n_mat;
+  int n_stage;         // nodes staged (prefix of the file's nodes)
+  int blob_bytes;      // multiple of 16
+  float E0, inv_dE, dE;
+  float mec2, inv_hc;
+};
+
+struct VolumeView {
+  const uint8_t* mat;
+  const __half* rho;
+  int nx, ny, nz;
+  float dx, dy, dz;
+  float inv_dx, inv_dy, inv_dz;
+  float hx, hy, hz;  // half extents (mm)
+};
+
+struct GeomView {
+  float sod, sdd, pu, pv;
+  int nu, nv;
+};
+
+struct SpectrumView {
+  const unsigned long long* prefix;  // [n_bins + 1] stratified history prefix sums
+  const float* energy;               // [n_bins]
+  const float* wbin;                 // [n_bins] S_n / M_n
+  const float* sn;                   // [n_bins] S_n
+  int n_bins;
+};
+
+struct TransportParams {
+  TableView tab;
+  VolumeView vol;
+  GeomView geo;
+  SpectrumView spec;
+  const float* angles;  // device [n_angles]
+  int n_angles;
+  unsigned long long n_photons, h_begin, h_count;
+  float step;
+  unsigned long long seed;
+  int n_split;
+  float rr_threshold;
+  int max_order;
+  int n_batches;
+  double* tally;                 // [n_batches][n_angles][nv][nu]
+  unsigned long long* stats;     // [S_NSTAT]
+};
+
+struct PrimaryParams {
+  TableView tab;
+  VolumeView vol;
+  GeomView geo;
+  SpectrumView spec;
+  const float* angles;
+  int n_angles;
+  float step;
+  float* out;  // [n_angles][nv][nu]
+};
+
+// launch wrappers (return cudaError_t of the launch)
+cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
+int transport_smem_bytes(const TableView& t, int n_bins, int block);
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm);
+cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
+cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
+// Checks a device-resident volume (ids < n_mat, finite non-negative binary16
+// densities); *bad_host = 1 if any voxel fails.  Synchronises s.
+cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size_t n, int n_mat, cudaStream_t s,
+                                   int* bad_host);
+
+// post-processing
+cudaError_t launch_sg_rows(const float* in, float* out, int n_img, int h, int w, const float* coef, int win,
+                           cudaStream_t s);
+cudaError_t launch_sg_cols(const float* in, float* out, int n_img, int h, int w, const float* coef, int win,
+                           cudaStream_t s);
+cudaError_t launch_lerp_upsample(const float* in, int nv, int nu, float* out, int n_out, int NV, int NU,
+                                 const int* a0, const int* a1, const float* fa, float cubic_a, cudaStream_t s);
+
+}  // namespace mcx

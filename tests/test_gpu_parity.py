@@ -1,0 +1,267 @@
+"""GPU vs oracle parity through the C ABI (arXiv 2201.13191 Sec. II-A, II-C).
+
+Primary images (eq. Ip) must match the FP64 oracle to 1e-5 relative per
+pixel; the only allowance is the oracle's own per-pixel bound of what an FP32
+re-evaluation may legitimately change (midpoints within 2e-4 voxel of a face
+between different voxels, FP32 rounding of the chord length).  Scatter images
+(eq. Is) are compared two ways: with the same seed, where GPU and oracle run
+the same histories on the same Philox4x32-10 streams and must agree nearly
+history for history; and with independent seeds, where they must agree within
+3 sigma of the combined Monte Carlo noise in >= 99% of pixels.
+"""
+
+import numpy as np
+import pytest
+
+from mc_inputs import ellipsoid_phantom, kramers_spectrum, make_workload, mono_spectrum
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(gpu, table_path, wl, **opt):
+    c = gpu.Context(0, **opt)
+    c.load_tables(table_path)
+    c.setup(wl)
+    return c
+
+
+def _orc(oracle_lib, table_path, wl, **opt):
+    o = oracle_lib.Oracle(table_path)
+    o.setup(wl)
+    if opt:
+        o.set_options(**opt)
+    return o
+
+
+def _small_poly_workload(tables, n=64, dv=2.0, nu=96, nv=80):
+    vol = ellipsoid_phantom(n=n, dv=dv, seed=3)
+    E, w = kramers_spectrum(tables)
+    return dict(
+        volume=vol, energies=E, weights=w,
+        geometry=dict(sod=300.0, sdd=600.0, nu=nu, nv=nv, pu=2.7, pv=3.1),
+        n_photons=200_000, step_mm=0.8, seed=5, angles=np.array([0.0], np.float32),
+    )
+
+
+def _check_primary(gpu_img, orc_img, bound):
+    rel = np.abs(gpu_img.astype(np.float64) / orc_img - 1.0)
+    fin = np.isfinite(bound)
+    assert np.all(rel[fin] <= 1e-5 + bound[fin]), (rel[fin] - bound[fin]).max()
+    assert np.all(rel[~fin] <= 1e-2)
+    strict = np.mean(rel <= 1e-5)
+    assert strict >= 0.99, strict
+    return strict
+
+
+@pytest.mark.parametrize("angle", [0.0, 0.7, 2.1])
+def test_primary_parity_cylinder(gpu, oracle_lib, table_path, tables, angle):
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl)
+    out = c.project([angle], 1000, wl["step_mm"], 1, scatter=False)
+    Ip, bound = _orc(oracle_lib, table_path, wl).primary(angle, wl["step_mm"])
+    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound)
+
+
+def test_primary_parity_polyenergetic_ragged(gpu, oracle_lib, table_path, tables):
+    wl = _small_poly_workload(tables)
+    c = _ctx(gpu, table_path, wl)
+    angles = np.array([0.3, 4.0], np.float32)
+    out = c.project(angles, 1000, wl["step_mm"], 1, scatter=False)
+    o = _orc(oracle_lib, table_path, wl)
+    for k, a in enumerate(angles):
+        Ip, bound = o.primary(float(a), wl["step_mm"])
+        _check_primary(out["primary"][k].cpu().numpy(), Ip, bound)
+
+
+def test_scatter_same_seed_cylinder(gpu, oracle_lib, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    N = 200_000
+    c = _ctx(gpu, table_path, wl)
+    g = c.project([0.4], N, wl["step_mm"], 9, primary=False)["scatter"][0].cpu().numpy().astype(np.float64)
+    st = c.last_stats()
+    r = _orc(oracle_lib, table_path, wl).scatter(0.4, N, wl["step_mm"], 9)
+    ref = r["Is"]
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert rel < 2e-3, rel
+    # the same histories ran: interaction and step counts agree closely
+    for k in ("compton", "rayleigh", "photo", "nee_rays"):
+        assert abs(st[k] / r["stats"][k] - 1.0) < 1e-3, k
+    assert abs((st["flight_steps"] + st["nee_steps"]) / (r["stats"]["flight_steps"] + r["stats"]["nee_steps"]) - 1) < 1e-3
+
+
+@pytest.mark.parametrize("h0", [0, 37_000_000, 99_990_000])
+def test_scatter_history_subrange_full_size(gpu, oracle_lib, table_path, tables, h0):
+    """Full-size polyenergetic workload (256^3, 512^2, 1e8 photons): histories
+    sampled from across the run match the oracle history for history."""
+    wl = make_workload("ell256", tables)
+    N, cnt = wl["n_photons"], 4000
+    c = _ctx(gpu, table_path, wl)
+    g = c.project_histories([0.0], N, h0, cnt, wl["step_mm"], wl["seed"])[0].cpu().numpy().astype(np.float64)
+    r = _orc(oracle_lib, table_path, wl).scatter(0.0, N, wl["step_mm"], wl["seed"], h_begin=h0, h_end=h0 + cnt)
+    ref = r["Is"]
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert rel < 1e-2, rel
+
+
+def test_scatter_independent_seeds_statistical(gpu, oracle_lib, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    N, B = 1_000_000, 20
+    c = _ctx(gpu, table_path, wl, n_batches=B)
+    out = c.project([0.0], N, wl["step_mm"], 21, primary=False, variance=True)
+    g = out["scatter"][0].cpu().numpy().astype(np.float64)
+    gv = out["variance"][0].cpu().numpy().astype(np.float64)
+    o = _orc(oracle_lib, table_path, wl)
+    parts = np.array([o.scatter(0.0, N, wl["step_mm"], 22, h_begin=b * N // B, h_end=(b + 1) * N // B)["Is"]
+                      for b in range(B)])
+    ref = parts.sum(0)
+    rv = parts.var(axis=0, ddof=1) * B
+    nz = ref > 0
+    z = np.abs(g - ref)[nz] / np.sqrt(gv[nz] + rv[nz])
+    assert np.mean(z < 3.0) >= 0.99, np.mean(z < 3.0)
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    noise = np.sqrt(np.sum(gv + rv)) / np.linalg.norm(ref)
+    assert rel < 1.5 * noise + 1e-3, (rel, noise)
+
+
+def test_multi_angle_launch_equals_single_angle_launches(gpu, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl)
+    angles = np.array([0.0, 1.0, 2.5], np.float32)
+    both = c.project(angles, 50_000, wl["step_mm"], 4)
+    for k, a in enumerate(angles):
+        one = c.project_histories(angles, 50_000, 0, 50_000, wl["step_mm"], 4)
+        np.testing.assert_allclose(one[k].cpu().numpy(), both["scatter"][k].cpu().numpy(), rtol=1e-5, atol=1e-12)
+    # angle index keys the random streams: different angles are independent
+    assert not np.allclose(both["scatter"][0].cpu().numpy(), both["scatter"][1].cpu().numpy())
+
+
+def test_deterministic_up_to_fp64_sum_order(gpu, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl)
+    a = c.project([0.2], 100_000, wl["step_mm"], 3)["scatter"].cpu().numpy()
+    b = c.project([0.2], 100_000, wl["step_mm"], 3)["scatter"].cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=0)
+
+
+def test_scatter_order_cap_matches_oracle(gpu, oracle_lib, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl, max_scatter_order=1)
+    out = c.project([0.0], 100_000, wl["step_mm"], 5, primary=False, allow_limit=True)
+    st = c.last_stats()
+    assert st["limit"] > 0
+    o = _orc(oracle_lib, table_path, wl, max_order=1)
+    ref = o.scatter(0.0, 100_000, wl["step_mm"], 5)["Is"]
+    g = out["scatter"][0].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 2e-3
+
+
+def test_russian_roulette_same_seed(gpu, oracle_lib, table_path, tables):
+    wl = make_workload("cyl64", tables)
+    thr = 2e-9
+    c = _ctx(gpu, table_path, wl, rr_threshold=thr, n_split=5)
+    g = c.project([0.0], 100_000, wl["step_mm"], 8, primary=False)["scatter"][0].cpu().numpy().astype(np.float64)
+    o = _orc(oracle_lib, table_path, wl, n_split=5, rr_threshold=thr)
+    r = o.scatter(0.0, 100_000, wl["step_mm"], 8)
+    assert r["stats"]["rr_killed"] > 0
+    assert np.linalg.norm(g - r["Is"]) / np.linalg.norm(r["Is"]) < 5e-3
+
+
+def test_edge_cases(gpu, oracle_lib, table_path, tables):
+    wl = make_workload("tiny8", tables)
+    c = _ctx(gpu, table_path, wl)
+    # a single photon, and an empty history range
+    one = c.project([0.0], 1, 0.5, 1)["scatter"].cpu().numpy()
+    ref = _orc(oracle_lib, table_path, wl).scatter(0.0, 1, 0.5, 1)["Is"]
+    np.testing.assert_allclose(one[0], ref, rtol=1e-4, atol=1e-12)
+    empty = c.project_histories([0.0], 1000, 500, 0, 0.5, 1)
+    assert float(empty.abs().sum()) == 0.0
+    # a 1 x 1 detector and a step longer than the volume
+    wl2 = dict(wl, geometry=dict(wl["geometry"], nu=1, nv=1))
+    c2 = _ctx(gpu, table_path, wl2)
+    o2 = _orc(oracle_lib, table_path, wl2)
+    g = c2.project([0.0], 20_000, 100.0, 2)
+    ref2 = o2.scatter(0.0, 20_000, 100.0, 2)["Is"]
+    assert abs(float(g["scatter"][0, 0, 0]) / ref2[0, 0] - 1.0) < 2e-3
+    Ip, _ = o2.primary(0.0, 100.0)
+    assert abs(float(g["primary"][0, 0, 0]) / Ip[0, 0] - 1.0) < 1e-5
+
+
+def test_errors(gpu, table_path, tables):
+    c = gpu.Context(0)
+    with pytest.raises(gpu.MCError, match="STATE"):
+        c.project([0.0], 10, 0.5, 1)
+    with pytest.raises(gpu.MCError, match="IO"):
+        c.load_tables("/nonexistent/tables.bin")
+    c.load_tables(table_path)
+    wl = make_workload("cyl64", tables)
+    c.setup(wl)
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.project([0.0], 10, 0.0, 1)
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.project([0.0], 10, 0.5, 1, variance=True)  # needs n_batches >= 2
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.set_geometry(50.0, 100.0, 8, 8, 1.0, 1.0)
+        c.project([0.0], 10, 0.5, 1)  # volume not between source and panel
+    bad = dict(wl["volume"])
+    bad["mat"] = bad["mat"].copy()
+    bad["mat"][0, 0, 0] = 200
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.load_volume(bad["mat"], bad["rho"], bad["spacing"])
+    torch = pytest.importorskip("torch")
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.load_volume(torch.from_numpy(bad["mat"]).cuda(), torch.from_numpy(bad["rho"].view(np.int16)).cuda(),
+                      bad["spacing"])
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.set_spectrum(np.array([500.0], np.float32), np.array([1.0]))  # outside the table
+
+
+def test_device_volume_load_matches_host(gpu, table_path, tables):
+    torch = pytest.importorskip("torch")
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl)
+    a = c.project([0.1], 20_000, 0.5, 3)
+    v = wl["volume"]
+    c.load_volume(torch.from_numpy(v["mat"]).cuda(), torch.from_numpy(v["rho"].view(np.int16)).cuda(), v["spacing"])
+    b = c.project([0.1], 20_000, 0.5, 3)
+    np.testing.assert_array_equal(a["primary"].cpu().numpy(), b["primary"].cpu().numpy())
+    np.testing.assert_allclose(a["scatter"].cpu().numpy(), b["scatter"].cpu().numpy(), rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# smoothing and dual interpolation (Sec. II-C.3, II-C.4)
+def test_smooth_upsample_parity(gpu):
+    from oracle import post
+
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    n_in, nv, nu = 5, 40, 48
+    imgs = rng.normal(1.0, 0.1, size=(n_in, nv, nu))
+    ia = np.sort(rng.uniform(0, 2 * np.pi, n_in)).astype(np.float32)
+    oa = rng.uniform(-1, 7, 7).astype(np.float32)
+    c = gpu.Context(0)
+    out = c.smooth_upsample(torch.tensor(imgs, dtype=torch.float32, device="cuda"), ia, oa, 120, 96)
+    ref = post.smooth_upsample(imgs.astype(np.float32), ia, oa, 120, 96, win=9, order=3, a=-0.5)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=2e-5, atol=2e-5)
+
+
+def test_upsample_only_a075_matches_torch(gpu):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    img = torch.tensor(rng.normal(size=(1, 33, 47)), dtype=torch.float32, device="cuda")
+    c = gpu.Context(0, cubic_a=-0.75, denoise_mode=2)
+    out = c.smooth_upsample(img, [0.0], [0.0], 101, 67)
+    ref = torch.nn.functional.interpolate(img[None], size=(67, 101), mode="bicubic", align_corners=False)[0]
+    np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), atol=2e-5)
+
+
+def test_smoothing_windows_and_edges(gpu):
+    from oracle import post
+
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    img = rng.normal(size=(2, 31, 37))
+    for win, order in ((5, 3), (11, 3), (7, 2)):
+        c = gpu.Context(0, sg_window=win, sg_order=order)
+        out = c.smooth_upsample(torch.tensor(img, dtype=torch.float32, device="cuda"), [0.0, 3.0], [0.0, 3.0], 37, 31)
+        for k in range(2):
+            np.testing.assert_allclose(out[k].cpu().numpy(), post.sg_smooth_2d(img[k], win, order), atol=3e-5)
