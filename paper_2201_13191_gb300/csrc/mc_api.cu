@@ -641,6 +641,8 @@ int mc_set_geometry(mc_ctx* ctx, float sod, float sdd, int nu, int nv, float pu,
 int mc_project(mc_ctx* ctx, const float* angles, int n_angles, uint64_t n_photons, float step_mm, uint64_t seed,
                float* primary_out, float* scatter_out, float* scatter_var_out, void* stream) {
   if (!ctx) return MC_ERR_INVALID_ARG;
+  const int rc = check_ready(ctx);
+  if (rc) return rc;
   if (!primary_out && !scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "no output requested");
   if (scatter_var_out && !scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "variance needs scatter_out");
   return project_impl(ctx, angles, n_angles, n_photons, 0, n_photons, step_mm, seed, primary_out, scatter_out,
@@ -650,6 +652,8 @@ int mc_project(mc_ctx* ctx, const float* angles, int n_angles, uint64_t n_photon
 int mc_project_histories(mc_ctx* ctx, const float* angles, int n_angles, uint64_t n_photons, uint64_t h_begin,
                          uint64_t h_count, float step_mm, uint64_t seed, float* scatter_out, void* stream) {
   if (!ctx) return MC_ERR_INVALID_ARG;
+  const int rc = check_ready(ctx);
+  if (rc) return rc;
   if (!scatter_out) return fail(ctx, MC_ERR_INVALID_ARG, "scatter_out is required");
   return project_impl(ctx, angles, n_angles, n_photons, h_begin, h_count, step_mm, seed, nullptr, scatter_out,
                       nullptr, stream);
