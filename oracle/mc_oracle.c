@@ -470,14 +470,15 @@ static size_t voxel_of(const orc_ctx *c, const double p[3], int ijk[3]) {
  * largest possible change of rho*mu_rho*h at energy Eb (an ambiguity bound for
  * FP32 re-evaluation); sets *namb if L/step is within 1e-5 of an integer.
  * Returns the number of steps. */
-static long march_rhoL(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
-                       double *rhoL, double *bound, double Eb, int *namb) {
+static long march_rhoL_n(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
+                         double *rhoL, double *bound, double Eb, int *namb, long n_force) {
   double ta, tb;
   if (!clip_box(c, p0, w, t0, t1, &ta, &tb)) return 0;
   double L = tb - ta;
   double q = L / step;
   long n = (long)ceil(q);
   if (n < 1) n = 1;
+  if (n_force > 0) n = n_force;
   if (namb) {
     double fr = q - floor(q + 0.5);
     if (fabs(fr) < 1e-5 * (q > 1 ? q : 1)) *namb = 1;
@@ -516,6 +517,11 @@ static long march_rhoL(const orc_ctx *c, const double p0[3], const double w[3], 
   return n;
 }
 
+static long march_rhoL(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
+                       double *rhoL, double *bound, double Eb, int *namb) {
+  return march_rhoL_n(c, p0, w, t0, t1, step, rhoL, bound, Eb, namb, 0);
+}
+
 /* Optical depth tau at energy E along the march (mm^-1 * mm). */
 static double march_tau(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
                         double E, long *nsteps) {
@@ -548,14 +554,32 @@ int orc_march(const orc_ctx *c, const double p0[3], const double w[3], double t0
 }
 
 /* ------------------------------------------------------------------ */
+/* Spectrum sum of eq. (Ip) for per-material column masses rhoL; also the
+ * transmitted-energy-weighted mean optical depth. */
+static double primary_sum(const orc_ctx *c, const double *rhoL, double *tau_mean) {
+  double sum = 0, wtau = 0;
+  for (int n = 0; n < c->n_bins; ++n) {
+    if (c->S[n] == 0) continue;
+    double tau = 0;
+    for (int m = 0; m < c->n_mat; ++m)
+      if (rhoL[m] != 0) tau += mu_rho_tot(c, m, c->Ebin[n]) * 0.1 * rhoL[m];
+    double e = c->S[n] * c->Ebin[n] * exp(-tau);
+    sum += e;
+    wtau += e * tau;
+  }
+  if (tau_mean) *tau_mean = sum > 0 ? wtau / sum : 0;
+  return sum;
+}
+
 /* Primary image, eq. (Ip), one angle.  Ip[j*nu + i] in keV per pixel per source
- * photon into 4 pi.  bound[] (nullable) is the relative change of Ip that a
- * re-evaluation in FP32 may legitimately produce: midpoints within eps_face of
- * a face between different voxels may fall on either side (their largest
- * optical-depth change, weighted over the spectrum), and the chord length
- * itself carries an FP32 rounding of a few units in the last place of the
- * larger ray parameter; INFINITY when the step count ceil(L/step) itself is
- * ambiguous. */
+ * photon into 4 pi.  bound[] (nullable) is, as an optical depth, what a
+ * re-evaluation in FP32 may legitimately change: midpoints within eps_face of
+ * a face between different voxels may fall on either side (largest optical
+ * depth change at the lowest spectrum energy); the chord length carries an FP32
+ * rounding of a few units in the last place of the larger ray parameter; and
+ * where ceil(L/step) itself is within rounding of an integer, either
+ * neighbouring step count is a valid evaluation (largest |ln| ratio of the
+ * images they give). */
 int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *bound) {
   if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
   if (!(step > 0)) return ORC_EINVAL;
@@ -564,7 +588,6 @@ int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *
   double Emin = 1e30;
   for (int n = 0; n < c->n_bins; ++n)
     if (c->S[n] > 0 && c->Ebin[n] < Emin) Emin = c->Ebin[n];
-  double *tau_n = malloc(c->n_bins * 8);
   for (int j = 0; j < c->nv; ++j) {
     for (int i = 0; i < c->nu; ++i) {
       double X[3];
@@ -573,35 +596,33 @@ int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *
       double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
       double w[3] = {D[0] / d, D[1] / d, D[2] / d};
       double rhoL[ORC_MAXMAT] = {0};
-      double b = 0;
+      double b = 0, tau_mean = 0;
       int namb = 0;
-      march_rhoL(c, P.s, w, 0.0, d, step, rhoL, &b, Emin, &namb);
-      double sum = 0, wt = 0, wtau = 0;
-      for (int n = 0; n < c->n_bins; ++n) {
-        tau_n[n] = 0;
-        if (c->S[n] == 0) continue;
-        double tau = 0;
-        for (int m = 0; m < c->n_mat; ++m)
-          if (rhoL[m] != 0) tau += mu_rho_tot(c, m, c->Ebin[n]) * 0.1 * rhoL[m];
-        double e = c->S[n] * c->Ebin[n] * exp(-tau);
-        sum += e;
-        wt += e;
-        wtau += e * tau;
-      }
+      long n = march_rhoL(c, P.s, w, 0.0, d, step, rhoL, &b, Emin, &namb);
+      double sum = primary_sum(c, rhoL, &tau_mean);
       double cosg = c->sdd / d;
       Ip[(size_t)j * c->nu + i] = sum * c->pu * c->pv * cosg / (4.0 * PI * d * d);
       if (bound) {
-        double ta, tb, chord = 0;
+        double ta, tb, extra = 0;
         if (clip_box(c, P.s, w, 0.0, d, &ta, &tb)) {
           double L = tb - ta, tmax = fmax(fabs(ta), fabs(tb));
           /* four FP32 units in the last place of the larger parameter */
-          chord = (wt > 0 ? wtau / wt : 0) * 4.0 * ldexp(1.0, ilogb(tmax) - 23) / L;
+          extra = tau_mean * 4.0 * ldexp(1.0, ilogb(tmax) - 23) / L;
         }
-        bound[(size_t)j * c->nu + i] = namb ? INFINITY : b + chord;
+        if (namb) {
+          for (long dn = -1; dn <= 1; dn += 2) {
+            if (n + dn < 1) continue;
+            double r2[ORC_MAXMAT] = {0}, b2 = 0;
+            march_rhoL_n(c, P.s, w, 0.0, d, step, r2, &b2, Emin, NULL, n + dn);
+            double s2 = primary_sum(c, r2, NULL);
+            double lr = fabs(log(s2 / sum)) + b2;
+            if (lr > extra) extra = lr;
+          }
+        }
+        bound[(size_t)j * c->nu + i] = b + extra;
       }
     }
   }
-  free(tau_n);
   return ORC_OK;
 }
 

@@ -182,24 +182,109 @@ __device__ __forceinline__ float3 rotate(float3 w, float ct, float phi) {
   return make_float3(o.x * in, o.y * in, o.z * in);
 }
 
-__global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
+// Interaction records queued by the flight phase for the pseudo-particle
+// phase, one slot per thread of the block (structure of arrays).
+struct Records {
+  float *X, *Y, *Z, *wx, *wy, *wz, *E, *W, *norm, *cb, *sb;
+  int* tm;  // type << 8 | material
+  uint32_t *hlo, *hhi, *ang, *k0;
+};
+
+// One pseudo-particle (eq. Th): random pixel and point in it from the counter
+// block k0 + s of the record's stream, scatter-toward-detector pdf, optional
+// Russian roulette, attenuation march to the panel, FP64 tally.
+__device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
+                                                int r, int s, float* my_mu, int stride, float nee_scale,
+                                                uint32_t npix, size_t img, Counters& C) {
+  const VolumeView& V = P.vol;
+  const GeomView& G = P.geo;
+  const uint32_t hlo = R.hlo[r], hhi = R.hhi[r], a = R.ang[r];
+  const uint4 blk = philox4x32_10(make_uint4(R.k0[r] + (uint32_t)s, a, hlo, hhi),
+                                  make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+  const float va = Rng::u01(blk.y), vb = Rng::u01(blk.z), vr = Rng::u01(blk.w);
+  const uint32_t pix = __umulhi(blk.x, npix);
+  const uint32_t pi = pix % (uint32_t)G.nu, pj = pix / (uint32_t)G.nu;
+  const float cb = R.cb[r], sb = R.sb[r];
+  Pose ps;
+  const float rr0 = G.sod - G.sdd;
+  ps.c = make_float3(rr0 * cb, rr0 * sb, 0.f);
+  ps.eu = make_float3(-sb, cb, 0.f);
+  ps.n = make_float3(cb, sb, 0.f);
+  const float3 x = make_float3(R.X[r], R.Y[r], R.Z[r]);
+  const float3 w = make_float3(R.wx[r], R.wy[r], R.wz[r]);
+  const float3 Pp = det_point(G, ps, (float)pi + va, (float)pj + vb);
+  const float3 DD = sub3(Pp, x);
+  const float dd2 = dot3(DD, DD);
+  const float idd = rsqrtf(dd2);
+  const float3 dir = make_float3(DD.x * idd, DD.y * idd, DD.z * idd);
+  const float lam = dot3(w, dir);
+  const float cosg = -dot3(dir, ps.n);
+  const int tm = R.tm[r];
+  const int type = tm >> 8, mint = tm & 255;
+  const float E = R.E[r];
+  float Ep, p;
+  if (type == 1) {
+    const float ratio = 1.f / fmaf(E / T.mec2, 1.f - lam, 1.f);
+    Ep = E * ratio;
+    p = ratio * ratio * (ratio + 1.f / ratio - 1.f + lam * lam) * R.norm[r];
+  } else {
+    Ep = E;
+    const float K = (E * T.inv_hc) * (E * T.inv_hc);
+    const float u = 0.5f * K * (1.f - lam);
+    float F2 = 0.f;
+    const int nc = T.ncomp[mint];
+    const float2* cp = T.comp + mint * kMaxComp;
+    for (int i = 0; i < nc; ++i) {
+      const float q = fmaf(cp[i].y, u, 1.f);
+      const float q2 = q * q;
+      F2 += cp[i].x / (q2 * q2);
+    }
+    p = (1.f + lam * lam) * F2 * R.norm[r];
+  }
+  float x0 = R.W[r] * Ep * p * cosg * nee_scale / dd2;
+  ++C.nee_rays;
+  if (P.rr_threshold > 0.f && x0 < P.rr_threshold) {
+    if (vr >= x0 / P.rr_threshold) return;
+    x0 = P.rr_threshold;
+  }
+  fill_mu(T, Ep, my_mu, stride);
+  const float tp = march_tau(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
+  const unsigned long long h = ((unsigned long long)hhi << 32) | hlo;
+  const int b = P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0;
+  atomicAdd(P.tally + ((size_t)b * P.n_angles + a) * img + pix, (double)(x0 * __expf(-tp)));
+}
+
+__global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
+  __shared__ int s_nrec;
   const int nm = P.tab.n_mat, ns = P.tab.n_stage;
-  // shared layout: [table blob][prefix u64 (n_bins+1)][energy f32][wbin f32][mu columns f32 nm x blockDim]
+  const int nb = P.spec.n_bins;
+  const int B = blockDim.x;
+  // shared layout: [table blob][prefix u64 (nb+1)][energy f32 nb][wbin f32 nb]
+  //                [mu columns f32 kMaxMat x B][records 16 x B words]
   float2* s_blob = reinterpret_cast<float2*>(smem);
   unsigned long long* s_pre = reinterpret_cast<unsigned long long*>(smem + P.tab.blob_bytes);
-  const int nb = P.spec.n_bins;
   float* s_E = reinterpret_cast<float*>(s_pre + nb + 1);
   float* s_wb = s_E + nb;
   float* s_mu = s_wb + nb;
+  float* rec = s_mu + kMaxMat * B;
+  Records R;
+  R.X = rec; R.Y = rec + B; R.Z = rec + 2 * B; R.wx = rec + 3 * B; R.wy = rec + 4 * B; R.wz = rec + 5 * B;
+  R.E = rec + 6 * B; R.W = rec + 7 * B; R.norm = rec + 8 * B; R.cb = rec + 9 * B; R.sb = rec + 10 * B;
+  R.tm = reinterpret_cast<int*>(rec + 11 * B);
+  R.hlo = reinterpret_cast<uint32_t*>(rec + 12 * B);
+  R.hhi = reinterpret_cast<uint32_t*>(rec + 13 * B);
+  R.ang = reinterpret_cast<uint32_t*>(rec + 14 * B);
+  R.k0 = reinterpret_cast<uint32_t*>(rec + 15 * B);
 
   const bool staged = stage_bulk(s_blob, P.tab.blob, P.tab.blob_bytes, &bar);
-  for (int i = threadIdx.x; i <= nb; i += blockDim.x) s_pre[i] = P.spec.prefix[i];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+  for (int i = threadIdx.x; i <= nb; i += B) s_pre[i] = P.spec.prefix[i];
+  for (int i = threadIdx.x; i < nb; i += B) {
     s_E[i] = P.spec.energy[i];
     s_wb[i] = P.spec.wbin[i];
   }
+  if (threadIdx.x == 0) s_nrec = 0;
   __syncthreads();
   if (!staged) {
     if (threadIdx.x == 0) atomicAdd(P.stats + S_INTERNAL, 1ull);
@@ -219,67 +304,77 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
 
   const VolumeView& V = P.vol;
   const GeomView& G = P.geo;
-  const int stride = blockDim.x;
   float* my_mu = s_mu + threadIdx.x;
   const uint32_t npix = (uint32_t)G.nu * (uint32_t)G.nv;
   const float A_det = (float)G.nu * G.pu * (float)G.nv * G.pv;
-  const float A_px = G.pu * G.pv;
-  const float nee_scale = A_px * ((float)npix / (float)P.n_split) / (2.f * kPi);
+  const float nee_scale = G.pu * G.pv * ((float)npix / (float)P.n_split) / (2.f * kPi);
   const size_t img = (size_t)npix;
+  const int n_split = P.n_split;
 
   Counters C = {};
   const unsigned long long total = (unsigned long long)P.n_angles * P.h_count;
-  for (unsigned long long w_i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w_i < total;
-       w_i += (unsigned long long)gridDim.x * blockDim.x) {
-    const int a = (int)(w_i / P.h_count);
-    const unsigned long long h = P.h_begin + (w_i - (unsigned long long)a * P.h_count);
-    // energy bin by the stratified prefix sums
-    int lo = 0, hi = nb - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_pre[mid] <= h) lo = mid;
-      else hi = mid - 1;
+  const unsigned long long stride = (unsigned long long)gridDim.x * B;
+  unsigned long long next = (unsigned long long)blockIdx.x * B + threadIdx.x;
+
+  // photon state
+  bool alive = false;
+  unsigned long long h = 0;
+  int a = 0, order = 0;
+  float3 x = make_float3(0.f, 0.f, 0.f), w = x;
+  float E = 0.f, W = 0.f, cb = 1.f, sb = 0.f;
+  Rng g;
+  g.init(0, 0, P.seed);
+
+  for (;;) {
+    // ---- flight phase: one free flight per live photon
+    if (!alive && next < total) {
+      a = (int)(next / P.h_count);
+      h = P.h_begin + (next - (unsigned long long)a * P.h_count);
+      next += stride;
+      int lo = 0, hi = nb - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= h) lo = mid;
+        else hi = mid - 1;
+      }
+      E = s_E[lo];
+      g.init(h, (uint32_t)a, P.seed);
+      sincosf(__ldg(P.angles + a), &sb, &cb);
+      const Pose ps = make_pose(G, __ldg(P.angles + a));
+      const float ua = g.u(), ub = g.u();
+      const float3 Q = det_point(G, ps, ua * (float)G.nu, ub * (float)G.nv);
+      const float3 D = sub3(Q, ps.s);
+      const float d = sqrtf(dot3(D, D));
+      w = make_float3(D.x / d, D.y / d, D.z / d);
+      W = s_wb[lo] * A_det * (G.sdd / d) / (4.f * kPi * d * d);
+      x = ps.s;
+      order = 0;
+      alive = true;
+      ++C.hist;
     }
-    const int bin = lo;
-    float E = s_E[bin];
-    Rng g;
-    g.init(h, (uint32_t)a, P.seed);
-    const Pose ps = make_pose(G, __ldg(P.angles + a));
-    double* tally = P.tally + ((size_t)(P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0) *
-                                   P.n_angles + a) * img;
-    // source: uniform point on the panel, solid-angle Jacobian weight
-    const float ua = g.u(), ub = g.u();
-    const float3 Q = det_point(G, ps, ua * (float)G.nu, ub * (float)G.nv);
-    float3 D = sub3(Q, ps.s);
-    float d = sqrtf(dot3(D, D));
-    float3 w = make_float3(D.x / d, D.y / d, D.z / d);
-    const float W = s_wb[bin] * A_det * (G.sdd / d) / (4.f * kPi * d * d);
-    float3 x = ps.s;
-    int order = 0;
-    ++C.hist;
-    for (;;) {
+    if (alive) {
       const float tau_star = -logf(g.u());
       float ta, tb;
       bool hit = false;
       float tint = 0.f;
       int mint = 0;
       if (clip_box(V, x, w, 0.f, __int_as_float(0x7f800000), ta, tb)) {
-        fill_mu(T, E, my_mu, stride);
+        fill_mu(T, E, my_mu, B);
         const float L = tb - ta;
         const int n = step_count(L, P.step);
         const float hh = L / (float)n;
-        VoxRay r;
-        r.set(V, x, w);
+        VoxRay vr;
+        vr.set(V, x, w);
         float tau = 0.f, mu_m = 0.f;
         int cur = -1, k = 0;
         for (; k < n; ++k) {
           const float t = fmaf((float)k + 0.5f, hh, ta);
-          const int v = r.voxel(V, t);
+          const int v = vr.voxel(V, t);
           const int m = __ldg(V.mat + v);
           const float rho = __half2float(__ldg(V.rho + v));
           if (m != cur) {
             cur = m;
-            mu_m = my_mu[m * stride];
+            mu_m = my_mu[m * B];
           }
           const float mu = mu_m * rho;
           if (fmaf(mu, hh, tau) >= tau_star) {
@@ -294,93 +389,69 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
       }
       if (!hit) {
         ++C.escape;
-        break;
-      }
-      x = make_float3(fmaf(tint, w.x, x.x), fmaf(tint, w.y, x.y), fmaf(tint, w.z, x.z));
-      // interaction type
-      int ti;
-      float tf;
-      T.locate(E, ti, tf);
-      const float pe = T.at(TAB_PE, mint, ti, tf), in = T.at(TAB_IN, mint, ti, tf),
-                  co = T.at(TAB_CO, mint, ti, tf);
-      const float ut = g.u() * (pe + in + co);
-      const int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
-      if (type == 0) {
-        ++C.photo;
-        break;
-      }
-      if (type == 1) ++C.compton;
-      else ++C.rayleigh;
-      // point-detector scoring split into n_split pseudo-particles (eq. Th)
-      const float alpha = E / T.mec2;
-      const float norm = type == 1 ? 1.f / T.kn_norm(ti, tf) : 1.f / T.at(TAB_ICOH, mint, ti, tf);
-      const float K = (E * T.inv_hc) * (E * T.inv_hc);
-      g.align();
-      for (int s = 0; s < P.n_split; ++s) {
-        g.refill();
-        const uint32_t rpix = g.buf.x;
-        const float va = Rng::u01(g.buf.y), vb = Rng::u01(g.buf.z), vr = Rng::u01(g.buf.w);
-        g.idx = 4;
-        const uint32_t pix = __umulhi(rpix, npix);
-        const uint32_t pi = pix % (uint32_t)G.nu, pj = pix / (uint32_t)G.nu;
-        const float3 Pp = det_point(G, ps, (float)pi + va, (float)pj + vb);
-        const float3 DD = sub3(Pp, x);
-        const float dd2 = dot3(DD, DD);
-        const float idd = rsqrtf(dd2);
-        const float3 dir = make_float3(DD.x * idd, DD.y * idd, DD.z * idd);
-        const float lam = dot3(w, dir);
-        const float cosg = -dot3(dir, ps.n);
-        float Ep, p;
-        if (type == 1) {
-          const float ratio = 1.f / fmaf(alpha, 1.f - lam, 1.f);
-          Ep = E * ratio;
-          p = ratio * ratio * (ratio + 1.f / ratio - 1.f + lam * lam) * norm;
-        } else {
-          Ep = E;
-          const float u = 0.5f * K * (1.f - lam);
-          float F2 = 0.f;
-          const int nc = T.ncomp[mint];
-          const float2* cp = T.comp + mint * kMaxComp;
-          for (int i = 0; i < nc; ++i) {
-            const float q = fmaf(cp[i].y, u, 1.f);
-            const float q2 = q * q;
-            F2 += cp[i].x / (q2 * q2);
-          }
-          p = (1.f + lam * lam) * F2 * norm;
-        }
-        float x0 = W * Ep * p * cosg * nee_scale / dd2;
-        ++C.nee_rays;
-        if (P.rr_threshold > 0.f && x0 < P.rr_threshold) {
-          if (vr >= x0 / P.rr_threshold) continue;
-          x0 = P.rr_threshold;
-        }
-        // Rayleigh keeps the energy, so the flight's column is still valid.
-        if (type == 1) fill_mu(T, Ep, my_mu, stride);
-        const float tp = march_tau(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
-        const float sc = x0 * __expf(-tp);
-        atomicAdd(tally + pix, (double)sc);
-      }
-      // new direction
-      bool fail = false;
-      float ct, Enew = E;
-      if (type == 1) {
-        const float r = kahn(g, alpha, fail);
-        ct = 1.f - (r - 1.f) / alpha;
-        Enew = E / r;
+        alive = false;
       } else {
-        ct = rayleigh(g, T, mint, E, fail);
-      }
-      const float phi = 2.f * kPi * g.u();
-      if (fail) ++C.fail;
-      w = rotate(w, ct, phi);
-      E = Enew;
-      ++order;
-      if (E < 1.f) break;
-      if (order >= P.max_order) {
-        ++C.limit;
-        break;
+        x = make_float3(fmaf(tint, w.x, x.x), fmaf(tint, w.y, x.y), fmaf(tint, w.z, x.z));
+        int ti;
+        float tf;
+        T.locate(E, ti, tf);
+        const float pe = T.at(TAB_PE, mint, ti, tf), in = T.at(TAB_IN, mint, ti, tf),
+                    co = T.at(TAB_CO, mint, ti, tf);
+        const float ut = g.u() * (pe + in + co);
+        const int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
+        if (type == 0) {
+          ++C.photo;
+          alive = false;
+        } else {
+          if (type == 1) ++C.compton;
+          else ++C.rayleigh;
+          // queue the interaction; its pseudo-particles use the next n_split counter blocks
+          g.align();
+          const int r = atomicAdd(&s_nrec, 1);
+          R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
+          R.wx[r] = w.x; R.wy[r] = w.y; R.wz[r] = w.z;
+          R.E[r] = E; R.W[r] = W; R.cb[r] = cb; R.sb[r] = sb;
+          R.norm[r] = type == 1 ? 1.f / T.kn_norm(ti, tf) : 1.f / T.at(TAB_ICOH, mint, ti, tf);
+          R.tm[r] = (type << 8) | mint;
+          R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
+          R.k0[r] = g.ctr.x;
+          g.ctr.x += (uint32_t)n_split;
+          // new direction
+          bool fail = false;
+          float ct, Enew = E;
+          if (type == 1) {
+            const float alpha = E / T.mec2;
+            const float rk = kahn(g, alpha, fail);
+            ct = 1.f - (rk - 1.f) / alpha;
+            Enew = E / rk;
+          } else {
+            ct = rayleigh(g, T, mint, E, fail);
+          }
+          const float phi = 2.f * kPi * g.u();
+          if (fail) ++C.fail;
+          w = rotate(w, ct, phi);
+          E = Enew;
+          ++order;
+          if (E < 1.f) {
+            alive = false;
+          } else if (order >= P.max_order) {
+            ++C.limit;
+            alive = false;
+          }
+        }
       }
     }
+    __syncthreads();
+    // ---- pseudo-particle phase: the block marches every queued ray together
+    const int n_jobs = s_nrec * n_split;
+    for (int j = threadIdx.x; j < n_jobs; j += B) {
+      const int r = j / n_split;
+      pseudo_particle(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C);
+    }
+    const bool more = alive || next < total;
+    __syncthreads();
+    if (threadIdx.x == 0) s_nrec = 0;
+    if (!__syncthreads_or(more)) break;
   }
   // block-level counter reduction
   __shared__ unsigned long long red[S_NSTAT];
@@ -422,7 +493,7 @@ __global__ void k_finalize(const double* __restrict__ tally, int B, size_t n, fl
 }  // namespace
 
 int transport_smem_bytes(const TableView& t, int n_bins, int block) {
-  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4;
+  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 16 * block * 4;
 }
 
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
