@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--photons", type=float, default=None, help="override photons per step")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--voxel-layout", type=int, default=0, help="0 default, 1 linear, 2 4^3 bricks")
     return p.parse_args()
 
 
@@ -210,7 +211,7 @@ def run_ours(args):
     tp, wl = make_inputs(tdir, args.photons)
     N = wl["n_photons"]
     seed = wl["seed"] + 1000 * rank
-    ctx = mcx.Context(local)
+    ctx = mcx.Context(local, voxel_layout=args.voxel_layout)
     ctx.load_tables(tp)
     ctx.setup(wl)
     stream = torch.cuda.current_stream()

@@ -68,6 +68,7 @@ typedef struct mc_options {
   int sg_order;          /* Savitzky-Golay polynomial order, default 3 (Sec. II-C.4) */
   float cubic_a;         /* Keys cubic parameter of the spatial up-sampling, default -0.5 (Sec. II-C.3) */
   int denoise_mode;      /* 0 = Savitzky-Golay, 2 = none */
+  int voxel_layout;      /* device volume layout: 0 = default, 1 = x fastest, 2 = 4x4x4 bricks */
 } mc_options;
 
 /* Fill *opt with the defaults listed above. */

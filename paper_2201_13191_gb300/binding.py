@@ -55,6 +55,7 @@ class Options(C.Structure):
         ("sg_order", C.c_int),
         ("cubic_a", C.c_float),
         ("denoise_mode", C.c_int),
+        ("voxel_layout", C.c_int),
     ]
 
 

@@ -19,6 +19,7 @@ __device__ __forceinline__ unsigned long long fp16_fixed24(uint16_t b) {
   return e == 0 ? (unsigned long long)f : ((unsigned long long)(f | 1024u) << (e - 1));
 }
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
   extern __shared__ float s_mub[];  // [n_bins][n_mat]: 0.1 * mu/rho at each bin energy
   const int nm = P.tab.n_mat, nb = P.spec.n_bins, ns = P.tab.n_stage;
@@ -54,19 +55,24 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
     h = L / (float)n;
     VoxRay r;
     r.set(V, ps.s, w);
-    const uint16_t* rho = reinterpret_cast<const uint16_t*>(V.rho);
-    int cur = __ldg(V.mat + r.voxel(V, fmaf(0.5f, h, ta)));
-    unsigned long long run = 0ull;
+    uint32_t word = __ldg(V.vox + r.voxel<LAYOUT>(V, fmaf(0.5f, h, ta)));
+    int cur = vox_mat(word), vprev = -1;
+    unsigned long long run = 0ull, val = 0ull;
     for (int k = 0; k < n; ++k) {
-      const int v = r.voxel(V, fmaf((float)k + 0.5f, h, ta));
-      const int m = __ldg(V.mat + v);
-      if (m != cur) {
+      const int v = r.voxel<LAYOUT>(V, fmaf((float)k + 0.5f, h, ta));
+      if (v != vprev) {
+        vprev = v;
+        word = __ldg(V.vox + v);
+        val = fp16_fixed24((uint16_t)(word & 0xffffu));
+        const int m = vox_mat(word);
+        if (m != cur) {
 #pragma unroll
-        for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
-        cur = m;
-        run = 0ull;
+          for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+          cur = m;
+          run = 0ull;
+        }
       }
-      run += fp16_fixed24(__ldg(rho + v));
+      run += val;
     }
 #pragma unroll
     for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
@@ -95,11 +101,8 @@ cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s) {
   const int npix = p.geo.nu * p.geo.nv;
   dim3 grid((npix + block - 1) / block, p.n_angles);
   const int smem = p.spec.n_bins * p.tab.n_mat * 4;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_primary, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_primary<<<grid, block, smem, s>>>(p);
+  if (p.vol.layout == VOX_BRICK) k_primary<VOX_BRICK><<<grid, block, smem, s>>>(p);
+  else k_primary<VOX_LIN><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -119,6 +122,33 @@ __global__ void k_validate_volume(const uint8_t* __restrict__ mat, const uint16_
   if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 }  // namespace
+
+__global__ void k_pack_volume(const uint8_t* __restrict__ mat, const uint16_t* __restrict__ rho, int nx, int ny,
+                              int nz, int layout, int nbx, int nby, uint32_t* __restrict__ out) {
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % nx);
+    const size_t r = i / nx;
+    const int iy = (int)(r % ny), iz = (int)(r / ny);
+    VolumeView v;
+    v.nx = nx; v.ny = ny; v.nz = nz; v.nbx = nbx; v.nby = nby;
+    const int o = layout == VOX_BRICK ? vox_index<VOX_BRICK>(v, ix, iy, iz) : vox_index<VOX_LIN>(v, ix, iy, iz);
+    out[o] = (uint32_t)rho[i] | ((uint32_t)mat[i] << 16);
+  }
+}
+
+size_t packed_words(int nx, int ny, int nz, int layout) {
+  if (layout != VOX_BRICK) return (size_t)nx * ny * nz;
+  return (size_t)((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4) * 64;
+}
+
+cudaError_t pack_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, int layout, uint32_t* out,
+                        size_t out_words, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, out_words * 4, s);
+  if (e != cudaSuccess) return e;
+  k_pack_volume<<<1024, 256, 0, s>>>(mat, rho, nx, ny, nz, layout, (nx + 3) / 4, (ny + 3) / 4, out);
+  return cudaGetLastError();
+}
 
 cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size_t n, int n_mat, cudaStream_t s,
                                    int* bad_host) {

@@ -75,6 +75,7 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 
 // Optical depth of the fixed-step march x + t w, t in [0, t1] (Sec. II-C.2),
 // material attenuation from smu (this thread's column); counts steps.
+template <int LAYOUT>
 __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3 w, float t1, float step,
                                            const float* smu, int stride, unsigned long long& nsteps) {
   float ta, tb;
@@ -84,17 +85,20 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   const float h = L / (float)n;
   VoxRay r;
   r.set(V, x, w);
-  float acc = 0.f;
-  int cur = -1;
-  float mu = 0.f;
+  float acc = 0.f, mu = 0.f, rho = 0.f;
+  int cur = -1, vprev = -1;
   for (int k = 0; k < n; ++k) {
     const float t = fmaf((float)k + 0.5f, h, ta);
-    const int v = r.voxel(V, t);
-    const int m = __ldg(V.mat + v);
-    const float rho = __half2float(__ldg(V.rho + v));
-    if (m != cur) {
-      cur = m;
-      mu = smu[m * stride];
+    const int v = r.voxel<LAYOUT>(V, t);
+    if (v != vprev) {  // consecutive midpoints often share a voxel: reuse it
+      vprev = v;
+      const uint32_t word = __ldg(V.vox + v);
+      rho = vox_rho(word);
+      const int m = vox_mat(word);
+      if (m != cur) {
+        cur = m;
+        mu = smu[m * stride];
+      }
     }
     acc = fmaf(mu, rho, acc);
   }
@@ -193,6 +197,7 @@ struct Records {
 // One pseudo-particle (eq. Th): random pixel and point in it from the counter
 // block k0 + s of the record's stream, scatter-toward-detector pdf, optional
 // Russian roulette, attenuation march to the panel, FP64 tally.
+template <int LAYOUT>
 __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
                                                 int r, int s, float* my_mu, int stride, float nee_scale,
                                                 uint32_t npix, size_t img, Counters& C) {
@@ -248,12 +253,13 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
     x0 = P.rr_threshold;
   }
   fill_mu(T, Ep, my_mu, stride);
-  const float tp = march_tau(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
+  const float tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
   const unsigned long long h = ((unsigned long long)hhi << 32) | hlo;
   const int b = P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0;
   atomicAdd(P.tally + ((size_t)b * P.n_angles + a) * img + pix, (double)(x0 * __expf(-tp)));
 }
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -365,21 +371,25 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
         const float hh = L / (float)n;
         VoxRay vr;
         vr.set(V, x, w);
-        float tau = 0.f, mu_m = 0.f;
-        int cur = -1, k = 0;
+        float tau = 0.f, mu_m = 0.f, rho = 0.f;
+        int cur = -1, k = 0, vprev = -1;
         for (; k < n; ++k) {
           const float t = fmaf((float)k + 0.5f, hh, ta);
-          const int v = vr.voxel(V, t);
-          const int m = __ldg(V.mat + v);
-          const float rho = __half2float(__ldg(V.rho + v));
-          if (m != cur) {
-            cur = m;
-            mu_m = my_mu[m * B];
+          const int v = vr.voxel<LAYOUT>(V, t);
+          if (v != vprev) {
+            vprev = v;
+            const uint32_t word = __ldg(V.vox + v);
+            rho = vox_rho(word);
+            const int m = vox_mat(word);
+            if (m != cur) {
+              cur = m;
+              mu_m = my_mu[m * B];
+            }
           }
           const float mu = mu_m * rho;
           if (fmaf(mu, hh, tau) >= tau_star) {
             tint = fmaf((float)k, hh, ta) + (tau_star - tau) / mu;
-            mint = m;
+            mint = cur;
             hit = true;
             break;
           }
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
     const int n_jobs = s_nrec * n_split;
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
-      pseudo_particle(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C);
+      pseudo_particle<LAYOUT>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C);
     }
     const bool more = alive || next < total;
     __syncthreads();
@@ -497,16 +507,25 @@ int transport_smem_bytes(const TableView& t, int n_bins, int block) {
 }
 
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_transport<VOX_BRICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN>, block, smem);
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
   const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block);
-  cudaError_t e = cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  k_transport<<<grid, block, smem, s>>>(p);
+  cudaError_t e;
+  if (p.vol.layout == VOX_BRICK) {
+    e = cudaFuncSetAttribute(k_transport<VOX_BRICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_transport<VOX_BRICK><<<grid, block, smem, s>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(k_transport<VOX_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_transport<VOX_LIN><<<grid, block, smem, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -35,8 +35,9 @@ struct mc_ctx {
   bool blob_dirty = true;
   // volume
   bool have_volume = false;
-  uint8_t* d_mat = nullptr;
-  __half* d_rho = nullptr;
+  uint32_t* d_vox = nullptr;  // packed voxel words (material | FP16 density)
+  size_t vox_cap = 0;
+  int layout = VOX_LIN;
   int nx = 0, ny = 0, nz = 0;
   float dx = 0, dy = 0, dz = 0;
   // spectrum
@@ -103,6 +104,7 @@ int validate_options(const mc_options* o, std::string& why) {
     return why = "sg_window must be odd, >= sg_order + 2 and <= 31", -1;
   if (!(o->cubic_a < 0.f && o->cubic_a > -3.f)) return why = "cubic_a must be in (-3, 0)", -1;
   if (o->denoise_mode != 0 && o->denoise_mode != 2) return why = "denoise_mode must be 0 or 2", -1;
+  if (o->voxel_layout < 0 || o->voxel_layout > 2) return why = "voxel_layout must be 0, 1 or 2", -1;
   return 0;
 }
 
@@ -183,8 +185,10 @@ TableView table_view(const mc_ctx* c) {
 
 VolumeView volume_view(const mc_ctx* c) {
   VolumeView v;
-  v.mat = c->d_mat;
-  v.rho = c->d_rho;
+  v.vox = c->d_vox;
+  v.layout = c->layout;
+  v.nbx = (c->nx + 3) / 4;
+  v.nby = (c->ny + 3) / 4;
   v.nx = c->nx; v.ny = c->ny; v.nz = c->nz;
   v.dx = c->dx; v.dy = c->dy; v.dz = c->dz;
   v.inv_dx = 1.f / c->dx; v.inv_dy = 1.f / c->dy; v.inv_dz = 1.f / c->dz;
@@ -443,6 +447,7 @@ void mc_default_options(mc_options* o) {
   o->sg_order = 3;
   o->cubic_a = -0.5f;
   o->denoise_mode = 0;
+  o->voxel_layout = 0;
 }
 
 int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {
@@ -477,8 +482,7 @@ void mc_destroy(mc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   cudaFree(ctx->d_blob);
-  cudaFree(ctx->d_mat);
-  cudaFree(ctx->d_rho);
+  cudaFree(ctx->d_vox);
   cudaFree(ctx->d_spec);
   cudaFree(ctx->d_tally);
   cudaFree(ctx->d_stats);
@@ -583,25 +587,45 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
       if (((h >> 10) & 31u) == 31u) return fail(ctx, MC_ERR_INVALID_ARG, "non-finite density");
     }
   }
-  if (ctx->have_volume && (size_t)ctx->nx * ctx->ny * ctx->nz != n) {
-    cudaFree(ctx->d_mat);
-    cudaFree(ctx->d_rho);
-    ctx->d_mat = nullptr;
-    ctx->d_rho = nullptr;
-  }
   ctx->have_volume = false;
-  if (!ctx->d_mat) CK(cudaMalloc((void**)&ctx->d_mat, n), "volume allocation");
-  if (!ctx->d_rho) CK(cudaMalloc((void**)&ctx->d_rho, n * 2), "volume allocation");
-  const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(ctx->d_mat, mat, n, kind, s), "volume copy");
-  CK(cudaMemcpyAsync(ctx->d_rho, rho_fp16, n * 2, kind, s), "volume copy");
-  if (is_device_ptr) {
-    // device data: validate on the device (max material id, finite non-negative densities)
-    int bad = 0;
-    cudaError_t e = validate_volume_device(ctx->d_mat, (const uint16_t*)ctx->d_rho, n, ctx->n_mat, s, &bad);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "volume validation");
-    if (bad) return fail(ctx, MC_ERR_INVALID_ARG, "volume holds an unknown material id or an invalid density");
+  // stage the two arrays on the device, validate, pack into voxel words
+  uint8_t* st_mat = nullptr;
+  uint16_t* st_rho = nullptr;
+  CK(cudaMallocAsync((void**)&st_mat, n, s), "volume staging allocation");
+  cudaError_t e = cudaMallocAsync((void**)&st_rho, n * 2, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(st_mat, s);
+    return cuda_fail(ctx, e, "volume staging allocation");
   }
+  auto release = [&]() {
+    cudaFreeAsync(st_mat, s);
+    cudaFreeAsync(st_rho, s);
+  };
+  const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  e = cudaMemcpyAsync(st_mat, mat, n, kind, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st_rho, rho_fp16, n * 2, kind, s);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(ctx, e, "volume copy");
+  }
+  if (is_device_ptr) {
+    // device data: validate on the device (material ids, finite non-negative densities)
+    int bad = 0;
+    e = validate_volume_device(st_mat, st_rho, n, ctx->n_mat, s, &bad);
+    if (e != cudaSuccess || bad) {
+      release();
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "volume validation");
+      return fail(ctx, MC_ERR_INVALID_ARG, "volume holds an unknown material id or an invalid density");
+    }
+  }
+  const int layout = ctx->opt.voxel_layout == 2 ? VOX_BRICK : VOX_LIN;
+  const size_t words = packed_words(nx, ny, nz, layout);
+  e = ensure(ctx->d_vox, ctx->vox_cap, words);
+  if (e == cudaSuccess) e = pack_volume(st_mat, st_rho, nx, ny, nz, layout, ctx->d_vox, words, s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "volume packing");
+  CK(cudaStreamSynchronize(s), "volume load");
+  ctx->layout = layout;
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz;
   ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   ctx->have_volume = true;

@@ -150,6 +150,16 @@ __device__ __forceinline__ bool clip_box(const VolumeView& v, float3 x, float3 w
   return b > a;
 }
 
+// Word index of voxel (ix, iy, iz) in the packed volume.
+template <int LAYOUT>
+__device__ __forceinline__ int vox_index(const VolumeView& vol, int ix, int iy, int iz) {
+  if (LAYOUT == VOX_LIN) return (iz * vol.ny + iy) * vol.nx + ix;
+  const int brick = ((iz >> 2) * vol.nby + (iy >> 2)) * vol.nbx + (ix >> 2);
+  const int lx = ix & 3, ly = iy & 3, lz = iz & 3;
+  const int m = (lx & 1) | ((ly & 1) << 1) | ((lz & 1) << 2) | ((lx & 2) << 2) | ((ly & 2) << 3) | ((lz & 2) << 4);
+  return (brick << 6) | m;
+}
+
 // Ray in voxel units: v(t) = v0 + t vw, voxel = floor(v) clamped.
 struct VoxRay {
   float3 v0, vw;
@@ -158,13 +168,17 @@ struct VoxRay {
                      fmaf(x.z, vol.inv_dz, 0.5f * (float)vol.nz));
     vw = make_float3(w.x * vol.inv_dx, w.y * vol.inv_dy, w.z * vol.inv_dz);
   }
+  template <int LAYOUT>
   __device__ __forceinline__ int voxel(const VolumeView& vol, float t) const {
     const int ix = min(max(__float2int_rd(fmaf(t, vw.x, v0.x)), 0), vol.nx - 1);
     const int iy = min(max(__float2int_rd(fmaf(t, vw.y, v0.y)), 0), vol.ny - 1);
     const int iz = min(max(__float2int_rd(fmaf(t, vw.z, v0.z)), 0), vol.nz - 1);
-    return (iz * vol.ny + iy) * vol.nx + ix;
+    return vox_index<LAYOUT>(vol, ix, iy, iz);
   }
 };
+
+__device__ __forceinline__ int vox_mat(uint32_t w) { return (int)((w >> 16) & 255u); }
+__device__ __forceinline__ float vox_rho(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
 
 __device__ __forceinline__ int step_count(float L, float step) { return max(1, (int)ceilf(L / step)); }
 

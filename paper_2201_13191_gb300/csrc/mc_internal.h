@@ -34,9 +34,16 @@ struct TableView {
   float mec2, inv_hc;
 };
 
+// Voxel word: bits 0-15 the FP16 density (g/cm^3), bits 16-23 the material id.
+// Layout LIN: x fastest.  Layout BRICK: 4x4x4 bricks (x fastest between
+// bricks), Morton order inside a brick, so each 32-byte sector holds a 2x2x2
+// cube and each 128-byte line a 4x4x2 slab whatever the ray direction.
+enum VoxLayout { VOX_LIN = 0, VOX_BRICK = 1 };
+
 struct VolumeView {
-  const uint8_t* mat;
-  const __half* rho;
+  const uint32_t* vox;
+  int layout;
+  int nbx, nby;  // bricks along x, y (BRICK layout)
   int nx, ny, nz;
   float dx, dy, dz;
   float inv_dx, inv_dy, inv_dz;
@@ -95,6 +102,10 @@ cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
 // densities); *bad_host = 1 if any voxel fails.  Synchronises s.
 cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size_t n, int n_mat, cudaStream_t s,
                                    int* bad_host);
+// Packs material + density into voxel words in the given layout.
+cudaError_t pack_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, int layout, uint32_t* out,
+                        size_t out_words, cudaStream_t s);
+size_t packed_words(int nx, int ny, int nz, int layout);
 
 // post-processing
 cudaError_t launch_sg_rows(const float* in, float* out, int n_img, int h, int w, const float* coef, int win,

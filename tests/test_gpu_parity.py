@@ -175,6 +175,23 @@ def test_multi_angle_launch(gpu, table_path, tables):
     assert not np.allclose(both["scatter"][0].cpu().numpy(), both["scatter"][1].cpu().numpy())
 
 
+def test_voxel_layouts_agree(gpu, table_path, tables):
+    """x-fastest and 4^3-brick device layouts hold the same volume: identical
+    primary images and the same scatter up to FP64 summation order; the
+    ragged 70 x 66 x 61 volume exercises partially filled bricks."""
+    wl = _small_poly_workload(tables)
+    v = wl["volume"]
+    v = dict(v, mat=np.ascontiguousarray(v["mat"][:61, :66, :70]), rho=np.ascontiguousarray(v["rho"][:61, :66, :70]))
+    wl = dict(wl, volume=v)
+    imgs = []
+    for layout in (1, 2):
+        c = _ctx(gpu, table_path, wl, voxel_layout=layout)
+        out = c.project([0.9, 2.0], 50_000, wl["step_mm"], 6)
+        imgs.append({k: t.cpu().numpy() for k, t in out.items()})
+    np.testing.assert_array_equal(imgs[0]["primary"], imgs[1]["primary"])
+    np.testing.assert_allclose(imgs[0]["scatter"], imgs[1]["scatter"], rtol=1e-5, atol=1e-12)
+
+
 def test_deterministic_up_to_fp64_sum_order(gpu, table_path, tables):
     wl = make_workload("cyl64", tables)
     c = _ctx(gpu, table_path, wl)
