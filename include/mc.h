@@ -162,6 +162,36 @@ int mc_last_stats(const mc_ctx *ctx, double *out, int n);
 int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_angles, int nu, int nv, float *out,
                        int n_out, const float *out_angles, int NU, int NV, void *stream);
 
+/* Scatter projection that allocates nothing (no counterpart in the paper: an
+ * integration aid).  Some callers cannot allocate device memory once running:
+ * services that reserve the whole GPU for a fixed memory pool at start-up (a
+ * later cudaMalloc fails or stalls their other streams) and real-time
+ * acquisition loops that cannot afford cudaMalloc's implicit device
+ * synchronisation per projection.  Such a caller loads tables, volume,
+ * spectrum and geometry once at start-up (those calls allocate), then calls
+ * this entry point, which computes the same scatter image as mc_project
+ * (scatter_out only, n_batches ignored) while keeping its scratch -- FP64
+ * tally image, counters, staged tables, spectrum block, angles -- in one
+ * file-scope __device__ array of about 32.4 MiB, held on every GPU that loads
+ * the library until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   - Limits: n_angles <= MC_STATIC_MAX_ANGLES and n_angles * nu * nv <=
+ *     MC_STATIC_MAX_TALLY; larger requests return MC_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call re-stages and zeroes what it uses, so it never sees an
+ *     earlier call's contents; but all calls share the one array, so calls
+ *     that overlap on the GPU (other streams, other host threads, other
+ *     contexts on the same device) race: serialise them.
+ *   - Uses about 80 KB of the calling thread's stack for host staging.
+ * Inputs: angles_rad host [n_angles]; scatter_out device FP32
+ * [n_angles][nv][nu].  Errors: as mc_project. */
+#define MC_STATIC_MAX_TALLY 4194304
+#define MC_STATIC_MAX_ANGLES 4096
+int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm,
+                              uint64_t seed, float *scatter_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

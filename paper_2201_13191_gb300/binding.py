@@ -32,7 +32,7 @@ STAT_NAMES = [
 EXPORTED = [
     "mc_default_options", "mc_create", "mc_destroy", "mc_set_options", "mc_last_error", "mc_load_tables",
     "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
-    "mc_last_stats", "mc_smooth_upsample",
+    "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static",
 ]
 
 
@@ -90,6 +90,7 @@ def library():
         L.mc_project_histories.argtypes = [P, vp, i, u64, u64, u64, f, u64, vp, vp]
         L.mc_last_stats.argtypes = [P, C.POINTER(C.c_double), i]
         L.mc_smooth_upsample.argtypes = [P, vp, i, vp, i, i, vp, i, vp, i, i, vp]
+        L.mc_project_scatter_static.argtypes = [P, vp, i, u64, f, u64, vp, vp]
         _lib = L
     return _lib
 
@@ -220,6 +221,19 @@ class Context:
             _t_ptr(out), _stream_handle(stream),
         )
         self._check(rc)
+        return out
+
+    def project_scatter_static(self, angles, n_photons, step_mm, seed, out=None, stream=None, allow_limit=False):
+        """Scatter image through the entry point that allocates nothing (its
+        scratch is a fixed array inside the library); out is allocated here by
+        torch only when the caller does not pass one."""
+        a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
+        if out is None:
+            out = self.empty_images(len(a))
+        rc = self.L.mc_project_scatter_static(
+            self.h, _np_ptr(a), len(a), int(n_photons), float(step_mm), int(seed), _t_ptr(out), _stream_handle(stream)
+        )
+        self._check(rc, allow_limit)
         return out
 
     def last_stats(self):

@@ -759,3 +759,131 @@ int mc_smooth_upsample(mc_ctx* ctx, const float* in, int n_in, const float* in_a
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Read-only accessors for the static-scratch entry point (k_static.cu).  None
+// of them allocates device or host heap memory: results go to caller buffers.
+namespace mcx {
+
+int static_check(mc_ctx* ctx, int* device, int* nu, int* nv) {
+  const int rc = check_ready(ctx);
+  if (rc) return rc;
+  *device = ctx->device;
+  *nu = ctx->nu;
+  *nv = ctx->nv;
+  return MC_OK;
+}
+
+int static_fail(mc_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
+int static_cuda_fail(mc_ctx* ctx, cudaError_t e, const char* where) { return cuda_fail(ctx, e, where); }
+
+// FP32 shared-memory table blob for the nodes the spectrum reaches, written
+// into dst (capacity cap bytes); same layout as the context's own blob.
+int static_build_blob(mc_ctx* ctx, unsigned char* dst, int cap, int* bytes_out, int* n_stage_out) {
+  double Emax = ctx->E0 + 1.0;
+  for (size_t n = 0; n < ctx->S.size(); ++n) Emax = std::max(Emax, (double)ctx->Ebin[n]);
+  int ns = (int)std::floor((Emax - ctx->E0) / ctx->dE) + 2;
+  ns = std::max(2, std::min(ns, ctx->n_E));
+  const int nm = ctx->n_mat;
+  const int bytes = tab_blob_bytes(nm, ns);
+  if (bytes > cap) return fail(ctx, MC_ERR_INVALID_ARG, "cross-section tables exceed the static table area");
+  std::memset(dst, 0, bytes);
+  float2* tab = reinterpret_cast<float2*>(dst);
+  for (int kind = 0; kind < kTabKinds; ++kind)
+    for (int m = 0; m < nm; ++m)
+      for (int i = 0; i < ns; ++i) {
+        auto val = [&](int j) {
+          const size_t q = (size_t)m * ctx->n_E + j;
+          switch (kind) {
+            case TAB_TOT: return ctx->pe[q] + ctx->in[q] + ctx->co[q];
+            case TAB_PE: return ctx->pe[q];
+            case TAB_IN: return ctx->in[q];
+            case TAB_CO: return ctx->co[q];
+            default: return ctx->icoh[q];
+          }
+        };
+        const double v0 = val(i), v1 = val(std::min(i + 1, ctx->n_E - 1));
+        tab[(kind * nm + m) * ns + i] = make_float2((float)v0, (float)(v1 - v0));
+      }
+  float2* jkn = reinterpret_cast<float2*>(dst + tab_off_jkn(nm, ns));
+  for (int i = 0; i < ns; ++i) {
+    const double E = ctx->E0 + ctx->dE * i;
+    const double j0 = kn_norm(E, ctx->mec2), j1 = kn_norm(E + ctx->dE, ctx->mec2);
+    jkn[i] = make_float2((float)j0, (float)(j1 - j0));
+  }
+  float2* comp = reinterpret_cast<float2*>(dst + tab_off_comp(nm, ns));
+  int* ncomp = reinterpret_cast<int*>(dst + tab_off_ncomp(nm, ns));
+  for (int m = 0; m < nm; ++m) {
+    ncomp[m] = ctx->n_comp[m];
+    for (int i = 0; i < kMaxComp; ++i) {
+      const double Z = ctx->comp[m][i][0], w = ctx->comp[m][i][1], b = ctx->comp[m][i][2];
+      comp[m * kMaxComp + i] = i < ctx->n_comp[m] ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
+    }
+  }
+  *bytes_out = bytes;
+  *n_stage_out = ns;
+  return MC_OK;
+}
+
+// Stratified counts (as in the main path) written as prefix sums, energies,
+// S_n / M_n and S_n into caller arrays of MC_MAX_BINS (+1) entries.
+int static_stratify(mc_ctx* ctx, uint64_t N, unsigned long long* pre, float* en, float* wb, float* sn, int* n_out) {
+  const int n = (int)ctx->S.size();
+  uint64_t M[MC_MAX_BINS];
+  int elig[MC_MAX_BINS];
+  double fr[MC_MAX_BINS];
+  uint64_t sum = 0;
+  for (int i = 0; i < n; ++i) {
+    const double x = (double)N * ctx->S[i];
+    const double fl = std::floor(x);
+    elig[i] = 0;
+    fr[i] = 0.0;
+    if (ctx->S[i] <= 0) M[i] = 0;
+    else if (fl < 1.0) M[i] = 1;
+    else {
+      M[i] = (uint64_t)fl;
+      elig[i] = 1;
+      fr[i] = x - fl;
+    }
+    sum += M[i];
+  }
+  if (sum > N) return fail(ctx, MC_ERR_INVALID_ARG, "n_photons is smaller than the number of non-empty energy bins");
+  uint64_t rem = N - sum;
+  while (rem > 0) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (elig[i] == 1 && (best < 0 || fr[i] > fr[best])) best = i;
+    if (best < 0) break;
+    M[best] += 1;
+    elig[best] = 2;
+    --rem;
+  }
+  if (rem) return fail(ctx, MC_ERR_INTERNAL, "stratification did not place every photon");
+  pre[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    pre[i + 1] = pre[i] + M[i];
+    en[i] = ctx->Ebin[i];
+    wb[i] = M[i] ? (float)(ctx->S[i] / (double)M[i]) : 0.f;
+    sn[i] = (float)ctx->S[i];
+  }
+  *n_out = n;
+  return MC_OK;
+}
+
+void static_views(mc_ctx* ctx, TableView* t, VolumeView* v, GeomView* g, mc_options* opt, int* sm_count) {
+  *t = table_view(ctx);
+  *v = volume_view(ctx);
+  *g = geom_view(ctx);
+  *opt = ctx->opt;
+  *sm_count = ctx->sm_count;
+}
+
+void static_set_stats(mc_ctx* ctx, const unsigned long long* st, float ms) {
+  const int map[10] = {S_HIST, S_FLIGHT_STEPS, S_NEE_STEPS, S_NEE_RAYS, S_PHOTO, S_COMPTON, S_RAYLEIGH, S_ESCAPE, S_LIMIT, S_SAMPLER_FAIL};
+  for (int i = 0; i < 10; ++i) ctx->stats[i] = (double)st[map[i]];
+  ctx->stats[10] = ms;
+  ctx->stats[11] = 0;
+}
+
+}  // namespace mcx
