@@ -123,30 +123,46 @@ __global__ void k_validate_volume(const uint8_t* __restrict__ mat, const uint16_
 }
 }  // namespace
 
-__global__ void k_pack_volume(const uint8_t* __restrict__ mat, const uint16_t* __restrict__ rho, int nx, int ny,
-                              int nz, int layout, int nbx, int nby, uint32_t* __restrict__ out) {
-  const size_t n = (size_t)nx * ny * nz;
+// Packs material + density into voxel words over the padded grid; border
+// voxels repeat the nearest edge voxel.
+__global__ void k_pack_volume(const uint8_t* __restrict__ mat, const uint16_t* __restrict__ rho, VolumeView v,
+                              uint32_t* __restrict__ out) {
+  const size_t n = (size_t)v.px * v.py * v.pz;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % nx);
-    const size_t r = i / nx;
-    const int iy = (int)(r % ny), iz = (int)(r / ny);
-    VolumeView v;
-    v.nx = nx; v.ny = ny; v.nz = nz; v.nbx = nbx; v.nby = nby;
-    const int o = layout == VOX_BRICK ? vox_index<VOX_BRICK>(v, ix, iy, iz) : vox_index<VOX_LIN>(v, ix, iy, iz);
-    out[o] = (uint32_t)rho[i] | ((uint32_t)mat[i] << 16);
+    const int px = (int)(i % v.px);
+    const size_t r = i / v.px;
+    const int py = (int)(r % v.py), pz = (int)(r / v.py);
+    const int ix = min(max(px - 1, 0), v.nx - 1), iy = min(max(py - 1, 0), v.ny - 1), iz = min(max(pz - 1, 0), v.nz - 1);
+    const size_t src = ((size_t)iz * v.ny + iy) * v.nx + ix;
+    const int o = v.layout == VOX_BRICK ? vox_index<VOX_BRICK>(v, px, py, pz) : vox_index<VOX_LIN>(v, px, py, pz);
+    out[o] = (uint32_t)rho[src] | ((uint32_t)mat[src] << 16);
   }
 }
 
+void padded_dims(int nx, int ny, int nz, int layout, VolumeView* v) {
+  v->nx = nx; v->ny = ny; v->nz = nz;
+  v->px = nx + 2; v->py = ny + 2; v->pz = nz + 2;
+  v->layout = layout;
+  v->nbx = (v->px + 3) / 4;
+  v->nby = (v->py + 3) / 4;
+  const size_t words = layout == VOX_BRICK ? (size_t)v->nbx * v->nby * ((v->pz + 3) / 4) * 64
+                                           : (size_t)v->px * v->py * v->pz;
+  v->words = (int)words;
+}
+
 size_t packed_words(int nx, int ny, int nz, int layout) {
-  if (layout != VOX_BRICK) return (size_t)nx * ny * nz;
-  return (size_t)((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4) * 64;
+  VolumeView v;
+  padded_dims(nx, ny, nz, layout, &v);
+  return (size_t)v.words;
 }
 
 cudaError_t pack_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, int layout, uint32_t* out,
                         size_t out_words, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, out_words * 4, s);
   if (e != cudaSuccess) return e;
-  k_pack_volume<<<1024, 256, 0, s>>>(mat, rho, nx, ny, nz, layout, (nx + 3) / 4, (ny + 3) / 4, out);
+  VolumeView v;
+  padded_dims(nx, ny, nz, layout, &v);
+  k_pack_volume<<<1024, 256, 0, s>>>(mat, rho, v, out);
   return cudaGetLastError();
 }
 

@@ -73,6 +73,35 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
   for (int m = 0; m < T.n_mat; ++m) smu[m * stride] = 0.1f * T.at(TAB_TOT, m, i, f);
 }
 
+// Gathers of the next MC_LOOKAHEAD midpoints are issued before any of them is
+// consumed: the step positions are fixed in advance, so the loads are
+// independent and several are in flight per warp.  A load is skipped when the
+// midpoint stays in the previous voxel.
+#ifndef MC_LOOKAHEAD
+#define MC_LOOKAHEAD 8
+#endif
+constexpr int kLook = MC_LOOKAHEAD;
+
+template <int LAYOUT>
+__device__ __forceinline__ void gather_ahead(const VolumeView& V, const VoxRay& r, int k0, int n, float h, float ta,
+                                             int& vprev, uint32_t& wprev, uint32_t (&wd)[kLook]) {
+  int idx[kLook];
+#pragma unroll
+  for (int u = 0; u < kLook; ++u) idx[u] = r.voxel<LAYOUT>(V, fmaf((float)(k0 + u) + 0.5f, h, ta));
+#pragma unroll
+  for (int u = 0; u < kLook; ++u) {
+    const int prev = u == 0 ? vprev : idx[u - 1];
+    if (k0 + u < n && idx[u] != prev) wd[u] = __ldg(V.vox + idx[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < kLook; ++u) {
+    const int prev = u == 0 ? vprev : idx[u - 1];
+    if (idx[u] == prev) wd[u] = u == 0 ? wprev : wd[u - 1];
+  }
+  vprev = idx[kLook - 1];
+  wprev = wd[kLook - 1];
+}
+
 // Optical depth of the fixed-step march x + t w, t in [0, t1] (Sec. II-C.2),
 // material attenuation from smu (this thread's column); counts steps.
 template <int LAYOUT>
@@ -85,22 +114,23 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   const float h = L / (float)n;
   VoxRay r;
   r.set(V, x, w);
-  float acc = 0.f, mu = 0.f, rho = 0.f;
+  float acc = 0.f, mu = 0.f;
   int cur = -1, vprev = -1;
-  for (int k = 0; k < n; ++k) {
-    const float t = fmaf((float)k + 0.5f, h, ta);
-    const int v = r.voxel<LAYOUT>(V, t);
-    if (v != vprev) {  // consecutive midpoints often share a voxel: reuse it
-      vprev = v;
-      const uint32_t word = __ldg(V.vox + v);
-      rho = vox_rho(word);
-      const int m = vox_mat(word);
-      if (m != cur) {
-        cur = m;
-        mu = smu[m * stride];
+  uint32_t wprev = 0;
+  for (int k0 = 0; k0 < n; k0 += kLook) {
+    uint32_t wd[kLook];
+    gather_ahead<LAYOUT>(V, r, k0, n, h, ta, vprev, wprev, wd);
+#pragma unroll
+    for (int u = 0; u < kLook; ++u) {
+      if (k0 + u < n) {
+        const int m = vox_mat(wd[u]);
+        if (m != cur) {
+          cur = m;
+          mu = smu[m * stride];
+        }
+        acc = fmaf(mu, vox_rho(wd[u]), acc);
       }
     }
-    acc = fmaf(mu, rho, acc);
   }
   nsteps += (unsigned long long)n;
   return acc * h;
@@ -189,7 +219,7 @@ __device__ __forceinline__ float3 rotate(float3 w, float ct, float phi) {
 // Interaction records queued by the flight phase for the pseudo-particle
 // phase, one slot per thread of the block (structure of arrays).
 struct Records {
-  float *X, *Y, *Z, *wx, *wy, *wz, *E, *W, *norm, *cb, *sb;
+  float *X, *Y, *Z, *wx, *wy, *wz, *E, *W, *norm, *cb, *sb, *len;
   int* tm;  // type << 8 | material
   uint32_t *hlo, *hhi, *ang, *k0;
 };
@@ -259,11 +289,23 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   atomicAdd(P.tally + ((size_t)b * P.n_angles + a) * img + pix, (double)(x0 * __expf(-tp)));
 }
 
+#ifndef MC_MIN_BLOCKS
+#define MC_MIN_BLOCKS 3
+#endif
+// Pseudo-particle jobs are handed out longest records first: records are
+// bucketed by the chord from the interaction point to the volume boundary
+// toward the panel centre, and each warp fetches the next 32 jobs.
+#ifndef MC_SORT
+#define MC_SORT 1
+#endif
+constexpr int kBuckets = 16;
+
 template <int LAYOUT>
-__global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
+__global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
-  __shared__ int s_nrec;
+  __shared__ int s_nrec, s_job;
+  __shared__ int s_bucket[kBuckets + 1];
   const int nm = P.tab.n_mat, ns = P.tab.n_stage;
   const int nb = P.spec.n_bins;
   const int B = blockDim.x;
@@ -283,6 +325,8 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
   R.hhi = reinterpret_cast<uint32_t*>(rec + 13 * B);
   R.ang = reinterpret_cast<uint32_t*>(rec + 14 * B);
   R.k0 = reinterpret_cast<uint32_t*>(rec + 15 * B);
+  R.len = rec + 16 * B;
+  int* s_ord = reinterpret_cast<int*>(rec + 17 * B);  // record order for the pseudo-particle phase
 
   const bool staged = stage_bulk(s_blob, P.tab.blob, P.tab.blob_bytes, &bar);
   for (int i = threadIdx.x; i <= nb; i += B) s_pre[i] = P.spec.prefix[i];
@@ -371,29 +415,31 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
         const float hh = L / (float)n;
         VoxRay vr;
         vr.set(V, x, w);
-        float tau = 0.f, mu_m = 0.f, rho = 0.f;
-        int cur = -1, k = 0, vprev = -1;
-        for (; k < n; ++k) {
-          const float t = fmaf((float)k + 0.5f, hh, ta);
-          const int v = vr.voxel<LAYOUT>(V, t);
-          if (v != vprev) {
-            vprev = v;
-            const uint32_t word = __ldg(V.vox + v);
-            rho = vox_rho(word);
-            const int m = vox_mat(word);
-            if (m != cur) {
-              cur = m;
-              mu_m = my_mu[m * B];
+        float tau = 0.f, mu_m = 0.f;
+        int cur = -1, vprev = -1, k = n;
+        uint32_t wprev = 0;
+        for (int k0 = 0; k0 < n && !hit; k0 += kLook) {
+          uint32_t wd[kLook];
+          gather_ahead<LAYOUT>(V, vr, k0, n, hh, ta, vprev, wprev, wd);
+#pragma unroll
+          for (int u = 0; u < kLook; ++u) {
+            if (!hit && k0 + u < n) {
+              const int m = vox_mat(wd[u]);
+              if (m != cur) {
+                cur = m;
+                mu_m = my_mu[m * B];
+              }
+              const float mu = mu_m * vox_rho(wd[u]);
+              if (fmaf(mu, hh, tau) >= tau_star) {
+                tint = fmaf((float)(k0 + u), hh, ta) + (tau_star - tau) / mu;
+                mint = cur;
+                hit = true;
+                k = k0 + u;
+              } else {
+                tau = fmaf(mu, hh, tau);
+              }
             }
           }
-          const float mu = mu_m * rho;
-          if (fmaf(mu, hh, tau) >= tau_star) {
-            tint = fmaf((float)k, hh, ta) + (tau_star - tau) / mu;
-            mint = cur;
-            hit = true;
-            break;
-          }
-          tau = fmaf(mu, hh, tau);
         }
         C.flight_steps += (unsigned long long)(hit ? k + 1 : n);
       }
@@ -426,6 +472,15 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
           R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
           R.k0[r] = g.ctr.x;
           g.ctr.x += (uint32_t)n_split;
+          {
+            // length key: chord toward the panel centre
+            const float rr0 = G.sod - G.sdd;
+            const float3 toc = make_float3(rr0 * cb - x.x, rr0 * sb - x.y, -x.z);
+            const float il = rsqrtf(dot3(toc, toc));
+            float ca, cbb;
+            R.len[r] = clip_box(V, x, make_float3(toc.x * il, toc.y * il, toc.z * il), 0.f,
+                                __int_as_float(0x7f800000), ca, cbb) ? cbb : 0.f;
+          }
           // new direction
           bool fail = false;
           float ct, Enew = E;
@@ -453,11 +508,45 @@ __global__ void __launch_bounds__(256, 3) k_transport(const TransportParams P) {
     }
     __syncthreads();
     // ---- pseudo-particle phase: the block marches every queued ray together
-    const int n_jobs = s_nrec * n_split;
+    const int nrec = s_nrec;
+    const int n_jobs = nrec * n_split;
+#if MC_SORT
+    {
+      // counting sort of the records into length buckets, longest first
+      const float lmax = 2.f * sqrtf(V.hx * V.hx + V.hy * V.hy + V.hz * V.hz);  // box diagonal
+      if (threadIdx.x <= kBuckets) s_bucket[threadIdx.x] = 0;
+      if (threadIdx.x == 0) s_job = 0;
+      __syncthreads();
+      int bk = 0, slot = 0;
+      if (threadIdx.x < nrec) {
+        bk = kBuckets - 1 - min(kBuckets - 1, (int)(R.len[threadIdx.x] * (float)kBuckets / lmax));
+        slot = atomicAdd(&s_bucket[bk + 1], 1);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int b = 1; b <= kBuckets; ++b) s_bucket[b] += s_bucket[b - 1];
+      __syncthreads();
+      if (threadIdx.x < nrec) s_ord[s_bucket[bk] + slot] = threadIdx.x;
+      __syncthreads();
+      const int lane = threadIdx.x & 31;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_job, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_jobs) break;
+        const int j = base + lane;
+        if (j < n_jobs) {
+          const int q = j / n_split;
+          pseudo_particle<LAYOUT>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C);
+        }
+      }
+    }
+#else
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
       pseudo_particle<LAYOUT>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C);
     }
+#endif
     const bool more = alive || next < total;
     __syncthreads();
     if (threadIdx.x == 0) s_nrec = 0;
@@ -503,7 +592,7 @@ __global__ void k_finalize(const double* __restrict__ tally, int B, size_t n, fl
 }  // namespace
 
 int transport_smem_bytes(const TableView& t, int n_bins, int block) {
-  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 16 * block * 4;
+  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 18 * block * 4;
 }
 
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {

@@ -185,11 +185,8 @@ TableView table_view(const mc_ctx* c) {
 
 VolumeView volume_view(const mc_ctx* c) {
   VolumeView v;
+  padded_dims(c->nx, c->ny, c->nz, c->layout, &v);
   v.vox = c->d_vox;
-  v.layout = c->layout;
-  v.nbx = (c->nx + 3) / 4;
-  v.nby = (c->ny + 3) / 4;
-  v.nx = c->nx; v.ny = c->ny; v.nz = c->nz;
   v.dx = c->dx; v.dy = c->dy; v.dz = c->dz;
   v.inv_dx = 1.f / c->dx; v.inv_dy = 1.f / c->dy; v.inv_dz = 1.f / c->dz;
   v.hx = 0.5f * c->nx * c->dx; v.hy = 0.5f * c->ny * c->dy; v.hz = 0.5f * c->nz * c->dz;
@@ -575,7 +572,10 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
   if (!mat || !rho_fp16 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0))
     return fail(ctx, MC_ERR_INVALID_ARG, "bad volume arguments");
   const size_t n = (size_t)nx * ny * nz;
-  if (n > (size_t)INT32_MAX) return fail(ctx, MC_ERR_INVALID_ARG, "volume larger than 2^31 voxels");
+  if (n > (size_t)INT32_MAX || packed_words(nx, ny, nz, VOX_BRICK) > (size_t)INT32_MAX)
+    return fail(ctx, MC_ERR_INVALID_ARG, "volume larger than 2^31 voxels");
+  if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+    return fail(ctx, MC_ERR_INVALID_ARG, "volume dimension above 2^20");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   if (!is_device_ptr) {

@@ -150,30 +150,41 @@ __device__ __forceinline__ bool clip_box(const VolumeView& v, float3 x, float3 w
   return b > a;
 }
 
-// Word index of voxel (ix, iy, iz) in the packed volume.
+// Word index of padded voxel (ix, iy, iz) in the packed volume.
 template <int LAYOUT>
-__device__ __forceinline__ int vox_index(const VolumeView& vol, int ix, int iy, int iz) {
-  if (LAYOUT == VOX_LIN) return (iz * vol.ny + iy) * vol.nx + ix;
+__device__ __host__ __forceinline__ int vox_index(const VolumeView& vol, int ix, int iy, int iz) {
+  if (LAYOUT == VOX_LIN) return (iz * vol.py + iy) * vol.px + ix;
   const int brick = ((iz >> 2) * vol.nby + (iy >> 2)) * vol.nbx + (ix >> 2);
   const int lx = ix & 3, ly = iy & 3, lz = iz & 3;
   const int m = (lx & 1) | ((ly & 1) << 1) | ((lz & 1) << 2) | ((lx & 2) << 2) | ((ly & 2) << 3) | ((lz & 2) << 4);
   return (brick << 6) | m;
 }
 
-// Ray in voxel units: v(t) = v0 + t vw, voxel = floor(v) clamped.
+// floor(y) for 0 <= y < 2^22 by one round-down add: 2^23 + y rounded toward
+// minus infinity is 2^23 + floor(y), whose bit pattern minus that of 2^23 is
+// the integer (full-rate FP add instead of a conversion).
+__device__ __forceinline__ int floor_pos(float y) {
+  return __float_as_int(__fadd_rd(y, 8388608.0f)) - 0x4B000000;
+}
+
+// Ray in padded voxel units: v(t) = v0 + t vw, voxel = floor(v).
 struct VoxRay {
   float3 v0, vw;
   __device__ __forceinline__ void set(const VolumeView& vol, float3 x, float3 w) {
-    v0 = make_float3(fmaf(x.x, vol.inv_dx, 0.5f * (float)vol.nx), fmaf(x.y, vol.inv_dy, 0.5f * (float)vol.ny),
-                     fmaf(x.z, vol.inv_dz, 0.5f * (float)vol.nz));
+    v0 = make_float3(fmaf(x.x, vol.inv_dx, 0.5f * (float)vol.nx + 1.f),
+                     fmaf(x.y, vol.inv_dy, 0.5f * (float)vol.ny + 1.f),
+                     fmaf(x.z, vol.inv_dz, 0.5f * (float)vol.nz + 1.f));
     vw = make_float3(w.x * vol.inv_dx, w.y * vol.inv_dy, w.z * vol.inv_dz);
   }
+  // Word index of the voxel holding the point at parameter t (a point inside
+  // the clipped chord; the border absorbs rounding, the final clamp only
+  // guards the array bounds).
   template <int LAYOUT>
   __device__ __forceinline__ int voxel(const VolumeView& vol, float t) const {
-    const int ix = min(max(__float2int_rd(fmaf(t, vw.x, v0.x)), 0), vol.nx - 1);
-    const int iy = min(max(__float2int_rd(fmaf(t, vw.y, v0.y)), 0), vol.ny - 1);
-    const int iz = min(max(__float2int_rd(fmaf(t, vw.z, v0.z)), 0), vol.nz - 1);
-    return vox_index<LAYOUT>(vol, ix, iy, iz);
+    const int ix = floor_pos(fmaf(t, vw.x, v0.x));
+    const int iy = floor_pos(fmaf(t, vw.y, v0.y));
+    const int iz = floor_pos(fmaf(t, vw.z, v0.z));
+    return min(max(vox_index<LAYOUT>(vol, ix, iy, iz), 0), vol.words - 1);
   }
 };
 

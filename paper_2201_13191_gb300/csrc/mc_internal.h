@@ -40,10 +40,16 @@ struct TableView {
 // cube and each 128-byte line a 4x4x2 slab whatever the ray direction.
 enum VoxLayout { VOX_LIN = 0, VOX_BRICK = 1 };
 
+// The packed volume carries a one-voxel border that repeats the edge voxels
+// (padded dims px = nx + 2, ...), so a midpoint that rounding puts a hair
+// outside the box reads the edge voxel, exactly as clamping would, and the
+// march needs no per-axis clamps.
 struct VolumeView {
   const uint32_t* vox;
   int layout;
-  int nbx, nby;  // bricks along x, y (BRICK layout)
+  int nbx, nby;    // bricks along x, y (BRICK layout, padded dims)
+  int px, py, pz;  // padded dims
+  int words;       // words in the packed array (last index + 1)
   int nx, ny, nz;
   float dx, dy, dz;
   float inv_dx, inv_dy, inv_dz;
@@ -106,6 +112,8 @@ cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size
 cudaError_t pack_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, int layout, uint32_t* out,
                         size_t out_words, cudaStream_t s);
 size_t packed_words(int nx, int ny, int nz, int layout);
+// Padded dimensions, brick counts and word count of a packed volume.
+void padded_dims(int nx, int ny, int nz, int layout, VolumeView* v);
 
 // post-processing
 cudaError_t launch_sg_rows(const float* in, float* out, int n_img, int h, int w, const float* coef, int win,
