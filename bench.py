@@ -46,6 +46,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--voxel-layout", type=int, default=0, help="0 default, 1 linear, 2 4^3 bricks")
+    p.add_argument("--workload", default=WORKLOAD, help="ell256 (default) or ell512 (batched angles)")
+    p.add_argument("--angles", type=int, default=1, help="projection angles per step (one launch)")
+    p.add_argument("--per-angle", action="store_true", help="one mc_project call per angle instead of one batch")
+    p.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
@@ -146,11 +151,11 @@ def oracle_rate(tp, wl, n_photons, budget_s):
     return rate, sample, t_primary, t_hist
 
 
-def make_inputs(tables_dir, photons):
+def make_inputs(tables_dir, photons, workload=WORKLOAD):
     from mc_inputs import default_table_path, make_workload, read_tables
 
     tp = default_table_path("full", tables_dir)
-    wl = make_workload(WORKLOAD, read_tables(tp))
+    wl = make_workload(workload, read_tables(tp))
     if photons:
         wl["n_photons"] = int(photons)
     return tp, wl
@@ -161,7 +166,7 @@ def run_reference(args):
     if rank != 0:
         return
     tdir = tempfile.mkdtemp(prefix="mcbench")
-    tp, wl = make_inputs(tdir, args.photons)
+    tp, wl = make_inputs(tdir, args.photons, args.workload)
     import oracle
 
     o = oracle.Oracle(tp)
@@ -185,7 +190,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "volume": "256^3 x 0.5 mm", "detector": "512^2 x 0.4 mm",
+        "config": {"workload": args.workload, "volume": "256^3 x 0.5 mm", "detector": "512^2 x 0.4 mm",
                    "photons_per_projection": N, "step_mm": wl["step_mm"], "n_split": 10,
                    "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -208,18 +213,32 @@ def run_ours(args):
 
     mcx.build()
     tdir = tempfile.mkdtemp(prefix=f"mcbench{rank}")
-    tp, wl = make_inputs(tdir, args.photons)
+    tp, wl = make_inputs(tdir, args.photons, args.workload)
     N = wl["n_photons"]
+    n_ang = max(1, args.angles)
+    angles = (2.0 * np.pi * np.arange(n_ang) / n_ang).astype(np.float32)
     seed = wl["seed"] + 1000 * rank
-    ctx = mcx.Context(local, voxel_layout=args.voxel_layout)
+    ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph))
     ctx.load_tables(tp)
     ctx.setup(wl)
     stream = torch.cuda.current_stream()
-    out = {"primary": ctx.empty_images(1), "scatter": ctx.empty_images(1)}
+    out = {"primary": ctx.empty_images(n_ang), "scatter": ctx.empty_images(n_ang)}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def step(k):
-        return ctx.project([0.0], N, wl["step_mm"], seed + k, out=out, stream=stream)
+        """One step: the projection(s) of all angles, batched or one call per angle."""
+        if not args.per_angle:
+            ctx.project(angles, N, wl["step_mm"], seed + k, out=out, stream=stream)
+            st = ctx.last_stats()
+            return st["transport_ms"], st["flight_steps"] + st["nee_steps"], 3
+        ms, steps = 0.0, 0.0
+        for i in range(n_ang):
+            o = {"primary": out["primary"][i : i + 1], "scatter": out["scatter"][i : i + 1]}
+            ctx.project(angles[i : i + 1], N, wl["step_mm"], seed + k * n_ang + i, out=o, stream=stream)
+            st = ctx.last_stats()
+            ms += st["transport_ms"]
+            steps += st["flight_steps"] + st["nee_steps"]
+        return ms, steps, 3 * n_ang
 
     for k in range(args.warmup):
         step(k)
@@ -231,17 +250,17 @@ def run_ours(args):
 
     clocks = Clocks(device_id(torch, local))
     clocks.start()
-    t_kernel, steps_per, stats = [], [], None
+    t_kernel, steps_per, launches = [], [], 0
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for k in range(args.steps):
-        flush.zero_()  # inputs fit in L2: evict them between steps
-        step(args.warmup + k)
-        stats = ctx.last_stats()
-        t_kernel.append(stats["transport_ms"])
-        steps_per.append(stats["flight_steps"] + stats["nee_steps"])
+        flush.zero_()  # evict the volume from L2 between steps
+        ms, stp, nl = step(args.warmup + k)
+        t_kernel.append(ms)
+        steps_per.append(stp)
+        launches += nl
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -251,32 +270,34 @@ def run_ours(args):
         t = torch.tensor([el_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         el_ms = float(t.item())
-    value = world * N * args.steps / (el_ms / 1e3)
+    value = world * N * n_ang * args.steps / (el_ms / 1e3)
 
     # end to end through the C ABI with host buffers: volume upload from pinned
     # host memory, projection, read-back of both images
     vol = wl["volume"]
-    h_mat = torch.from_numpy(vol["mat"]).pin_memory()
-    h_rho = torch.from_numpy(vol["rho"].view(np.int16)).pin_memory()
-    h_out = torch.empty((2, 1, ctx.nv, ctx.nu), dtype=torch.float32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        ctx.load_volume(h_mat, h_rho, vol["spacing"], stream=stream)
-        ctx.project([0.0], N, wl["step_mm"], seed + 100 + k, out=out, stream=stream)
-        h_out[0].copy_(out["primary"], non_blocking=True)
-        h_out[1].copy_(out["scatter"], non_blocking=True)
+    e2e_value = None
+    h2d = vol["mat"].nbytes + vol["rho"].nbytes + 4 * n_ang + len(wl["weights"]) * 12
+    d2h = 2 * ctx.nu * ctx.nv * 4 * n_ang
+    if not args.no_e2e:
+        h_mat = torch.from_numpy(vol["mat"]).pin_memory()
+        h_rho = torch.from_numpy(vol["rho"].view(np.int16)).pin_memory()
+        h_out = torch.empty((2, n_ang, ctx.nv, ctx.nu), dtype=torch.float32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * N * e2e_steps / e2e_s
-    h2d = vol["mat"].nbytes + vol["rho"].nbytes + 4 + len(wl["weights"]) * 12
-    d2h = 2 * ctx.nu * ctx.nv * 4
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            ctx.load_volume(h_mat, h_rho, vol["spacing"], stream=stream)
+            ctx.project(angles, N, wl["step_mm"], seed + 100 + k, out=out, stream=stream)
+            h_out[0].copy_(out["primary"], non_blocking=True)
+            h_out[1].copy_(out["scatter"], non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = world * N * n_ang * e2e_steps / e2e_s
 
     # roofline of the dominant kernel (transport): FP32 issue
     props = torch.cuda.get_device_properties(local)
@@ -302,16 +323,19 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ellipsoid phantom, Kramers spectrum)",
-            "config": {"workload": WORKLOAD, "volume": "256^3 x 0.5 mm uint8 material + fp16 density",
-                       "detector": "512^2 x 0.4 mm", "photons_per_projection": N, "step_mm": wl["step_mm"],
-                       "n_split": 10, "spectrum": "120 kVp, 111 bins", "l2_flush": True,
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": {"workload": args.workload, "volume": "x".join(map(str, vol["mat"].shape)) + " voxels, uint8 "
+                       "material + fp16 density", "detector": f"{ctx.nu}x{ctx.nv}",
+                       "photons_per_projection": N, "angles_per_step": n_ang,
+                       "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
+                       "step_mm": wl["step_mm"], "n_split": 10, "spectrum": f"{len(wl['weights'])} bins",
+                       "l2_flush": True, "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 3 * args.steps,
+            "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                                   "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
             "clocks": clk,
-            "s_per_projection": el_ms / 1e3 / args.steps,
+            "s_per_projection": el_ms / 1e3 / args.steps / n_ang,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -52,9 +52,11 @@ extern "C" {
 typedef struct mc_ctx mc_ctx;
 
 /* Tally modes for the scatter image (Sec. II-A, eq. Is). */
-#define MC_TALLY_AUTO 0   /* shared-memory histogram when the image fits, else global */
+#define MC_TALLY_AUTO 0   /* the fastest measured mode: currently GLOBAL on every workload */
 #define MC_TALLY_GLOBAL 1 /* every pseudo-particle adds straight into the FP64 image */
-#define MC_TALLY_SHARED 2 /* per-block FP32 shared-memory image, flushed into FP64 */
+#define MC_TALLY_SHARED 2 /* per-block FP32 shared-memory image (warp-combined adds), flushed into
+                             FP64 at block end; needs n_batches x n_angles x nu x nv <= 12288 */
+#define MC_TALLY_WARP 3   /* lanes of a warp hitting the same pixel combine (match + shuffle) first */
 
 typedef struct mc_options {
   int n_split;           /* pseudo-particles per scatter interaction (Sec. II-C.1), default 10 */
@@ -69,6 +71,7 @@ typedef struct mc_options {
   float cubic_a;         /* Keys cubic parameter of the spatial up-sampling, default -0.5 (Sec. II-C.3) */
   int denoise_mode;      /* 0 = Savitzky-Golay, 2 = none */
   int voxel_layout;      /* device volume layout: 0 = default, 1 = x fastest, 2 = 4x4x4 bricks */
+  int use_graph;         /* 1: mc_project replays one captured CUDA graph while its launch shape is unchanged */
 } mc_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -161,6 +164,28 @@ int mc_last_stats(const mc_ctx *ctx, double *out, int n);
  * Errors: INVALID_ARG (sizes, window, unsorted angles), CUDA/OOM. */
 int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_angles, int nu, int nv, float *out,
                        int n_out, const float *out_angles, int NU, int NV, void *stream);
+
+/* Autotuner of the projection (Sec. II-C.2 controllable step; launch shape).
+ * 1. Ray step: primary images (eq. Ip) at step_min and at candidate steps
+ *    between step_max and step_min are compared; the largest step whose image
+ *    stays within step_tol relative L2 of the step_min image is chosen (the
+ *    deterministic primary measures the fixed-step discretisation error).
+ * 2. Launch shape: short transport runs of probe_photons histories per angle
+ *    at the chosen step, over block size {128, 192, 256}, blocks per SM
+ *    {1 .. occupancy} and tally mode {global, warp}; the fastest is kept.
+ * The chosen block_size, blocks_per_sm and tally_mode are written into the
+ * context's options; *out receives them with the step and the measured
+ * histories/s.  Allocates temporary device buffers.  Errors as mc_project. */
+typedef struct mc_tuning {
+  float step_mm;
+  int block_size;
+  int blocks_per_sm;
+  int tally_mode;
+  double histories_per_s;
+  double step_error; /* relative L2 of the chosen step's primary vs step_min */
+} mc_tuning;
+int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t probe_photons, float step_min,
+                float step_max, float step_tol, mc_tuning *out, void *stream);
 
 /* Scatter projection that allocates nothing (no counterpart in the paper: an
  * integration aid).  Some callers cannot allocate device memory once running:

@@ -10,6 +10,7 @@ loaded, every call raises.
 from .binding import (  # noqa: F401
     MCError,
     Options,
+    Tuning,
     Context,
     library,
     library_path,

@@ -32,7 +32,7 @@ STAT_NAMES = [
 EXPORTED = [
     "mc_default_options", "mc_create", "mc_destroy", "mc_set_options", "mc_last_error", "mc_load_tables",
     "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
-    "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static",
+    "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune",
 ]
 
 
@@ -40,6 +40,17 @@ class MCError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class Tuning(C.Structure):
+    _fields_ = [
+        ("step_mm", C.c_float),
+        ("block_size", C.c_int),
+        ("blocks_per_sm", C.c_int),
+        ("tally_mode", C.c_int),
+        ("histories_per_s", C.c_double),
+        ("step_error", C.c_double),
+    ]
 
 
 class Options(C.Structure):
@@ -56,6 +67,7 @@ class Options(C.Structure):
         ("cubic_a", C.c_float),
         ("denoise_mode", C.c_int),
         ("voxel_layout", C.c_int),
+        ("use_graph", C.c_int),
     ]
 
 
@@ -91,6 +103,7 @@ def library():
         L.mc_last_stats.argtypes = [P, C.POINTER(C.c_double), i]
         L.mc_smooth_upsample.argtypes = [P, vp, i, vp, i, i, vp, i, vp, i, i, vp]
         L.mc_project_scatter_static.argtypes = [P, vp, i, u64, f, u64, vp, vp]
+        L.mc_autotune.argtypes = [P, vp, i, u64, f, f, f, C.POINTER(Tuning), vp]
         _lib = L
     return _lib
 
@@ -235,6 +248,34 @@ class Context:
         )
         self._check(rc, allow_limit)
         return out
+
+    def autotune(self, angles, probe_photons, step_min, step_max, step_tol, stream=None, cache=None, cache_key=None):
+        """Run mc_autotune; with cache (a JSON path) and cache_key, reuse an
+        earlier result for the same key instead of tuning again."""
+        import json
+
+        if cache and cache_key and os.path.exists(cache):
+            with open(cache) as f:
+                saved = json.load(f).get(cache_key)
+            if saved:
+                self.set_options(block_size=saved["block_size"], blocks_per_sm=saved["blocks_per_sm"],
+                                 tally_mode=saved["tally_mode"])
+                return saved
+        a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
+        t = Tuning()
+        self._check(self.L.mc_autotune(self.h, _np_ptr(a), len(a), int(probe_photons), float(step_min),
+                                       float(step_max), float(step_tol), C.byref(t), _stream_handle(stream)))
+        self.opt.block_size, self.opt.blocks_per_sm, self.opt.tally_mode = t.block_size, t.blocks_per_sm, t.tally_mode
+        res = {k: getattr(t, k) for k, _ in Tuning._fields_}
+        if cache and cache_key:
+            data = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    data = json.load(f)
+            data[cache_key] = res
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1)
+        return res
 
     def last_stats(self):
         buf = (C.c_double * len(STAT_NAMES))()

@@ -163,6 +163,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   tp.n_batches = 1;
   tp.tally = tally;
   tp.stats = stats;
+  tp.tally_mode = TALLY_GLOBAL;
   const int block = opt.block_size ? opt.block_size : 256;
   const int smem = transport_smem_bytes(tv, nb, block);
   int per_sm = opt.blocks_per_sm;

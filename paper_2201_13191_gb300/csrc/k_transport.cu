@@ -216,6 +216,10 @@ __device__ __forceinline__ float3 rotate(float3 w, float ct, float phi) {
   return make_float3(o.x * in, o.y * in, o.z * in);
 }
 
+__device__ __forceinline__ uint32_t G_npix(const TransportParams& P) {
+  return (uint32_t)P.geo.nu * (uint32_t)P.geo.nv;
+}
+
 // Interaction records queued by the flight phase for the pseudo-particle
 // phase, one slot per thread of the block (structure of arrays).
 struct Records {
@@ -227,15 +231,46 @@ struct Records {
 // One pseudo-particle (eq. Th): random pixel and point in it from the counter
 // block k0 + s of the record's stream, scatter-toward-detector pdf, optional
 // Russian roulette, attenuation march to the panel, FP64 tally.
-template <int LAYOUT>
+// Adds v to the FP64 image at word offset off (see TallyMode).  Lanes that
+// reach this point together (the active mask) and share an offset are combined
+// by a shuffle sum; the lowest lane of each group does the one add.
+// COMBINE = false: one FP64 atomic add per pseudo-particle, no other code
+// (measured fastest on every workload: the tally is one add per ~200 march
+// steps).  COMBINE = true: TALLY_WARP or TALLY_SHARED as selected at run time.
+template <bool COMBINE>
+__device__ __forceinline__ void tally_add(const TransportParams& P, float* s_img, size_t off, float v);
+
+template <>
+__device__ __forceinline__ void tally_add<false>(const TransportParams& P, float*, size_t off, float v) {
+  atomicAdd(P.tally + off, (double)v);
+}
+
+__device__ __noinline__ void tally_combine(const TransportParams& P, float* s_img, size_t off, float v) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, (unsigned long long)off);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  float sum = 0.f;
+  for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
+  if (lane != leader) return;
+  if (P.tally_mode == TALLY_SHARED) atomicAdd(s_img + off, sum);
+  else atomicAdd(P.tally + off, (double)sum);
+}
+
+template <>
+__device__ __forceinline__ void tally_add<true>(const TransportParams& P, float* s_img, size_t off, float v) {
+  tally_combine(P, s_img, off, v);
+}
+
+template <int LAYOUT, bool COMBINE>
 __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
                                                 int r, int s, float* my_mu, int stride, float nee_scale,
-                                                uint32_t npix, size_t img, Counters& C) {
+                                                uint32_t npix, size_t img, Counters& C, float* s_img,
+                                                uint2 key) {
   const VolumeView& V = P.vol;
   const GeomView& G = P.geo;
   const uint32_t hlo = R.hlo[r], hhi = R.hhi[r], a = R.ang[r];
-  const uint4 blk = philox4x32_10(make_uint4(R.k0[r] + (uint32_t)s, a, hlo, hhi),
-                                  make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32)));
+  const uint4 blk = philox4x32_10(make_uint4(R.k0[r] + (uint32_t)s, a, hlo, hhi), key);
   const float va = Rng::u01(blk.y), vb = Rng::u01(blk.z), vr = Rng::u01(blk.w);
   const uint32_t pix = __umulhi(blk.x, npix);
   const uint32_t pi = pix % (uint32_t)G.nu, pj = pix / (uint32_t)G.nu;
@@ -286,7 +321,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   const float tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
   const unsigned long long h = ((unsigned long long)hhi << 32) | hlo;
   const int b = P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0;
-  atomicAdd(P.tally + ((size_t)b * P.n_angles + a) * img + pix, (double)(x0 * __expf(-tp)));
+  tally_add<COMBINE>(P, s_img, ((size_t)b * P.n_angles + a) * img + pix, x0 * __expf(-tp));
 }
 
 #ifndef MC_MIN_BLOCKS
@@ -300,7 +335,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 #endif
 constexpr int kBuckets = 16;
 
-template <int LAYOUT>
+template <int LAYOUT, bool COMBINE>
 __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -327,6 +362,10 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   R.k0 = reinterpret_cast<uint32_t*>(rec + 15 * B);
   R.len = rec + 16 * B;
   int* s_ord = reinterpret_cast<int*>(rec + 17 * B);  // record order for the pseudo-particle phase
+  float* s_img = rec + 18 * B;                         // shared tally image (TALLY_SHARED)
+  const int n_simg =
+      (COMBINE && P.tally_mode == TALLY_SHARED) ? (int)((size_t)P.n_batches * P.n_angles * G_npix(P)) : 0;
+  for (int i = threadIdx.x; i < n_simg; i += B) s_img[i] = 0.f;
 
   const bool staged = stage_bulk(s_blob, P.tab.blob, P.tab.blob_bytes, &bar);
   for (int i = threadIdx.x; i <= nb; i += B) s_pre[i] = P.spec.prefix[i];
@@ -373,7 +412,9 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   float3 x = make_float3(0.f, 0.f, 0.f), w = x;
   float E = 0.f, W = 0.f, cb = 1.f, sb = 0.f;
   Rng g;
-  g.init(0, 0, P.seed);
+  const unsigned long long seed = P.seed_dev ? __ldg(P.seed_dev) : P.seed;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  g.init(0, 0, seed);
 
   for (;;) {
     // ---- flight phase: one free flight per live photon
@@ -388,7 +429,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         else hi = mid - 1;
       }
       E = s_E[lo];
-      g.init(h, (uint32_t)a, P.seed);
+      g.init(h, (uint32_t)a, seed);
       sincosf(__ldg(P.angles + a), &sb, &cb);
       const Pose ps = make_pose(G, __ldg(P.angles + a));
       const float ua = g.u(), ub = g.u();
@@ -537,20 +578,25 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         const int j = base + lane;
         if (j < n_jobs) {
           const int q = j / n_split;
-          pseudo_particle<LAYOUT>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C);
+          pseudo_particle<LAYOUT, COMBINE>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
         }
       }
     }
 #else
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
-      pseudo_particle<LAYOUT>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C);
+      pseudo_particle<LAYOUT, COMBINE>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
     }
 #endif
     const bool more = alive || next < total;
     __syncthreads();
     if (threadIdx.x == 0) s_nrec = 0;
     if (!__syncthreads_or(more)) break;
+  }
+  if (COMBINE && n_simg) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_simg; i += B)
+      if (s_img[i] != 0.f) atomicAdd(P.tally + i, (double)s_img[i]);
   }
   // block-level counter reduction
   __shared__ unsigned long long red[S_NSTAT];
@@ -591,31 +637,33 @@ __global__ void k_finalize(const double* __restrict__ tally, int B, size_t n, fl
 
 }  // namespace
 
-int transport_smem_bytes(const TableView& t, int n_bins, int block) {
-  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 18 * block * 4;
+int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels) {
+  return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 18 * block * 4 + shared_pixels * 4;
 }
 
-cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_transport<VOX_BRICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+namespace {
+template <int LAYOUT, bool COMBINE>
+cudaError_t launch_one(const TransportParams& p, int grid, int block, int smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_transport<LAYOUT, COMBINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN>, block, smem);
+  k_transport<LAYOUT, COMBINE><<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false>, block, smem);
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
-  const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block);
-  cudaError_t e;
-  if (p.vol.layout == VOX_BRICK) {
-    e = cudaFuncSetAttribute(k_transport<VOX_BRICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_transport<VOX_BRICK><<<grid, block, smem, s>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(k_transport<VOX_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_transport<VOX_LIN><<<grid, block, smem, s>>>(p);
-  }
-  return cudaGetLastError();
+  const int simg = p.tally_mode == TALLY_SHARED ? (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv) : 0;
+  const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, simg);
+  const bool combine = p.tally_mode != TALLY_GLOBAL;
+  if (p.vol.layout == VOX_BRICK)
+    return combine ? launch_one<VOX_BRICK, true>(p, grid, block, smem, s) : launch_one<VOX_BRICK, false>(p, grid, block, smem, s);
+  return combine ? launch_one<VOX_LIN, true>(p, grid, block, smem, s) : launch_one<VOX_LIN, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s) {

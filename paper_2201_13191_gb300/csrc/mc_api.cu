@@ -60,6 +60,14 @@ struct mc_ctx {
   size_t post_cap = 0;
   double stats[MC_STAT_N] = {};
   cudaEvent_t ev[4] = {};
+  // pinned host staging (spectrum block + seed, angles, counters) and the
+  // cached CUDA graph of one projection
+  unsigned char* h_pin = nullptr;
+  size_t h_pin_cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  int graph_builds = 0;
 };
 
 namespace {
@@ -99,12 +107,13 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
     return why = "block_size must be 0 or a multiple of 32 in [32, 256]", -1;
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return why = "blocks_per_sm must be in [0, 64]", -1;
-  if (o->tally_mode < 0 || o->tally_mode > 2) return why = "tally_mode must be 0, 1 or 2", -1;
+  if (o->tally_mode < 0 || o->tally_mode > 3) return why = "tally_mode must be 0, 1, 2 or 3", -1;
   if (o->sg_order < 0 || o->sg_window < o->sg_order + 2 || o->sg_window % 2 == 0 || o->sg_window > 31)
     return why = "sg_window must be odd, >= sg_order + 2 and <= 31", -1;
   if (!(o->cubic_a < 0.f && o->cubic_a > -3.f)) return why = "cubic_a must be in (-3, 0)", -1;
   if (o->denoise_mode != 0 && o->denoise_mode != 2) return why = "denoise_mode must be 0 or 2", -1;
   if (o->voxel_layout < 0 || o->voxel_layout > 2) return why = "voxel_layout must be 0, 1 or 2", -1;
+  if (o->use_graph < 0 || o->use_graph > 1) return why = "use_graph must be 0 or 1", -1;
   return 0;
 }
 
@@ -200,8 +209,11 @@ GeomView geom_view(const mc_ctx* c) {
 }
 
 // Stratified counts (largest remainder, at least one photon per non-empty bin)
-// and the device spectrum block.
-int stage_spectrum(mc_ctx* ctx, uint64_t N, cudaStream_t s, SpectrumView& sv) {
+// written into the host block that mirrors the device spectrum block:
+//   seed u64 | prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n]
+size_t spectrum_block_bytes(int n) { return 8 + (size_t)(n + 1) * 8 + (size_t)n * 12; }
+
+int fill_spectrum(mc_ctx* ctx, uint64_t N, uint64_t seed, unsigned char* host) {
   const int n = (int)ctx->S.size();
   std::vector<uint64_t> M(n, 0);
   std::vector<int> elig(n, 0);
@@ -231,9 +243,8 @@ int stage_spectrum(mc_ctx* ctx, uint64_t N, cudaStream_t s, SpectrumView& sv) {
     --rem;
   }
   if (rem) return fail(ctx, MC_ERR_INTERNAL, "stratification did not place every photon");
-  const size_t bytes = (size_t)(n + 1) * 8 + (size_t)n * 12;
-  std::vector<unsigned char> host(bytes);
-  auto* pre = reinterpret_cast<unsigned long long*>(host.data());
+  std::memcpy(host, &seed, 8);
+  auto* pre = reinterpret_cast<unsigned long long*>(host + 8);
   float* en = reinterpret_cast<float*>(pre + n + 1);
   float* wb = en + n;
   float* sn = wb + n;
@@ -244,19 +255,19 @@ int stage_spectrum(mc_ctx* ctx, uint64_t N, cudaStream_t s, SpectrumView& sv) {
     wb[i] = M[i] ? (float)(ctx->S[i] / (double)M[i]) : 0.f;
     sn[i] = (float)ctx->S[i];
   }
-  unsigned char* d = (unsigned char*)ctx->d_spec;
-  cudaError_t e = ensure(d, ctx->d_spec_cap, bytes);
-  ctx->d_spec = d;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum allocation");
-  e = cudaMemcpyAsync(ctx->d_spec, host.data(), bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum upload");
-  unsigned char* base = (unsigned char*)ctx->d_spec;
+  return MC_OK;
+}
+
+SpectrumView spectrum_view(const mc_ctx* ctx) {
+  const int n = (int)ctx->S.size();
+  unsigned char* base = (unsigned char*)ctx->d_spec + 8;
+  SpectrumView sv;
   sv.prefix = reinterpret_cast<const unsigned long long*>(base);
   sv.energy = reinterpret_cast<const float*>(base + (size_t)(n + 1) * 8);
   sv.wbin = sv.energy + n;
   sv.sn = sv.wbin + n;
   sv.n_bins = n;
-  return MC_OK;
+  return sv;
 }
 
 int check_ready(mc_ctx* ctx) {
@@ -272,28 +283,20 @@ int check_ready(mc_ctx* ctx) {
   return MC_OK;
 }
 
-int upload_angles(mc_ctx* ctx, const float* angles, int n, cudaStream_t s) {
-  if (!angles || n < 1) return fail(ctx, MC_ERR_INVALID_ARG, "n_angles must be >= 1 with a host angle array");
-  for (int i = 0; i < n; ++i)
-    if (!std::isfinite(angles[i])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must be finite");
-  if (n > ctx->angles_cap) {
-    if (ctx->d_angles) cudaFree(ctx->d_angles);
-    ctx->d_angles = nullptr;
-    ctx->angles_cap = 0;
-    CK(cudaMalloc((void**)&ctx->d_angles, (size_t)n * 4), "angle allocation");
-    ctx->angles_cap = n;
-  }
-  CK(cudaMemcpyAsync(ctx->d_angles, angles, (size_t)n * 4, cudaMemcpyHostToDevice, s), "angle upload");
-  return MC_OK;
-}
-
-// Shared body of mc_project / mc_project_histories.
+// Shared body of mc_project / mc_project_histories.  Inputs are staged in a
+// pinned host buffer and the whole projection is one enqueue sequence: spectrum
+// block (with the seed) and angles to the device, counter and tally resets,
+// primary, transport, finalize, counters back.  With opt.use_graph the sequence
+// is captured once into a CUDA graph and replayed while its launch shape
+// (sizes, pointers, options) stays the same; the seed is read on the device, so
+// one graph serves every seed.
 int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uint64_t h_begin, uint64_t h_count,
                  float step, uint64_t seed, float* primary_out, float* scatter_out, float* var_out, void* stream) {
   int rc = check_ready(ctx);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();  // a failed call elsewhere must not be blamed on this one
   if (!(step > 0.f) || !std::isfinite(step)) return fail(ctx, MC_ERR_INVALID_ARG, "step_mm must be > 0");
   {
     // bound the steps of one march: the longest chord is the volume diagonal
@@ -304,20 +307,53 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
   if (N < 1) return fail(ctx, MC_ERR_INVALID_ARG, "n_photons must be >= 1");
   if (h_begin > N || h_count > N - h_begin) return fail(ctx, MC_ERR_INVALID_ARG, "history range outside the run");
   if (var_out && ctx->opt.n_batches < 2) return fail(ctx, MC_ERR_INVALID_ARG, "scatter_var_out needs n_batches >= 2");
+  if (!angles || n_angles < 1) return fail(ctx, MC_ERR_INVALID_ARG, "n_angles must be >= 1 with a host angle array");
+  for (int i = 0; i < n_angles; ++i)
+    if (!std::isfinite(angles[i])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must be finite");
   const int nb_img = var_out ? ctx->opt.n_batches : 1;
   rc = stage_tables(ctx);
   if (rc) return rc;
-  SpectrumView sv;
-  rc = stage_spectrum(ctx, N, s, sv);
-  if (rc) return rc;
-  rc = upload_angles(ctx, angles, n_angles, s);
-  if (rc) return rc;
-  for (double& v : ctx->stats) v = 0;
   const size_t img = (size_t)ctx->nu * ctx->nv * n_angles;
-  CK(cudaMemsetAsync(ctx->d_stats, 0, S_NSTAT * 8, s), "stats reset");
-  float ms_t = 0, ms_p = 0;
+
+  // ---- buffers (allocated before any capture)
+  const int nbins = (int)ctx->S.size();
+  const size_t spec_bytes = spectrum_block_bytes(nbins);
+  const size_t ang_off = (spec_bytes + 255) / 256 * 256;
+  const size_t st_off = (ang_off + (size_t)n_angles * 4 + 255) / 256 * 256;
+  const size_t pin_bytes = st_off + S_NSTAT * 8;
+  if (pin_bytes > ctx->h_pin_cap) {
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    ctx->h_pin = nullptr;
+    ctx->h_pin_cap = 0;
+    CK(cudaMallocHost((void**)&ctx->h_pin, pin_bytes), "pinned staging allocation");
+    ctx->h_pin_cap = pin_bytes;
+  }
+  {
+    unsigned char* d = (unsigned char*)ctx->d_spec;
+    CK(ensure(d, ctx->d_spec_cap, spec_bytes), "spectrum allocation");
+    ctx->d_spec = d;
+  }
+  if (n_angles > ctx->angles_cap) {
+    if (ctx->d_angles) cudaFree(ctx->d_angles);
+    ctx->d_angles = nullptr;
+    ctx->angles_cap = 0;
+    CK(cudaMalloc((void**)&ctx->d_angles, (size_t)n_angles * 4), "angle allocation");
+    ctx->angles_cap = n_angles;
+  }
+  if (scatter_out) CK(ensure(ctx->d_tally, ctx->tally_cap, img * nb_img), "tally allocation");
+  // the previous call synchronised its stream, so the pinned buffer is free
+  rc = fill_spectrum(ctx, N, seed, ctx->h_pin);
+  if (rc) return rc;
+  std::memcpy(ctx->h_pin + ang_off, angles, (size_t)n_angles * 4);
+  const SpectrumView sv = spectrum_view(ctx);
+
+  // ---- kernel parameters (zeroed first: they also form the graph key)
+  PrimaryParams pp;
+  TransportParams tp;
+  std::memset(&pp, 0, sizeof(pp));
+  std::memset((void*)&tp, 0, sizeof(tp));
+  int grid = 0, block = 0;
   if (primary_out) {
-    PrimaryParams pp;
     pp.tab = table_view(ctx);
     pp.vol = volume_view(ctx);
     pp.geo = geom_view(ctx);
@@ -326,14 +362,8 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     pp.n_angles = n_angles;
     pp.step = step;
     pp.out = primary_out;
-    CK(cudaEventRecord(ctx->ev[2], s), "event");
-    CK(launch_primary(pp, s), "primary launch");
-    CK(cudaEventRecord(ctx->ev[3], s), "event");
   }
   if (scatter_out) {
-    CK(ensure(ctx->d_tally, ctx->tally_cap, img * nb_img), "tally allocation");
-    CK(cudaMemsetAsync(ctx->d_tally, 0, img * nb_img * sizeof(double), s), "tally reset");
-    TransportParams tp;
     tp.tab = table_view(ctx);
     tp.vol = volume_view(ctx);
     tp.geo = geom_view(ctx);
@@ -344,15 +374,27 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     tp.h_begin = h_begin;
     tp.h_count = h_count;
     tp.step = step;
-    tp.seed = seed;
+    tp.seed = 0;
+    tp.seed_dev = reinterpret_cast<const unsigned long long*>(ctx->d_spec);
     tp.n_split = ctx->opt.n_split;
     tp.rr_threshold = ctx->opt.rr_threshold;
     tp.max_order = ctx->opt.max_scatter_order;
     tp.n_batches = nb_img;
     tp.tally = ctx->d_tally;
     tp.stats = ctx->d_stats;
-    const int block = ctx->opt.block_size ? ctx->opt.block_size : 256;
-    const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block);
+    const size_t tally_pixels = img * nb_img;
+    if (ctx->opt.tally_mode == MC_TALLY_SHARED) {
+      if (tally_pixels > (size_t)kSharedTallyMaxPixels)
+        return fail(ctx, MC_ERR_INVALID_ARG, "tally_mode SHARED needs n_batches x n_angles x nu x nv <= 12288");
+      tp.tally_mode = TALLY_SHARED;
+    } else if (ctx->opt.tally_mode == MC_TALLY_WARP) {
+      tp.tally_mode = TALLY_WARP;
+    } else {
+      // automatic and global: plain FP64 adds, measured fastest even on an 8 x 8 panel
+      tp.tally_mode = TALLY_GLOBAL;
+    }
+    block = ctx->opt.block_size ? ctx->opt.block_size : 256;
+    const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, tp.tally_mode == TALLY_SHARED ? (int)tally_pixels : 0);
     int per_sm = ctx->opt.blocks_per_sm;
     if (per_sm == 0) {
       CK(transport_occupancy(block, smem, &per_sm), "occupancy query");
@@ -360,17 +402,71 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     }
     const unsigned long long work = (unsigned long long)n_angles * h_count;
     const unsigned long long need = (work + block - 1) / block;
-    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(need, (unsigned long long)ctx->sm_count * per_sm));
-    CK(cudaEventRecord(ctx->ev[0], s), "event");
-    if (work > 0) CK(launch_transport(tp, grid, block, s), "transport launch");
-    CK(cudaEventRecord(ctx->ev[1], s), "event");
-    CK(launch_finalize(ctx->d_tally, nb_img, img, scatter_out, var_out, s), "finalize launch");
+    grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(need, (unsigned long long)ctx->sm_count * per_sm));
+    if (work == 0) grid = 0;
   }
-  unsigned long long st[S_NSTAT] = {};
-  CK(cudaMemcpyAsync(st, ctx->d_stats, S_NSTAT * 8, cudaMemcpyDeviceToHost, s), "stats readback");
+
+  // ---- the enqueue sequence
+  unsigned long long* h_st = reinterpret_cast<unsigned long long*>(ctx->h_pin + st_off);
+  // under capture an event record must be an external record node to time the replay
+  auto record = [&](cudaEvent_t ev, cudaStream_t q, bool capture) {
+    return cudaEventRecordWithFlags(ev, q, capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+  };
+  auto enqueue = [&](cudaStream_t q, bool capture) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_spec, ctx->h_pin, spec_bytes, cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_angles, ctx->h_pin + ang_off, (size_t)n_angles * 4, cudaMemcpyHostToDevice, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_stats, 0, S_NSTAT * 8, q);
+    if (e == cudaSuccess && primary_out) {
+      e = record(ctx->ev[2], q, capture);
+      if (e == cudaSuccess) e = launch_primary(pp, q);
+      if (e == cudaSuccess) e = record(ctx->ev[3], q, capture);
+    }
+    if (e == cudaSuccess && scatter_out) {
+      e = cudaMemsetAsync(ctx->d_tally, 0, img * nb_img * sizeof(double), q);
+      if (e == cudaSuccess) e = record(ctx->ev[0], q, capture);
+      if (e == cudaSuccess && grid > 0) e = launch_transport(tp, grid, block, q);
+      if (e == cudaSuccess) e = record(ctx->ev[1], q, capture);
+      if (e == cudaSuccess) e = launch_finalize(ctx->d_tally, nb_img, img, scatter_out, var_out, q);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_st, ctx->d_stats, S_NSTAT * 8, cudaMemcpyDeviceToHost, q);
+    return e;
+  };
+  if (ctx->opt.use_graph) {
+    // graph key: every parameter and size the captured sequence depends on
+    std::vector<unsigned char> key(sizeof(pp) + sizeof(tp) + 64);
+    std::memcpy(key.data(), &pp, sizeof(pp));
+    std::memcpy(key.data() + sizeof(pp), (const void*)&tp, sizeof(tp));
+    const uint64_t extra[8] = {(uint64_t)grid, (uint64_t)block, (uint64_t)nb_img, (uint64_t)img, (uint64_t)(uintptr_t)var_out,
+                               (uint64_t)(uintptr_t)scatter_out, (uint64_t)(uintptr_t)ctx->h_pin, (uint64_t)spec_bytes};
+    std::memcpy(key.data() + sizeof(pp) + sizeof(tp), extra, 64);
+    if (!ctx->graph_exec || key != ctx->graph_key) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+      CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+      const cudaError_t e = enqueue(ctx->cap_stream, true);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture");
+      }
+      const cudaError_t e3 = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "graph instantiate");
+      ctx->graph_key.swap(key);
+      ++ctx->graph_builds;
+    }
+    CK(cudaGraphLaunch(ctx->graph_exec, s), "graph launch");
+  } else {
+    CK(enqueue(s, false), "projection enqueue");
+  }
   CK(cudaStreamSynchronize(s), "stream synchronize");
+  float ms_t = 0, ms_p = 0;
   if (scatter_out) CK(cudaEventElapsedTime(&ms_t, ctx->ev[0], ctx->ev[1]), "event time");
   if (primary_out) CK(cudaEventElapsedTime(&ms_p, ctx->ev[2], ctx->ev[3]), "event time");
+  unsigned long long st[S_NSTAT];
+  std::memcpy(st, h_st, sizeof(st));
   const int map[10] = {S_HIST, S_FLIGHT_STEPS, S_NEE_STEPS, S_NEE_RAYS, S_PHOTO, S_COMPTON, S_RAYLEIGH, S_ESCAPE, S_LIMIT, S_SAMPLER_FAIL};
   for (int i = 0; i < 10; ++i) ctx->stats[i] = (double)st[map[i]];
   ctx->stats[10] = ms_t;
@@ -445,6 +541,7 @@ void mc_default_options(mc_options* o) {
   o->cubic_a = -0.5f;
   o->denoise_mode = 0;
   o->voxel_layout = 0;
+  o->use_graph = 0;
 }
 
 int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {
@@ -487,6 +584,9 @@ void mc_destroy(mc_ctx* ctx) {
   cudaFree(ctx->d_post);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   delete ctx;
 }
 
@@ -577,6 +677,7 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
   if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
     return fail(ctx, MC_ERR_INVALID_ARG, "volume dimension above 2^20");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)stream;
   if (!is_device_ptr) {
     // host data: validate here
@@ -683,6 +784,109 @@ int mc_project_histories(mc_ctx* ctx, const float* angles, int n_angles, uint64_
                       nullptr, stream);
 }
 
+int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, float step_min, float step_max,
+                float step_tol, mc_tuning* out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (!out || !angles || n_angles < 1 || probe < 1 || !(step_min > 0.f) || !(step_max >= step_min) || !(step_tol > 0.f))
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad autotune arguments");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t n = (size_t)ctx->nu * ctx->nv * n_angles;
+  float *d_ref = nullptr, *d_img = nullptr;
+  CK(cudaMalloc((void**)&d_ref, n * 4), "autotune allocation");
+  cudaError_t e = cudaMalloc((void**)&d_img, n * 4);
+  if (e != cudaSuccess) {
+    cudaFree(d_ref);
+    return cuda_fail(ctx, e, "autotune allocation");
+  }
+  std::vector<float> ref(n), img(n);
+  auto finish = [&](int code) {
+    cudaFree(d_ref);
+    cudaFree(d_img);
+    return code;
+  };
+  // 1. largest step within tolerance of the finest
+  rc = project_impl(ctx, angles, n_angles, 1, 0, 1, step_min, 1, d_ref, nullptr, nullptr, stream);
+  if (rc) return finish(rc);
+  e = cudaMemcpy(ref.data(), d_ref, n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "autotune readback"));
+  double rn = 0;
+  for (float v : ref) rn += (double)v * v;
+  float best_step = step_min;
+  double best_err = 0;
+  const int n_cand = 8;
+  for (int c = 0; c < n_cand; ++c) {
+    const float st = step_max * std::pow(step_min / step_max, (float)c / (n_cand - 1));
+    if (st <= step_min) break;
+    rc = project_impl(ctx, angles, n_angles, 1, 0, 1, st, 1, d_img, nullptr, nullptr, stream);
+    if (rc) return finish(rc);
+    e = cudaMemcpy(img.data(), d_img, n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "autotune readback"));
+    double dn = 0;
+    for (size_t i = 0; i < n; ++i) dn += ((double)img[i] - ref[i]) * ((double)img[i] - ref[i]);
+    const double err = rn > 0 ? std::sqrt(dn / rn) : 0;
+    if (err <= step_tol) {
+      best_step = st;
+      best_err = err;
+      break;
+    }
+  }
+  // 2. launch shape at the chosen step
+  const mc_options saved = ctx->opt;
+  int smem = 0, max_per_sm = 1;
+  {
+    const TableView tv = table_view(ctx);
+    smem = transport_smem_bytes(tv, (int)ctx->S.size(), 256, 0);
+    e = transport_occupancy(256, smem, &max_per_sm);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "occupancy query"));
+  }
+  double best_rate = -1;
+  mc_options best = saved;
+  const int blocks[3] = {128, 192, 256};
+  const int tallies[2] = {MC_TALLY_GLOBAL, MC_TALLY_WARP};
+  for (int bi = 0; bi < 3; ++bi) {
+    int occ = 1;
+    e = transport_occupancy(blocks[bi], transport_smem_bytes(table_view(ctx), (int)ctx->S.size(), blocks[bi], 0), &occ);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "occupancy query"));
+    for (int per = 1; per <= std::max(1, occ); ++per) {
+      for (int ti = 0; ti < 2; ++ti) {
+        ctx->opt = saved;
+        ctx->opt.block_size = blocks[bi];
+        ctx->opt.blocks_per_sm = per;
+        ctx->opt.tally_mode = tallies[ti];
+        ctx->opt.use_graph = 0;
+        double ms = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+          rc = project_impl(ctx, angles, n_angles, probe, 0, probe, best_step, 7 + rep, nullptr, d_img, nullptr, stream);
+          if (rc && rc != MC_ERR_LIMIT) {
+            ctx->opt = saved;
+            return finish(rc);
+          }
+          ms = std::min(ms, ctx->stats[10]);
+        }
+        const double rate = (double)probe * n_angles / (ms / 1e3);
+        if (rate > best_rate) {
+          best_rate = rate;
+          best = ctx->opt;
+        }
+      }
+    }
+  }
+  ctx->opt = saved;
+  ctx->opt.block_size = best.block_size;
+  ctx->opt.blocks_per_sm = best.blocks_per_sm;
+  ctx->opt.tally_mode = best.tally_mode;
+  out->step_mm = best_step;
+  out->block_size = best.block_size;
+  out->blocks_per_sm = best.blocks_per_sm;
+  out->tally_mode = best.tally_mode;
+  out->histories_per_s = best_rate;
+  out->step_error = best_err;
+  (void)max_per_sm;
+  return finish(MC_OK);
+}
+
 int mc_last_stats(const mc_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0 || n > MC_STAT_N) return MC_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) out[i] = ctx->stats[i];
@@ -729,6 +933,7 @@ int mc_smooth_upsample(mc_ctx* ctx, const float* in, int n_in, const float* in_a
     fa[o] = (float)((th - lo) / (hi - lo));
   }
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nimg = (size_t)n_in * nu * nv;
   const size_t meta = (size_t)win * win + 3 * (size_t)n_out + 64;

@@ -85,7 +85,20 @@ struct TransportParams {
   int n_batches;
   double* tally;                 // [n_batches][n_angles][nv][nu]
   unsigned long long* stats;     // [S_NSTAT]
+  int tally_mode = 0;            // TALLY_* below
+  // when set, the Philox key is read from device memory at kernel start (a
+  // captured graph then serves every seed); otherwise `seed` is used
+  const unsigned long long* seed_dev = nullptr;
 };
+
+// How pseudo-particle scores reach the FP64 image (eq. Is):
+//   TALLY_GLOBAL  one FP64 atomic add per pseudo-particle;
+//   TALLY_WARP    lanes of a warp that hit the same pixel first combine
+//                 their scores (match + shuffle), one atomic per pixel group;
+//   TALLY_SHARED  a per-block FP32 image in shared memory (warp-combined adds),
+//                 flushed into the FP64 image once at the end of the block.
+enum TallyMode { TALLY_GLOBAL = 0, TALLY_WARP = 1, TALLY_SHARED = 2 };
+constexpr int kSharedTallyMaxPixels = 12288;  // 48 KB of FP32 per block
 
 struct PrimaryParams {
   TableView tab;
@@ -100,7 +113,7 @@ struct PrimaryParams {
 
 // launch wrappers (return cudaError_t of the launch)
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
-int transport_smem_bytes(const TableView& t, int n_bins, int block);
+int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels = 0);
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);

@@ -192,6 +192,52 @@ def test_voxel_layouts_agree(gpu, table_path, tables):
     np.testing.assert_allclose(imgs[0]["scatter"], imgs[1]["scatter"], rtol=1e-5, atol=1e-12)
 
 
+@pytest.mark.parametrize("mode", [2, 3])
+def test_tally_modes_agree(gpu, table_path, tables, mode):
+    """Global FP64 adds, the shared-memory image and warp-combined adds give
+    the same scatter image up to summation order."""
+    wl = make_workload("tiny8", tables)
+    ref = _ctx(gpu, table_path, wl, tally_mode=1).project([0.4, 1.1], 100_000, 0.5, 2, primary=False)["scatter"]
+    got = _ctx(gpu, table_path, wl, tally_mode=mode).project([0.4, 1.1], 100_000, 0.5, 2, primary=False)["scatter"]
+    np.testing.assert_allclose(got.cpu().numpy(), ref.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    if mode == 2:
+        big = _ctx(gpu, table_path, make_workload("cyl64", tables), tally_mode=2)
+        with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+            big.project([0.0], 1000, 0.5, 1, primary=False)  # 128^2 pixels do not fit
+
+
+def test_graph_replay_matches_direct_launches(gpu, table_path, tables):
+    """The captured CUDA graph replays the same projection: one graph serves
+    every seed (the seed is read on the device), and a changed launch shape
+    is captured anew."""
+    wl = make_workload("cyl64", tables)
+    angles = np.array([0.2, 2.9], np.float32)
+    direct = _ctx(gpu, table_path, wl)
+    graph = _ctx(gpu, table_path, wl, use_graph=1)
+    outs = {"primary": graph.empty_images(2), "scatter": graph.empty_images(2)}
+    for seed, n in ((3, 60_000), (4, 60_000), (5, 30_000)):
+        ref = direct.project(angles, n, 0.5, seed)
+        got = graph.project(angles, n, 0.5, seed, out=outs)
+        np.testing.assert_array_equal(got["primary"].cpu().numpy(), ref["primary"].cpu().numpy())
+        np.testing.assert_allclose(got["scatter"].cpu().numpy(), ref["scatter"].cpu().numpy(), rtol=1e-5, atol=1e-12)
+        assert graph.last_stats()["histories"] == 2 * n
+
+
+def test_autotune_picks_a_valid_configuration(gpu, table_path, tables, tmp_path):
+    wl = make_workload("cyl64", tables)
+    c = _ctx(gpu, table_path, wl)
+    ref = c.project([0.5], 100_000, 0.25, 9, primary=False)["scatter"].cpu().numpy()
+    res = c.autotune([0.0, 1.0], 200_000, 0.1, 0.8, 5e-3, cache=str(tmp_path / "tune.json"), cache_key="cyl64")
+    assert 0.1 <= res["step_mm"] <= 0.8 + 1e-6 and res["step_error"] <= 5e-3
+    assert res["block_size"] in (128, 192, 256) and res["blocks_per_sm"] >= 1 and res["histories_per_s"] > 0
+    # the tuned launch shape computes the same image
+    got = c.project([0.5], 100_000, 0.25, 9, primary=False)["scatter"].cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-12)
+    # a second context reuses the cached result
+    c2 = _ctx(gpu, table_path, wl)
+    assert c2.autotune([0.0], 10, 0.1, 0.8, 5e-3, cache=str(tmp_path / "tune.json"), cache_key="cyl64") == res
+
+
 def test_deterministic_up_to_fp64_sum_order(gpu, table_path, tables):
     wl = make_workload("cyl64", tables)
     c = _ctx(gpu, table_path, wl)
