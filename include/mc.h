@@ -69,8 +69,9 @@ typedef struct mc_options {
   int sg_window;         /* Savitzky-Golay window (odd, >= order + 2), default 9 (Sec. II-C.4) */
   int sg_order;          /* Savitzky-Golay polynomial order, default 3 (Sec. II-C.4) */
   float cubic_a;         /* Keys cubic parameter of the spatial up-sampling, default -0.5 (Sec. II-C.3) */
-  int denoise_mode;      /* 0 = Savitzky-Golay, 2 = none */
-  int voxel_layout;      /* device volume layout: 0 = default, 1 = x fastest, 2 = 4x4x4 bricks */
+  int denoise_mode;      /* 0 = Savitzky-Golay, 1 = learned denoiser (mc_denoise_*), 2 = none */
+  int voxel_layout;      /* device volume layout: 1 = x fastest, 2 = 4x4x4 Morton bricks, 0 = default:
+                            x fastest while the packed volume fits in 3/4 of L2, bricks beyond */
   int use_graph;         /* 1: mc_project replays one captured CUDA graph while its launch shape is unchanged */
 } mc_options;
 
@@ -164,6 +165,46 @@ int mc_last_stats(const mc_ctx *ctx, double *out, int n);
  * Errors: INVALID_ARG (sizes, window, unsorted angles), CUDA/OOM. */
 int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_angles, int nu, int nv, float *out,
                        int n_out, const float *out_angles, int NU, int NV, void *stream);
+
+/* Learned scatter denoiser (replaces the Savitzky-Golay smoothing of
+ * Sec. II-C.4 at low photon counts; no counterpart network in the paper): a
+ * residual U-Net, 4 levels, 32 base channels, 3x3 convolutions, 2x2 max
+ * pooling, nearest up-sampling with concatenated skips, BF16 weights and
+ * activations, FP32 accumulation on the tcgen05 tensor cores, Adam.  Images
+ * are normalised by their mean; the network predicts a residual.
+ *   mc_denoise_init: allocate for height x width images (multiples of 16) and
+ *     up to max_batch images per call; seeded He initialisation.
+ *   mc_denoise_train_step: one Adam step (lr; lr = 0 computes gradients only)
+ *     on n device FP32 image pairs [n][height][width]; *loss = mean squared
+ *     error of the normalised images before the step.
+ *   mc_denoise_infer: n device FP32 images in, denoised images out (any n).
+ *   mc_denoise_get_layer / set_layer: host FP32 weights [cout][9][cin], biases
+ *     [cout] and last gradients of layer 0..14 (nullable pointers).
+ *   mc_denoise_save / load: FP32 checkpoint file.
+ * Errors: STATE (not initialised), INVALID_ARG, CUDA/OOM, TIMEOUT, IO. */
+int mc_denoise_init(mc_ctx *ctx, int height, int width, int max_batch, uint64_t seed);
+int mc_denoise_train_step(mc_ctx *ctx, const float *noisy, const float *clean, int n, float lr, float *loss,
+                          void *stream);
+int mc_denoise_infer(mc_ctx *ctx, const float *in, float *out, int n, void *stream);
+int mc_denoise_get_layer(mc_ctx *ctx, int layer, float *w, float *b, float *gw, float *gb, int *cin, int *cout);
+int mc_denoise_set_layer(mc_ctx *ctx, int layer, const float *w, const float *b);
+int mc_denoise_save(mc_ctx *ctx, const char *path);
+int mc_denoise_load(mc_ctx *ctx, const char *path, int max_batch);
+
+/* Denoiser convolution primitives on the tcgen05 tensor cores (device
+ * pointers, NHWC, BF16 stored as uint16, cin and cout multiples of 16,
+ * cout <= 256), enqueued on `stream` without synchronising:
+ *   mc_nn_conv3x3: y = relu?(conv3x3_same(x, w) + bias); w [cout][9][cin]
+ *     (tap = 3 (dy+1) + (dx+1)), bias FP32 [cout] or NULL, y BF16 or FP32
+ *     (out_f32) [n][h][w][cout];
+ *   mc_nn_conv3x3_wgrad: dw[cout][9][cin] (FP32, accumulated: zero it first)
+ *     += sum over pixels of dy[p][co] x[p shifted by tap][ci], pixels split
+ *     over `splits` CTA groups.
+ * *err (device int) is set to 1 if a bounded wait gave up. */
+int mc_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int n, int h, int wd, int cin, int cout,
+                  int relu, int out_f32, int *err, void *stream);
+int mc_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, int n, int h, int wd, int cin, int cout, int splits,
+                        int *err, void *stream);
 
 /* Autotuner of the projection (Sec. II-C.2 controllable step; launch shape).
  * 1. Ray step: primary images (eq. Ip) at step_min and at candidate steps

@@ -15,5 +15,7 @@ from .binding import (  # noqa: F401
     library,
     library_path,
     STAT_NAMES,
+    conv3x3,
+    conv3x3_wgrad,
 )
 from .build import build  # noqa: F401

@@ -32,7 +32,9 @@ STAT_NAMES = [
 EXPORTED = [
     "mc_default_options", "mc_create", "mc_destroy", "mc_set_options", "mc_last_error", "mc_load_tables",
     "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
-    "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune",
+    "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
+    "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
+    "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad",
 ]
 
 
@@ -104,6 +106,17 @@ def library():
         L.mc_smooth_upsample.argtypes = [P, vp, i, vp, i, i, vp, i, vp, i, i, vp]
         L.mc_project_scatter_static.argtypes = [P, vp, i, u64, f, u64, vp, vp]
         L.mc_autotune.argtypes = [P, vp, i, u64, f, f, f, C.POINTER(Tuning), vp]
+        fp = C.POINTER(C.c_float)
+        ip = C.POINTER(C.c_int)
+        L.mc_denoise_init.argtypes = [P, i, i, i, u64]
+        L.mc_denoise_train_step.argtypes = [P, vp, vp, i, f, fp, vp]
+        L.mc_denoise_infer.argtypes = [P, vp, vp, i, vp]
+        L.mc_denoise_get_layer.argtypes = [P, i, vp, vp, vp, vp, ip, ip]
+        L.mc_denoise_set_layer.argtypes = [P, i, vp, vp]
+        L.mc_denoise_save.argtypes = [P, C.c_char_p]
+        L.mc_denoise_load.argtypes = [P, C.c_char_p, i]
+        L.mc_nn_conv3x3.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, i, vp, vp]
+        L.mc_nn_conv3x3_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
         _lib = L
     return _lib
 
@@ -114,6 +127,43 @@ def _np_ptr(a):
 
 def _t_ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def conv3x3(x, w, bias=None, relu=False, out_f32=True, stream=None):
+    """Tensor-core 3x3 convolution (mc_nn_conv3x3): x BF16 [n][h][w][cin] (torch.bfloat16 on the device),
+    w BF16 [cout][9][cin], bias FP32 [cout] or None; returns FP32 or BF16 [n][h][w][cout]."""
+    import torch
+
+    n, h, wd, cin = x.shape
+    cout = w.shape[0]
+    y = torch.empty((n, h, wd, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    rc = library().mc_nn_conv3x3(_t_ptr(x.contiguous()), _t_ptr(w.contiguous()), _t_ptr(bias), _t_ptr(y), n, h, wd,
+                                 cin, cout, int(relu), int(out_f32), _t_ptr(err), _stream_handle(stream))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_nn_conv3x3 failed")
+    torch.cuda.synchronize()
+    if int(err.item()):
+        raise MCError(-5, "a tensor-core wait gave up")
+    return y
+
+
+def conv3x3_wgrad(x, dy, splits=8, stream=None):
+    """Weight gradient on the tensor cores (mc_nn_conv3x3_wgrad): FP32 [cout][9][cin]."""
+    import torch
+
+    n, h, wd, cin = x.shape
+    cout = dy.shape[-1]
+    dw = torch.zeros((cout, 9, cin), dtype=torch.float32, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    rc = library().mc_nn_conv3x3_wgrad(_t_ptr(x.contiguous()), _t_ptr(dy.contiguous()), _t_ptr(dw), n, h, wd, cin,
+                                       cout, splits, _t_ptr(err), _stream_handle(stream))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_nn_conv3x3_wgrad failed")
+    torch.cuda.synchronize()
+    if int(err.item()):
+        raise MCError(-5, "a tensor-core wait gave up")
+    return dw
 
 
 def _stream_handle(stream):
@@ -276,6 +326,48 @@ class Context:
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1)
         return res
+
+    # ---- learned denoiser
+    def denoise_init(self, height, width, max_batch, seed=0):
+        self._check(self.L.mc_denoise_init(self.h, height, width, max_batch, seed))
+
+    def denoise_train_step(self, noisy, clean, lr, stream=None):
+        """noisy, clean: device FP32 [n][h][w]; returns the batch loss before the step."""
+        loss = C.c_float()
+        n = noisy.shape[0]
+        self._check(self.L.mc_denoise_train_step(self.h, _t_ptr(noisy.contiguous()), _t_ptr(clean.contiguous()), n,
+                                                 float(lr), C.byref(loss), _stream_handle(stream)))
+        return loss.value
+
+    def denoise_infer(self, images, out=None, stream=None):
+        images = images.contiguous()
+        if out is None:
+            out = self.torch.empty_like(images)
+        self._check(self.L.mc_denoise_infer(self.h, _t_ptr(images), _t_ptr(out), images.shape[0],
+                                            _stream_handle(stream)))
+        return out
+
+    def denoise_layer(self, i):
+        ci, co = C.c_int(), C.c_int()
+        self._check(self.L.mc_denoise_get_layer(self.h, i, None, None, None, None, C.byref(ci), C.byref(co)))
+        w = np.zeros((co.value, 9, ci.value), np.float32)
+        b = np.zeros(co.value, np.float32)
+        gw = np.zeros_like(w)
+        gb = np.zeros_like(b)
+        self._check(self.L.mc_denoise_get_layer(self.h, i, _np_ptr(w), _np_ptr(b), _np_ptr(gw), _np_ptr(gb),
+                                                C.byref(ci), C.byref(co)))
+        return w, b, gw, gb
+
+    def denoise_set_layer(self, i, w, b):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        self._check(self.L.mc_denoise_set_layer(self.h, i, _np_ptr(w), _np_ptr(b)))
+
+    def denoise_save(self, path):
+        self._check(self.L.mc_denoise_save(self.h, str(path).encode()))
+
+    def denoise_load(self, path, max_batch=16):
+        self._check(self.L.mc_denoise_load(self.h, str(path).encode(), max_batch))
 
     def last_stats(self):
         buf = (C.c_double * len(STAT_NAMES))()

@@ -68,6 +68,7 @@ struct mc_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
   int graph_builds = 0;
+  Denoiser* denoiser = nullptr;  // learned denoiser (mc_denoise_*)
 };
 
 namespace {
@@ -111,7 +112,7 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->sg_order < 0 || o->sg_window < o->sg_order + 2 || o->sg_window % 2 == 0 || o->sg_window > 31)
     return why = "sg_window must be odd, >= sg_order + 2 and <= 31", -1;
   if (!(o->cubic_a < 0.f && o->cubic_a > -3.f)) return why = "cubic_a must be in (-3, 0)", -1;
-  if (o->denoise_mode != 0 && o->denoise_mode != 2) return why = "denoise_mode must be 0 or 2", -1;
+  if (o->denoise_mode < 0 || o->denoise_mode > 2) return why = "denoise_mode must be 0, 1 or 2", -1;
   if (o->voxel_layout < 0 || o->voxel_layout > 2) return why = "voxel_layout must be 0, 1 or 2", -1;
   if (o->use_graph < 0 || o->use_graph > 1) return why = "use_graph must be 0 or 1", -1;
   return 0;
@@ -586,6 +587,7 @@ void mc_destroy(mc_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  denoiser_destroy(ctx->denoiser);
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   delete ctx;
 }
@@ -719,7 +721,14 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
       return fail(ctx, MC_ERR_INVALID_ARG, "volume holds an unknown material id or an invalid density");
     }
   }
-  const int layout = ctx->opt.voxel_layout == 2 ? VOX_BRICK : VOX_LIN;
+  // default layout: x fastest while the packed volume fits in 3/4 of L2 (measured faster there);
+  // 4^3 bricks once it streams from HBM (every ray direction then reuses its sectors)
+  int layout = ctx->opt.voxel_layout == 2 ? VOX_BRICK : VOX_LIN;
+  if (ctx->opt.voxel_layout == 0) {
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device), "L2 size query");
+    if ((double)packed_words(nx, ny, nz, VOX_LIN) * 4.0 > 0.75 * (double)l2) layout = VOX_BRICK;
+  }
   const size_t words = packed_words(nx, ny, nz, layout);
   e = ensure(ctx->d_vox, ctx->vox_cap, words);
   if (e == cudaSuccess) e = pack_volume(st_mat, st_rho, nx, ny, nz, layout, ctx->d_vox, words, s);
@@ -887,6 +896,151 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   return finish(MC_OK);
 }
 
+// ---------------------------------------------------------------------------
+// Learned denoiser
+int mc_denoise_init(mc_ctx* ctx, int height, int width, int max_batch, uint64_t seed) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (height < 16 || width < 16 || height % 16 || width % 16 || max_batch < 1 || max_batch > 4096)
+    return fail(ctx, MC_ERR_INVALID_ARG, "denoiser images must be multiples of 16 (>= 16) and 1 <= batch <= 4096");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  denoiser_destroy(ctx->denoiser);
+  ctx->denoiser = nullptr;
+  CK(denoiser_create(height, width, max_batch, seed, &ctx->denoiser), "denoiser creation");
+  return MC_OK;
+}
+
+int mc_denoise_train_step(mc_ctx* ctx, const float* noisy, const float* clean, int n, float lr, float* loss_out,
+                          void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoiser not initialised");
+  if (!noisy || !clean || !loss_out || !(lr >= 0.f)) return fail(ctx, MC_ERR_INVALID_ARG, "bad training arguments");
+  int H, W, B;
+  denoiser_size(ctx->denoiser, &H, &W, &B);
+  if (n < 1 || n > B) return fail(ctx, MC_ERR_INVALID_ARG, "batch outside 1..max_batch");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  int err = 0;
+  CK(denoiser_train_step(ctx->denoiser, noisy, clean, n, lr, loss_out, &err, (cudaStream_t)stream), "training step");
+  if (err) return fail(ctx, MC_ERR_TIMEOUT, "a tensor-core wait gave up");
+  return MC_OK;
+}
+
+int mc_denoise_infer(mc_ctx* ctx, const float* in, float* out, int n, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoiser not initialised");
+  if (!in || !out || n < 1) return fail(ctx, MC_ERR_INVALID_ARG, "bad inference arguments");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  CK(denoiser_infer(ctx->denoiser, in, out, n, (cudaStream_t)stream), "inference");
+  CK(cudaStreamSynchronize((cudaStream_t)stream), "inference");
+  return MC_OK;
+}
+
+int mc_denoise_get_layer(mc_ctx* ctx, int layer, float* w, float* b, float* gw, float* gb, int* cin, int* cout) {
+  if (!ctx || !cin || !cout) return MC_ERR_INVALID_ARG;
+  if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoiser not initialised");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaDeviceSynchronize(), "synchronize");
+  if (!denoiser_get_layer(ctx->denoiser, layer, w, b, gw, gb, cin, cout))
+    return fail(ctx, MC_ERR_INVALID_ARG, "layer index out of range");
+  return MC_OK;
+}
+
+int mc_denoise_set_layer(mc_ctx* ctx, int layer, const float* w, const float* b) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoiser not initialised");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!denoiser_set_layer(ctx->denoiser, layer, w, b)) return fail(ctx, MC_ERR_INVALID_ARG, "bad layer or copy");
+  return MC_OK;
+}
+
+int mc_denoise_save(mc_ctx* ctx, const char* path) {
+  if (!ctx || !path) return MC_ERR_INVALID_ARG;
+  if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoiser not initialised");
+  int H, W, B;
+  const int nl = denoiser_size(ctx->denoiser, &H, &W, &B);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, MC_ERR_IO, std::string("cannot write ") + path);
+  const int32_t hdr[4] = {1, H, W, nl};
+  bool ok = std::fwrite("MCXDEN01", 1, 8, f) == 8 && std::fwrite(hdr, 4, 4, f) == 4;
+  for (int i = 0; i < nl && ok; ++i) {
+    int ci = 0, co = 0;
+    denoiser_get_layer(ctx->denoiser, i, nullptr, nullptr, nullptr, nullptr, &ci, &co);
+    std::vector<float> w((size_t)co * 9 * ci), b(co);
+    denoiser_get_layer(ctx->denoiser, i, w.data(), b.data(), nullptr, nullptr, &ci, &co);
+    const int32_t dims[2] = {ci, co};
+    ok = std::fwrite(dims, 4, 2, f) == 2 && std::fwrite(w.data(), 4, w.size(), f) == w.size() &&
+         std::fwrite(b.data(), 4, b.size(), f) == b.size();
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MC_OK : fail(ctx, MC_ERR_IO, "write failed");
+}
+
+int mc_denoise_load(mc_ctx* ctx, const char* path, int max_batch) {
+  if (!ctx || !path) return MC_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, MC_ERR_IO, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t hdr[4];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "MCXDEN01", 8) || std::fread(hdr, 4, 4, f) != 4 ||
+      hdr[0] != 1 || hdr[3] != denoiser_layer_count()) {
+    std::fclose(f);
+    return fail(ctx, MC_ERR_IO, "not a denoiser checkpoint");
+  }
+  int rc = mc_denoise_init(ctx, hdr[1], hdr[2], max_batch > 0 ? max_batch : 16, 0);
+  if (rc) {
+    std::fclose(f);
+    return rc;
+  }
+  for (int i = 0; i < hdr[3]; ++i) {
+    int ci = 0, co = 0;
+    denoiser_get_layer(ctx->denoiser, i, nullptr, nullptr, nullptr, nullptr, &ci, &co);
+    int32_t dims[2];
+    std::vector<float> w((size_t)co * 9 * ci), b(co);
+    if (std::fread(dims, 4, 2, f) != 2 || dims[0] != ci || dims[1] != co || std::fread(w.data(), 4, w.size(), f) != w.size() ||
+        std::fread(b.data(), 4, b.size(), f) != b.size()) {
+      std::fclose(f);
+      return fail(ctx, MC_ERR_IO, "truncated or mismatched denoiser checkpoint");
+    }
+    denoiser_set_layer(ctx->denoiser, i, w.data(), b.data());
+  }
+  std::fclose(f);
+  return MC_OK;
+}
+
+int mc_nn_conv3x3(const void* x, const void* w, const float* bias, void* y, int n, int h, int wd, int cin, int cout,
+                  int relu, int out_f32, int* err, void* stream) {
+  if (!x || !w || !y || !err || n < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256)
+    return MC_ERR_INVALID_ARG;
+  ConvParams p;
+  p.x = (const __nv_bfloat16*)x;
+  p.wt = (const __nv_bfloat16*)w;
+  p.bias = bias;
+  p.y = y;
+  p.n = n; p.h = h; p.w = wd; p.cin = cin; p.cout = cout;
+  p.relu = relu; p.out_f32 = out_f32;
+  p.err = err;
+  (void)cudaGetLastError();
+  const cudaError_t e = launch_conv3x3_fwd(p, (cudaStream_t)stream);
+  return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
+
+int mc_nn_conv3x3_wgrad(const void* x, const void* dy, float* dw, int n, int h, int wd, int cin, int cout, int splits,
+                        int* err, void* stream) {
+  if (!x || !dy || !dw || !err || n < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 || cout < 16 || cout % 16 ||
+      cout > 256 || splits < 1 || splits > 65535)
+    return MC_ERR_INVALID_ARG;
+  WgradParams p;
+  p.x = (const __nv_bfloat16*)x;
+  p.dy = (const __nv_bfloat16*)dy;
+  p.dw = dw;
+  p.n = n; p.h = h; p.w = wd; p.cin = cin; p.cout = cout;
+  p.err = err;
+  (void)cudaGetLastError();
+  const cudaError_t e = launch_conv3x3_wgrad(p, splits, (cudaStream_t)stream);
+  return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
+
 int mc_last_stats(const mc_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0 || n > MC_STAT_N) return MC_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) out[i] = ctx->stats[i];
@@ -899,7 +1053,7 @@ int mc_smooth_upsample(mc_ctx* ctx, const float* in, int n_in, const float* in_a
   if (!in || !out || !in_angles || !out_angles || n_in < 1 || n_out < 1 || nu < 1 || nv < 1 || NU < 1 || NV < 1)
     return fail(ctx, MC_ERR_INVALID_ARG, "bad smooth_upsample arguments");
   const int win = ctx->opt.sg_window, ord = ctx->opt.sg_order;
-  const bool smooth = ctx->opt.denoise_mode == 0;
+  const bool smooth = ctx->opt.denoise_mode == 0;  // 1: learned denoiser, 2: none
   if (smooth && (nu < win || nv < win)) return fail(ctx, MC_ERR_INVALID_ARG, "image smaller than the smoothing window");
   const double two_pi = 6.283185307179586;
   for (int i = 0; i < n_in; ++i) {
@@ -956,6 +1110,13 @@ int mc_smooth_upsample(mc_ctx* ctx, const float* in, int n_in, const float* in_a
   if (smooth) {
     CK(launch_sg_rows(in, t0, n_in, nv, nu, coef, win, s), "smoothing launch");
     CK(launch_sg_cols(t0, t1, n_in, nv, nu, coef, win, s), "smoothing launch");
+    src = t1;
+  } else if (ctx->opt.denoise_mode == 1) {
+    int dh = 0, dw = 0, db = 0;
+    if (!ctx->denoiser) return fail(ctx, MC_ERR_STATE, "denoise_mode 1 needs mc_denoise_init or mc_denoise_load");
+    denoiser_size(ctx->denoiser, &dh, &dw, &db);
+    if (dh != nv || dw != nu) return fail(ctx, MC_ERR_INVALID_ARG, "image size differs from the denoiser's");
+    CK(denoiser_infer(ctx->denoiser, in, t1, n_in, s), "denoiser inference");
     src = t1;
   }
   CK(launch_lerp_upsample(src, nv, nu, out, n_out, NV, NU, d_a0, d_a1, d_fa, ctx->opt.cubic_a, s), "upsample launch");

@@ -136,4 +136,37 @@ cudaError_t launch_sg_cols(const float* in, float* out, int n_img, int h, int w,
 cudaError_t launch_lerp_upsample(const float* in, int nv, int nu, float* out, int n_out, int NV, int NU,
                                  const int* a0, const int* a1, const float* fa, float cubic_a, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Denoiser convolutions (k_conv.cu): NHWC BF16, channels multiples of 16.
+struct ConvParams {
+  const __nv_bfloat16* x;   // [n][h][w][cin]
+  const __nv_bfloat16* wt;  // [cout][9 * cin], k = tap * cin + c, tap = 3 * (dy + 1) + (dx + 1)
+  const float* bias;        // [cout] or null
+  void* y;                  // [n][h][w][cout], BF16 or FP32
+  int n, h, w, cin, cout;
+  int relu, out_f32;
+  int* err;                 // set to 1 if a bounded wait gave up
+};
+struct WgradParams {
+  const __nv_bfloat16* x;   // [n][h][w][cin] layer input
+  const __nv_bfloat16* dy;  // [n][h][w][cout] gradient at the layer output (pre-activation)
+  float* dw;                // [cout][9 * cin] FP32, accumulated (zero it first)
+  int n, h, w, cin, cout;
+  int* err;
+};
+cudaError_t launch_conv3x3_fwd(const ConvParams& p, cudaStream_t s);
+cudaError_t launch_conv3x3_wgrad(const WgradParams& p, int splits, cudaStream_t s);
+
+// Learned denoiser (denoiser.cu)
+struct Denoiser;
+cudaError_t denoiser_create(int H, int W, int B, unsigned long long seed, Denoiser** out);
+void denoiser_destroy(Denoiser* d);
+cudaError_t denoiser_infer(Denoiser* d, const float* img, float* out, int n, cudaStream_t s);
+cudaError_t denoiser_train_step(Denoiser* d, const float* noisy, const float* clean, int n, float lr, float* loss_out,
+                                int* err_out, cudaStream_t s);
+int denoiser_size(const Denoiser* d, int* H, int* W, int* B);
+bool denoiser_get_layer(const Denoiser* d, int i, float* w, float* b, float* gw, float* gb, int* cin, int* cout);
+bool denoiser_set_layer(Denoiser* d, int i, const float* w, const float* b);
+int denoiser_layer_count();
+
 }  // namespace mcx
