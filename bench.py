@@ -51,6 +51,13 @@ def parse():
     p.add_argument("--per-angle", action="store_true", help="one mc_project call per angle instead of one batch")
     p.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--denoise-eval", action="store_true",
+                   help="seconds per projection at <= 2%% scatter error: plain MC vs smoothing vs learned denoiser")
+    p.add_argument("--train-phantoms", type=int, default=96)
+    p.add_argument("--train-angles", type=int, default=4)
+    p.add_argument("--train-steps", type=int, default=1500)
+    p.add_argument("--ref-photons", type=float, default=1e10)
+    p.add_argument("--eval-angles", type=int, default=4)
     return p.parse_args()
 
 
@@ -342,9 +349,137 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_denoise_eval(args):
+    """Photons and seconds per projection needed to reach <= 2% relative L2
+    scatter error against a high-photon reference, for plain Monte Carlo, the
+    paper's Savitzky-Golay smoothing (Sec. II-C.4) and the learned denoiser
+    trained here on pairs produced by this Monte Carlo (128^2 panel of the
+    64^3 cylinder/rod phantom family, 60 keV, SOD/SDD 300/600, step 0.5 mm)."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+    from mc_inputs import cylinder_variant_phantom, default_table_path, mono_spectrum
+
+    mcx.build()
+    tdir = tempfile.mkdtemp(prefix="mcden")
+    tp = default_table_path("full", tdir)
+    ctx = mcx.Context(0)
+    ctx.load_tables(tp)
+    E, w = mono_spectrum(60.0)
+    ctx.set_spectrum(E, w)
+    H = W = 128
+    ctx.set_geometry(300.0, 600.0, W, H, 1.0, 1.0)
+    step = 0.5
+    rng = np.random.default_rng(0)
+
+    def scatter(n_photons, angle, seed):
+        out = ctx.project([angle], int(n_photons), step, seed, primary=False)["scatter"][0]
+        return out, ctx.last_stats()["transport_ms"]
+
+    # ---- training pairs
+    low_levels = [2e5, 5e5, 1e6, 2e6]
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    for k in range(args.train_phantoms):
+        v = cylinder_variant_phantom(k)
+        ctx.load_volume(v["mat"], v["rho"], v["spacing"])
+        for j in range(args.train_angles):
+            ang = float(rng.uniform(0, 2 * np.pi))
+            hi, _ = scatter(1e8, ang, 1_000_000 + 7919 * k + j)
+            for q, nl in enumerate(low_levels):
+                lo, _ = scatter(nl, ang, 2_000_000 + 104729 * k + 31 * j + q)
+                xs.append(lo.clone())
+                ys.append(hi)
+    X = torch.stack(xs)
+    Y = torch.stack(ys)
+    t_data = time.perf_counter() - t0
+    # ---- training
+    ctx.denoise_init(H, W, 16, seed=1)
+    t0 = time.perf_counter()
+    losses = []
+    order = torch.randperm(len(X), generator=torch.Generator().manual_seed(0))
+    for it in range(args.train_steps):
+        lr = 1e-3 * 0.5 * (1 + np.cos(np.pi * it / args.train_steps)) + 2e-5
+        idx = order[(it * 16) % len(X) : (it * 16) % len(X) + 16]
+        if len(idx) < 16:
+            order = torch.randperm(len(X))
+            idx = order[:16]
+        losses.append(ctx.denoise_train_step(X[idx], Y[idx], lr))
+    t_train = time.perf_counter() - t0
+    # ---- held-out phantom: reference and the error/photon curves
+    v = cylinder_variant_phantom(50_000)
+    ctx.load_volume(v["mat"], v["rho"], v["spacing"])
+    angles = [2 * np.pi * a / args.eval_angles + 0.1 for a in range(args.eval_angles)]
+    refs = [scatter(args.ref_photons, a, 9_000 + i)[0].double() for i, a in enumerate(angles)]
+    grid = [1e5, 2e5, 5e5, 1e6, 2e6, 5e6, 1e7, 2e7, 5e7, 1e8, 2e8, 5e8]
+    sg = mcx.Context(0)  # Savitzky-Golay (window 9, cubic) through mc_smooth_upsample
+    curves = {"plain": [], "smoothed": [], "denoised": []}
+    times = {"plain": [], "smoothed": [], "denoised": []}
+    for n in grid:
+        errs = {k: [] for k in curves}
+        t_mc = []
+        t_post = {"smoothed": [], "denoised": []}
+        for i, a in enumerate(angles):
+            img, ms = scatter(n, a, 5_000 + 17 * i + int(np.log10(n) * 100))
+            t_mc.append(ms)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            smooth = sg.smooth_upsample(img[None], [0.0], [0.0], W, H)[0]
+            ev1.record()
+            torch.cuda.synchronize()
+            t_post["smoothed"].append(ev0.elapsed_time(ev1))
+            ev0.record()
+            den = ctx.denoise_infer(img[None])[0]
+            ev1.record()
+            torch.cuda.synchronize()
+            t_post["denoised"].append(ev0.elapsed_time(ev1))
+            r = refs[i]
+            nr = torch.linalg.norm(r)
+            errs["plain"].append(float(torch.linalg.norm(img.double() - r) / nr))
+            errs["smoothed"].append(float(torch.linalg.norm(smooth.double() - r) / nr))
+            errs["denoised"].append(float(torch.linalg.norm(den.double() - r) / nr))
+        for k in curves:
+            curves[k].append(float(np.mean(errs[k])))
+            times[k].append(float(np.mean(t_mc)) + (float(np.mean(t_post[k])) if k in t_post else 0.0))
+
+    def at_target(k, target=0.02):
+        """Photons and ms per projection where the error curve crosses the target (log-log interpolation)."""
+        e = curves[k]
+        for j in range(len(grid)):
+            if e[j] <= target:
+                if j == 0:
+                    return grid[0], times[k][0]
+                f = (np.log(e[j - 1]) - np.log(target)) / (np.log(e[j - 1]) - np.log(e[j]))
+                n = float(np.exp(np.log(grid[j - 1]) + f * (np.log(grid[j]) - np.log(grid[j - 1]))))
+                t = float(np.exp(np.log(times[k][j - 1]) + f * (np.log(times[k][j]) - np.log(times[k][j - 1]))))
+                return n, t
+        return None, None
+
+    res = {k: at_target(k) for k in curves}
+    line = {
+        "metric": "s/projection at <=2% relative L2 scatter error vs a high-photon reference",
+        "unit": "s/projection", "higher_is_better": False,
+        "config": {"workload": "cylinder/rod family, 64^3 x 1 mm, 128^2 x 1 mm panel, 60 keV, step 0.5 mm",
+                   "train_pairs": int(len(X)), "train_inputs_photons": low_levels, "train_target_photons": 1e8,
+                   "train_steps": args.train_steps, "reference_photons": args.ref_photons,
+                   "eval_angles": args.eval_angles, "denoiser": "residual U-Net, 4 levels, 32 base channels, BF16"},
+        "photons_at_2pct": {k: res[k][0] for k in res},
+        "s_per_projection_at_2pct": {k: (None if res[k][1] is None else res[k][1] / 1e3) for k in res},
+        "speedup_vs_plain": {k: (None if res[k][1] is None or res["plain"][1] is None else res["plain"][1] / res[k][1])
+                             for k in ("smoothed", "denoised")},
+        "error_curves": {"photons": grid, **{k: curves[k] for k in curves}},
+        "ms_per_projection": {"photons": grid, **times},
+        "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
+        "seconds": {"data": t_data, "train": t_train},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.denoise_eval:
+        run_denoise_eval(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

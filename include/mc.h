@@ -166,6 +166,58 @@ int mc_last_stats(const mc_ctx *ctx, double *out, int n);
 int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_angles, int nu, int nv, float *out,
                        int n_out, const float *out_angles, int NU, int NV, void *stream);
 
+/* Iterative scatter correction (Sec. II-E and its flowchart; eq. Correction).
+ * Measured intensities raw_I (device [n_proj][NV][NU], the panel set by
+ * mc_set_geometry at NU x NV pixels) and the flat field I0 (device [NV][NU])
+ * give a = -ln(I/I0).  Each of n_iter iterations:
+ *   1. FDK reconstruction of the current projections c (c = a at first) on
+ *      the nx x ny x nz grid (Ram-Lak ramp, cosine pre-weighting, voxel-driven
+ *      backprojection with bilinear interpolation);
+ *   2. Otsu segmentation into `classes` (2 or 3) classes of the histogram over
+ *      [mu_lo, mu_hi) mm^-1; class 0 becomes class_material[0] at density
+ *      class_density0, class k >= 1 becomes class_material[k] with density
+ *      mu / (mu_rho(class_material[k], e_eff_keV) x 0.1);
+ *   3. Monte Carlo on a sim_nu x sim_nv grid over the same panel: scatter
+ *      (photons histories each) at every sim_angle_stride-th angle; the
+ *      primary at every angle, on the same grid or (primary_full_res) on the
+ *      NU x NV panel;
+ *   4. smoothing (options.denoise_mode) of the scatter, linear interpolation
+ *      to every angle and cubic up-sampling to NU x NV (of the primary too
+ *      unless it was computed at full resolution);
+ *   5. c = a - ln(Ip / (Ip + Is)).
+ * corrected_a_out (device, like raw_I) receives the final c; volume_out
+ * (device [nz][ny][nx] FP32, nullable) the last reconstruction (of the last
+ * corrected projections when n_iter >= 1); iter_seconds (host [n_iter],
+ * nullable) the wall time of each iteration.  angles_rad (host) must cover a
+ * full orbit in increasing order.  The context's volume is replaced by the
+ * segmented reconstruction.  Allocates temporary device buffers.
+ * Errors: STATE, INVALID_ARG, CUDA/OOM, and those of mc_project. */
+typedef struct mc_correct_params {
+  int nx, ny, nz;
+  float dx, dy, dz;
+  int sim_nu, sim_nv;
+  int sim_angle_stride;
+  uint64_t photons;
+  float step_mm;
+  uint64_t seed;
+  int classes;
+  int class_material[3];
+  float class_density0;
+  float e_eff_keV;
+  float mu_lo, mu_hi;
+  int primary_full_res; /* 1: primary computed on the NU x NV panel itself (exact, cheap); 0: on the
+                           simulation grid and up-sampled with the scatter, as the paper does */
+} mc_correct_params;
+int mc_correct_iter(mc_ctx *ctx, const float *raw_I, const float *I0, int n_proj, const float *angles_rad, int NU,
+                    int NV, int n_iter, const mc_correct_params *prm, float *corrected_a_out, float *volume_out,
+                    double *iter_seconds, void *stream);
+
+/* Plain FDK reconstruction (step 1 above) of line-integral projections p
+ * (device [n_proj][NV][NU], the context's panel geometry) into vol (device
+ * [nz][ny][nx], mm^-1).  Errors: STATE (no geometry), INVALID_ARG, CUDA/OOM. */
+int mc_fdk(mc_ctx *ctx, const float *p, int n_proj, const float *angles_rad, int NU, int NV, int nx, int ny, int nz,
+           float dx, float dy, float dz, float *vol, void *stream);
+
 /* Learned scatter denoiser (replaces the Savitzky-Golay smoothing of
  * Sec. II-C.4 at low photon counts; no counterpart network in the paper): a
  * residual U-Net, 4 levels, 32 base channels, 3x3 convolutions, 2x2 max

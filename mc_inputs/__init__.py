@@ -18,6 +18,7 @@ from .tables import (  # noqa: F401
 )
 from .phantoms import (  # noqa: F401
     cylinder_rod_phantom,
+    cylinder_variant_phantom,
     ellipsoid_phantom,
     tiny_phantom,
     slab_phantom,

@@ -132,3 +132,35 @@ def slab_phantom(n=(16, 16, 16), dv=(2.0, 2.0, 2.0), material=MAT_WATER, density
     out = _finish(mat, dens)
     out.update(shape=(nz, ny, nx), spacing=(dv[0], dv[1], dv[2]))
     return out
+
+
+def cylinder_variant_phantom(seed, n=64, dv=1.0):
+    """Seeded variant of the cylinder + rod phantom for denoiser training:
+    cylinder radius 18-28 mm and height 40-60 mm, rod radius 3-8 mm at a random
+    offset inside the cylinder, rod material aluminium, bone or PMMA, and up to
+    three small water/bone/PMMA/aluminium ellipsoids inside the cylinder."""
+    rng = np.random.default_rng(10_000 + seed)
+    c = _centres(n, dv)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    half = n * dv / 2.0
+    r_cyl = rng.uniform(0.56, 0.88) * half * 1.0
+    h_cyl = rng.uniform(0.62, 0.94) * 2 * half
+    r_rod = rng.uniform(3.0, 8.0) * dv
+    ang = rng.uniform(0, 2 * np.pi)
+    off = rng.uniform(0.0, max(r_cyl - r_rod - dv, 0.0))
+    rx, ry = off * np.cos(ang), off * np.sin(ang)
+    mat = np.full((n, n, n), MAT_AIR, dtype=np.uint8)
+    inz = np.abs(z) <= h_cyl / 2.0
+    mat[(x**2 + y**2 <= r_cyl**2) & inz] = MAT_WATER
+    rod_mat = [MAT_AL, MAT_BONE, MAT_PMMA][int(rng.integers(0, 3))]
+    mat[((x - rx) ** 2 + (y - ry) ** 2 <= r_rod**2) & inz] = rod_mat
+    for _ in range(int(rng.integers(0, 4))):
+        cx, cy = rng.uniform(-0.6, 0.6, 2) * r_cyl
+        cz = rng.uniform(-0.4, 0.4) * h_cyl
+        ax = rng.uniform(2.0, 8.0, 3) * dv
+        m = [MAT_WATER, MAT_BONE, MAT_PMMA, MAT_AL][int(rng.integers(0, 4))]
+        inside = ((x - cx) / ax[0]) ** 2 + ((y - cy) / ax[1]) ** 2 + ((z - cz) / ax[2]) ** 2 <= 1.0
+        mat[inside & (mat != MAT_AIR)] = m
+    out = _finish(mat)
+    out.update(shape=(n, n, n), spacing=(dv, dv, dv))
+    return out

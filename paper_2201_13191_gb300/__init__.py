@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     MCError,
     Options,
     Tuning,
+    CorrectParams,
     Context,
     library,
     library_path,

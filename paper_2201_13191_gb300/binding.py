@@ -34,7 +34,7 @@ EXPORTED = [
     "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
-    "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad",
+    "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
 ]
 
 
@@ -52,6 +52,24 @@ class Tuning(C.Structure):
         ("tally_mode", C.c_int),
         ("histories_per_s", C.c_double),
         ("step_error", C.c_double),
+    ]
+
+
+class CorrectParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dx", C.c_float), ("dy", C.c_float), ("dz", C.c_float),
+        ("sim_nu", C.c_int), ("sim_nv", C.c_int),
+        ("sim_angle_stride", C.c_int),
+        ("photons", C.c_uint64),
+        ("step_mm", C.c_float),
+        ("seed", C.c_uint64),
+        ("classes", C.c_int),
+        ("class_material", C.c_int * 3),
+        ("class_density0", C.c_float),
+        ("e_eff_keV", C.c_float),
+        ("mu_lo", C.c_float), ("mu_hi", C.c_float),
+        ("primary_full_res", C.c_int),
     ]
 
 
@@ -117,6 +135,8 @@ def library():
         L.mc_denoise_load.argtypes = [P, C.c_char_p, i]
         L.mc_nn_conv3x3.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, i, vp, vp]
         L.mc_nn_conv3x3_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
+        L.mc_correct_iter.argtypes = [P, vp, vp, i, vp, i, i, i, C.POINTER(CorrectParams), vp, vp, vp, vp]
+        L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
         _lib = L
     return _lib
 
@@ -326,6 +346,27 @@ class Context:
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1)
         return res
+
+    # ---- correction plumbing
+    def fdk(self, p, angles, NU, NV, grid, stream=None):
+        """FDK of line integrals p (device [n][NV][NU]); grid = (nx, ny, nz, dx, dy, dz) -> [nz][ny][nx]."""
+        nx, ny, nz, dx, dy, dz = grid
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        vol = self.torch.empty((max(nz, 1), max(ny, 1), max(nx, 1)), dtype=self.torch.float32, device=self.device)
+        self._check(self.L.mc_fdk(self.h, _t_ptr(p.contiguous()), len(a), _np_ptr(a), NU, NV, nx, ny, nz, dx, dy, dz,
+                                  _t_ptr(vol), _stream_handle(stream)))
+        return vol
+
+    def correct_iter(self, raw_I, I0, angles, NU, NV, n_iter, prm, stream=None):
+        """Iterative scatter correction; returns (corrected line integrals, last volume, seconds per iteration)."""
+        a = np.ascontiguousarray(angles, dtype=np.float32)
+        out = self.torch.empty_like(raw_I)
+        vol = self.torch.empty((prm.nz, prm.ny, prm.nx), dtype=self.torch.float32, device=self.device)
+        secs = np.zeros(max(n_iter, 1))
+        self._check(self.L.mc_correct_iter(self.h, _t_ptr(raw_I.contiguous()), _t_ptr(I0.contiguous()), len(a),
+                                           _np_ptr(a), NU, NV, n_iter, C.byref(prm), _t_ptr(out), _t_ptr(vol),
+                                           _np_ptr(secs), _stream_handle(stream)))
+        return out, vol, list(secs[:n_iter])
 
     # ---- learned denoiser
     def denoise_init(self, height, width, max_batch, seed=0):

@@ -1,0 +1,232 @@
+// Iterative scatter correction plumbing (arXiv 2201.13191 Sec. II-E, Fig.
+// flowchart, eq. Correction): conversion of intensities to line integrals,
+// FDK (cone-beam filtered backprojection) for the circular orbit of this
+// library's geometry, multi-level Otsu segmentation, conversion of the
+// segmented volume to material ids and densities, and the correction
+// c = a - ln(Ip / (Ip + Is)).
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "mc_internal.h"
+
+namespace mcx {
+namespace {
+
+__device__ __forceinline__ size_t gtid() { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ size_t gstride() { return (size_t)gridDim.x * blockDim.x; }
+int blocks_for(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+// a = -ln(I / I0) per pixel (I0 is one flat-field image shared by all projections).
+__global__ void k_log_norm(const float* __restrict__ I, const float* __restrict__ I0, size_t img, size_t n,
+                           float* __restrict__ a) {
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const float v = fmaxf(I[i], 1e-30f), f = fmaxf(I0[i % img], 1e-30f);
+    a[i] = -logf(v / f);
+  }
+}
+
+// FDK pre-weighting and ramp filtering of one detector row per block:
+//   q(u_i) = du * sum_j h(i - j) * w(u_j, v) p(u_j),  w = D / sqrt(D^2 + u^2 + v^2)
+// with u, v the pixel-centre offsets scaled to the isocentre plane, D = SOD,
+// du the isocentre pixel pitch and h the discrete Ram-Lak kernel
+// h(0) = 1/(4 du^2), h(odd n) = -1/(n pi du)^2, h(even n != 0) = 0.
+__global__ void k_fdk_filter(const float* __restrict__ p, int nu, int nv, float du_iso, float dv_iso, float sod,
+                             float* __restrict__ q) {
+  extern __shared__ float row[];
+  const int r = blockIdx.x;  // row index over all projections: proj * nv + v
+  const int v = r % nv;
+  const float vv = ((float)v - 0.5f * (float)(nv - 1)) * dv_iso;
+  const float* src = p + (size_t)r * nu;
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+    const float uu = ((float)i - 0.5f * (float)(nu - 1)) * du_iso;
+    row[i] = src[i] * sod * rsqrtf(sod * sod + uu * uu + vv * vv);
+  }
+  __syncthreads();
+  const float inv_pi2 = 1.f / (9.8696044f * du_iso * du_iso);
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+    float acc = row[i] * (0.25f / (du_iso * du_iso));
+    for (int j = (i & 1) ? 0 : 1; j < nu; j += 2) {  // only odd offsets i - j contribute
+      const float n = (float)(i - j);
+      acc -= row[j] * inv_pi2 / (n * n);
+    }
+    q[(size_t)r * nu + i] = acc * du_iso;
+  }
+}
+
+// Voxel-driven backprojection: f(x) = (dbeta / 2) sum_beta (D / (D - x.n))^2 q(u(x), v(x)),
+// q bilinearly interpolated at the voxel's projection (zero outside the panel).
+__global__ void k_fdk_backproject(const float* __restrict__ q, const float* __restrict__ cb, const float* __restrict__ sb,
+                                  int n_proj, int nu, int nv, float du_iso, float dv_iso, float sod, int nx, int ny,
+                                  int nz, float dx, float dy, float dz, float scale, float* __restrict__ vol) {
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const int ix = (int)(i % nx);
+    const size_t t = i / nx;
+    const int iy = (int)(t % ny), iz = (int)(t / ny);
+    const float x = ((float)ix - 0.5f * (float)(nx - 1)) * dx;
+    const float y = ((float)iy - 0.5f * (float)(ny - 1)) * dy;
+    const float z = ((float)iz - 0.5f * (float)(nz - 1)) * dz;
+    float acc = 0.f;
+    for (int k = 0; k < n_proj; ++k) {
+      const float c = __ldg(cb + k), s = __ldg(sb + k);
+      const float depth = sod - (x * c + y * s);  // distance from the source along the central ray
+      const float mag = sod / depth;
+      const float u = (-x * s + y * c) * mag;     // isocentre-plane coordinates
+      const float v = z * mag;
+      const float fu = u / du_iso + 0.5f * (float)(nu - 1);
+      const float fv = v / dv_iso + 0.5f * (float)(nv - 1);
+      const int u0 = __float2int_rd(fu), v0 = __float2int_rd(fv);
+      const float au = fu - (float)u0, av = fv - (float)v0;
+      const float* qp = q + (size_t)k * nu * nv;
+      float val = 0.f;
+      if (u0 >= 0 && u0 + 1 < nu && v0 >= 0 && v0 + 1 < nv) {
+        const float* r0 = qp + (size_t)v0 * nu + u0;
+        val = (1.f - av) * ((1.f - au) * __ldg(r0) + au * __ldg(r0 + 1)) +
+              av * ((1.f - au) * __ldg(r0 + nu) + au * __ldg(r0 + nu + 1));
+      }
+      acc = fmaf(mag * mag, val, acc);
+    }
+    vol[i] = acc * scale;
+  }
+}
+
+// Histogram of vol over [lo, hi) in nbins bins (values outside are clamped to the end bins).
+__global__ void k_hist(const float* __restrict__ vol, size_t n, float lo, float hi, int nbins,
+                       unsigned int* __restrict__ hist) {
+  extern __shared__ unsigned int sh[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+  const float sc = (float)nbins / (hi - lo);
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const int b = min(max((int)((vol[i] - lo) * sc), 0), nbins - 1);
+    atomicAdd(&sh[b], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+// Multi-level Otsu (classes = 2 or 3): thresholds maximising the between-class
+// variance of the histogram, exhaustively (one block; nbins <= 256).
+__global__ void k_otsu(const unsigned int* __restrict__ hist, int nbins, int classes, int* __restrict__ thr) {
+  __shared__ double P[257], S[257];
+  __shared__ double best_val[256];
+  __shared__ int best_a[256], best_b[256];
+  if (threadIdx.x == 0) {
+    P[0] = 0;
+    S[0] = 0;
+    for (int b = 0; b < nbins; ++b) {
+      P[b + 1] = P[b] + hist[b];
+      S[b + 1] = S[b] + (double)hist[b] * (b + 0.5);
+    }
+  }
+  __syncthreads();
+  const double N = P[nbins], mu = S[nbins] / fmax(N, 1.0);
+  auto term = [&](int a, int b) {  // class [a, b)
+    const double w = P[b] - P[a];
+    if (w <= 0) return 0.0;
+    const double m = (S[b] - S[a]) / w;
+    return w * (m - mu) * (m - mu);
+  };
+  double bv = -1;
+  int ba = 1, bb = nbins;
+  for (int a = 1 + threadIdx.x; a < nbins; a += blockDim.x) {
+    if (classes == 2) {
+      const double v = term(0, a) + term(a, nbins);
+      if (v > bv) { bv = v; ba = a; bb = nbins; }
+    } else {
+      for (int b = a + 1; b < nbins; ++b) {
+        const double v = term(0, a) + term(a, b) + term(b, nbins);
+        if (v > bv) { bv = v; ba = a; bb = b; }
+      }
+    }
+  }
+  best_val[threadIdx.x] = bv;
+  best_a[threadIdx.x] = ba;
+  best_b[threadIdx.x] = bb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int t = 1; t < (int)blockDim.x; ++t)
+      if (best_val[t] > best_val[k] || (best_val[t] == best_val[k] && (best_a[t] < best_a[k] ||
+                                                                     (best_a[t] == best_a[k] && best_b[t] < best_b[k]))))
+        k = t;
+    thr[0] = best_a[k];
+    thr[1] = best_b[k];
+  }
+}
+
+// Class of each voxel by the thresholds (bins) -> material id and density
+// rho = mu / (mu_rho(material) * 0.1), clamped to [0, rho_max]; class 0 -> the
+// background material at its nominal density.
+__global__ void k_segment(const float* __restrict__ vol, size_t n, float lo, float hi, int nbins,
+                          const int* __restrict__ thr, int classes, const int* __restrict__ cls_mat,
+                          const float* __restrict__ cls_murho, const float* __restrict__ cls_rho0, float rho_max,
+                          uint8_t* __restrict__ mat, uint16_t* __restrict__ rho) {
+  const float sc = (float)nbins / (hi - lo);
+  const int t0 = thr[0], t1 = thr[1];
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const int b = min(max((int)((vol[i] - lo) * sc), 0), nbins - 1);
+    const int c = b < t0 ? 0 : ((classes == 2 || b < t1) ? 1 : 2);
+    mat[i] = (uint8_t)cls_mat[c];
+    float r = c == 0 ? cls_rho0[0] : fminf(fmaxf(vol[i] / (0.1f * cls_murho[c]), 0.f), rho_max);
+    rho[i] = __half_as_ushort(__float2half_rn(r));
+  }
+}
+
+// c = a - ln(Ip / (Ip + Is)) (eq. Correction).
+__global__ void k_correct(const float* __restrict__ a, const float* __restrict__ ip, const float* __restrict__ is,
+                          size_t n, float* __restrict__ c) {
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const float p = fmaxf(ip[i], 1e-30f), sc = fmaxf(is[i], 0.f);
+    c[i] = a[i] - logf(p / (p + sc));
+  }
+}
+
+}  // namespace
+
+cudaError_t recon_log_norm(const float* I, const float* I0, size_t img, size_t n, float* a, cudaStream_t s) {
+  k_log_norm<<<blocks_for(n), 256, 0, s>>>(I, I0, img, n, a);
+  return cudaGetLastError();
+}
+
+cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const float* d_sin, int nu, int nv, float pu,
+                      float pv, float sod, float sdd, int nx, int ny, int nz, float dx, float dy, float dz, float* q_tmp,
+                      float* vol, cudaStream_t s) {
+  const float du = pu * sod / sdd, dv = pv * sod / sdd;  // pixel pitch at the isocentre
+  if ((size_t)nu * 4 > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, nu * 4);
+  if (e != cudaSuccess) return e;
+  k_fdk_filter<<<n_proj * nv, 256, nu * 4, s>>>(p, nu, nv, du, dv, sod, q_tmp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // full orbit: (dbeta / 2) with dbeta = 2 pi / n_proj
+  const float scale = 3.14159265358979f / (float)n_proj;
+  const size_t n = (size_t)nx * ny * nz;
+  k_fdk_backproject<<<blocks_for(n), 256, 0, s>>>(q_tmp, d_cos, d_sin, n_proj, nu, nv, du, dv, sod, nx, ny, nz, dx,
+                                                  dy, dz, scale, vol);
+  return cudaGetLastError();
+}
+
+cudaError_t recon_otsu_segment(const float* vol, size_t n, float lo, float hi, int classes, const int* d_cls_mat,
+                               const float* d_cls_murho, const float* d_cls_rho0, float rho_max, unsigned int* d_hist,
+                               int* d_thr, uint8_t* mat, uint16_t* rho, cudaStream_t s) {
+  const int nbins = 256;
+  cudaError_t e = cudaMemsetAsync(d_hist, 0, nbins * 4, s);
+  if (e != cudaSuccess) return e;
+  k_hist<<<blocks_for(n), 256, nbins * 4, s>>>(vol, n, lo, hi, nbins, d_hist);
+  k_otsu<<<1, 256, 0, s>>>(d_hist, nbins, classes, d_thr);
+  k_segment<<<blocks_for(n), 256, 0, s>>>(vol, n, lo, hi, nbins, d_thr, classes, d_cls_mat, d_cls_murho, d_cls_rho0,
+                                          rho_max, mat, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t recon_correct(const float* a, const float* ip, const float* is, size_t n, float* c, cudaStream_t s) {
+  k_correct<<<blocks_for(n), 256, 0, s>>>(a, ip, is, n, c);
+  return cudaGetLastError();
+}
+
+}  // namespace mcx

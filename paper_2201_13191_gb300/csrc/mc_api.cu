@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -894,6 +895,170 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   out->step_error = best_err;
   (void)max_per_sm;
   return finish(MC_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Correction plumbing
+int mc_fdk(mc_ctx* ctx, const float* p, int n_proj, const float* angles, int NU, int NV, int nx, int ny, int nz,
+           float dx, float dy, float dz, float* vol, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
+  if (!p || !vol || !angles || n_proj < 1 || NU < 2 || NV < 2 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) ||
+      !(dy > 0) || !(dz > 0) || NU > 50000)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad reconstruction arguments");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  cudaStream_t s = (cudaStream_t)stream;
+  const float pu = ctx->pu * (float)ctx->nu / (float)NU, pv = ctx->pv * (float)ctx->nv / (float)NV;
+  std::vector<float> cs(2 * (size_t)n_proj);
+  for (int k = 0; k < n_proj; ++k) {
+    cs[k] = std::cos((double)angles[k]);
+    cs[n_proj + k] = std::sin((double)angles[k]);
+  }
+  float *d_cs = nullptr, *q = nullptr;
+  CK(cudaMalloc((void**)&d_cs, cs.size() * 4), "fdk allocation");
+  cudaError_t e = cudaMalloc((void**)&q, (size_t)n_proj * NU * NV * 4);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cs, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = recon_fdk(p, n_proj, d_cs, d_cs + n_proj, NU, NV, pu, pv, ctx->sod, ctx->sdd, nx, ny, nz, dx, dy, dz, q, vol, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(q);
+  cudaFree(d_cs);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fdk");
+  return MC_OK;
+}
+
+int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj, const float* angles, int NU, int NV,
+                    int n_iter, const mc_correct_params* prm, float* c_out, float* vol_out, double* iter_seconds,
+                    void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables || !ctx->have_spectrum || !ctx->have_geometry)
+    return fail(ctx, MC_ERR_STATE, "tables, spectrum and geometry are needed");
+  if (!raw_I || !I0 || !angles || !prm || !c_out || n_proj < 2 || NU < 2 || NV < 2 || n_iter < 0)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad correction arguments");
+  const mc_correct_params& P = *prm;
+  if (P.nx < 1 || P.ny < 1 || P.nz < 1 || !(P.dx > 0) || !(P.dy > 0) || !(P.dz > 0) || P.sim_nu < 1 || P.sim_nv < 1 ||
+      P.sim_angle_stride < 1 || P.photons < 1 || !(P.step_mm > 0) || (P.classes != 2 && P.classes != 3) ||
+      !(P.mu_hi > P.mu_lo) || !(P.e_eff_keV >= ctx->E0) || !(P.e_eff_keV <= ctx->E0 + ctx->dE * (ctx->n_E - 1)))
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad correction parameters");
+  for (int k = 0; k < P.classes; ++k)
+    if (P.class_material[k] < 0 || P.class_material[k] >= ctx->n_mat)
+      return fail(ctx, MC_ERR_INVALID_ARG, "class material outside the table");
+  for (int k = 1; k < n_proj; ++k)
+    if (!(angles[k] > angles[k - 1])) return fail(ctx, MC_ERR_INVALID_ARG, "angles must increase");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t img = (size_t)NU * NV, nall = img * n_proj;
+  const size_t nvox = (size_t)P.nx * P.ny * P.nz;
+  const size_t simg = (size_t)P.sim_nu * P.sim_nv;
+  std::vector<float> sim_angles;
+  for (int k = 0; k < n_proj; k += P.sim_angle_stride) sim_angles.push_back(angles[k]);
+  const int n_sim = (int)sim_angles.size();
+  // buffers
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  auto release = [&](int code) {
+    cudaStreamSynchronize(s);
+    for (void* p : bufs) cudaFree(p);
+    return code;
+  };
+  float* a = (float*)alloc(nall * 4);
+  float* c = (float*)alloc(nall * 4);
+  float* ip = (float*)alloc(nall * 4);
+  float* is = (float*)alloc(nall * 4);
+  float* vol = (float*)alloc(nvox * 4);
+  uint8_t* mat = (uint8_t*)alloc(nvox);
+  uint16_t* rho = (uint16_t*)alloc(nvox * 2);
+  float* ip_sim = (float*)alloc((size_t)n_proj * simg * 4);
+  float* is_sim = (float*)alloc((size_t)n_sim * simg * 4);
+  unsigned int* hist = (unsigned int*)alloc(256 * 4);
+  int* thr = (int*)alloc(2 * 4 + 3 * 4 + 6 * 4);
+  if (bufs.size() != 11) return release(fail(ctx, MC_ERR_OOM, "correction buffers"));
+  int* d_cls_mat = thr + 2;
+  float* d_cls_murho = reinterpret_cast<float*>(thr + 5);
+  float* d_cls_rho0 = d_cls_murho + 3;
+  {
+    int cm[3];
+    float cmu[6];
+    for (int k = 0; k < 3; ++k) {
+      cm[k] = k < P.classes ? P.class_material[k] : 0;
+      const int m = cm[k];
+      // mass attenuation at the effective energy (linear between nodes)
+      const double x = (P.e_eff_keV - ctx->E0) / ctx->dE;
+      int i = std::max(0, std::min((int)std::floor(x), ctx->n_E - 2));
+      const double f = x - i;
+      auto tot = [&](int j) {
+        const size_t q = (size_t)m * ctx->n_E + j;
+        return ctx->pe[q] + ctx->in[q] + ctx->co[q];
+      };
+      cmu[k] = (float)(tot(i) + f * (tot(i + 1) - tot(i)));
+    }
+    cmu[3] = P.class_density0;
+    cmu[4] = cmu[5] = 0.f;
+    cudaError_t e = cudaMemcpyAsync(d_cls_mat, cm, sizeof(cm), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cls_murho, cmu, sizeof(cmu), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return release(cuda_fail(ctx, e, "class tables"));
+  }
+  // geometry of the simulation grid over the same panel
+  const float sod = ctx->sod, sdd = ctx->sdd, pu = ctx->pu, pv = ctx->pv;
+  const int nu0 = ctx->nu, nv0 = ctx->nv;
+  const float PU = pu * (float)nu0 / (float)NU, PV = pv * (float)nv0 / (float)NV;
+  const float spu = PU * (float)NU / (float)P.sim_nu, spv = PV * (float)NV / (float)P.sim_nv;
+  auto restore = [&]() { mc_set_geometry(ctx, sod, sdd, nu0, nv0, pu, pv); };
+  cudaError_t e = recon_log_norm(raw_I, I0, img, nall, a, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c, a, nall * 4, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return release(cuda_fail(ctx, e, "line integrals"));
+  const int saved_mode = ctx->opt.denoise_mode;
+  for (int it = 0; it < n_iter; ++it) {
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = mc_fdk(ctx, c, n_proj, angles, NU, NV, P.nx, P.ny, P.nz, P.dx, P.dy, P.dz, vol, stream);
+    if (rc) return release(rc);
+    e = recon_otsu_segment(vol, nvox, P.mu_lo, P.mu_hi, P.classes, d_cls_mat, d_cls_murho, d_cls_rho0, 30.f, hist, thr,
+                           mat, rho, s);
+    if (e != cudaSuccess) return release(cuda_fail(ctx, e, "segmentation"));
+    rc = mc_load_volume(ctx, mat, rho, P.nx, P.ny, P.nz, P.dx, P.dy, P.dz, 1, stream);
+    if (rc) return release(rc);
+    if (P.primary_full_res) {
+      rc = mc_set_geometry(ctx, sod, sdd, NU, NV, PU, PV);
+      if (rc == MC_OK) rc = mc_project(ctx, angles, n_proj, 1, P.step_mm, P.seed, ip, nullptr, nullptr, stream);
+      if (rc) {
+        restore();
+        return release(rc);
+      }
+    }
+    rc = mc_set_geometry(ctx, sod, sdd, P.sim_nu, P.sim_nv, spu, spv);
+    if (rc) return release(rc);
+    if (!P.primary_full_res) rc = mc_project(ctx, angles, n_proj, 1, P.step_mm, P.seed, ip_sim, nullptr, nullptr, stream);
+    if (rc == MC_OK)
+      rc = mc_project(ctx, sim_angles.data(), n_sim, P.photons, P.step_mm, P.seed + 7919ull * (it + 1), nullptr,
+                      is_sim, nullptr, stream);
+    restore();
+    if (rc && rc != MC_ERR_LIMIT) return release(rc);
+    rc = mc_smooth_upsample(ctx, is_sim, n_sim, sim_angles.data(), P.sim_nu, P.sim_nv, is, n_proj, angles, NU, NV, stream);
+    if (rc == MC_OK && !P.primary_full_res) {
+      ctx->opt.denoise_mode = 2;  // the primary is noise free: interpolate only
+      rc = mc_smooth_upsample(ctx, ip_sim, n_proj, angles, P.sim_nu, P.sim_nv, ip, n_proj, angles, NU, NV, stream);
+      ctx->opt.denoise_mode = saved_mode;
+    }
+    if (rc) return release(rc);
+    e = recon_correct(a, ip, is, nall, c, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return release(cuda_fail(ctx, e, "correction"));
+    if (iter_seconds) iter_seconds[it] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  e = cudaMemcpyAsync(c_out, c, nall * 4, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return release(cuda_fail(ctx, e, "output"));
+  if (vol_out) {
+    const int rc = mc_fdk(ctx, c, n_proj, angles, NU, NV, P.nx, P.ny, P.nz, P.dx, P.dy, P.dz, vol_out, stream);
+    if (rc) return release(rc);
+  }
+  return release(MC_OK);
 }
 
 // ---------------------------------------------------------------------------

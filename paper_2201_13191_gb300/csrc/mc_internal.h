@@ -157,6 +157,16 @@ struct WgradParams {
 cudaError_t launch_conv3x3_fwd(const ConvParams& p, cudaStream_t s);
 cudaError_t launch_conv3x3_wgrad(const WgradParams& p, int splits, cudaStream_t s);
 
+// Correction plumbing (k_recon.cu)
+cudaError_t recon_log_norm(const float* I, const float* I0, size_t img, size_t n, float* a, cudaStream_t s);
+cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const float* d_sin, int nu, int nv, float pu,
+                      float pv, float sod, float sdd, int nx, int ny, int nz, float dx, float dy, float dz, float* q_tmp,
+                      float* vol, cudaStream_t s);
+cudaError_t recon_otsu_segment(const float* vol, size_t n, float lo, float hi, int classes, const int* d_cls_mat,
+                               const float* d_cls_murho, const float* d_cls_rho0, float rho_max, unsigned int* d_hist,
+                               int* d_thr, uint8_t* mat, uint16_t* rho, cudaStream_t s);
+cudaError_t recon_correct(const float* a, const float* ip, const float* is, size_t n, float* c, cudaStream_t s);
+
 // Learned denoiser (denoiser.cu)
 struct Denoiser;
 cudaError_t denoiser_create(int H, int W, int B, unsigned long long seed, Denoiser** out);
