@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--denoise-eval", action="store_true",
                    help="seconds per projection at <= 2%% scatter error: plain MC vs smoothing vs learned denoiser")
+    p.add_argument("--conv-bench", action="store_true",
+                   help="tensor-core throughput of the denoiser's convolutions and its inference latency")
+    p.add_argument("--conv-size", type=int, default=256)
+    p.add_argument("--conv-batch", type=int, default=8)
     p.add_argument("--train-phantoms", type=int, default=96)
     p.add_argument("--train-angles", type=int, default=4)
     p.add_argument("--train-steps", type=int, default=1500)
@@ -135,27 +139,77 @@ def measured_peaks():
         return {}
 
 
-def oracle_rate(tp, wl, n_photons, budget_s):
-    """Oracle histories/s on a bounded sample of the workload (single thread)."""
+def host_cpu():
+    """Host core count and model name (for the CPU-baseline record)."""
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not name:
+        try:
+            name = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            name = next((l.split(":", 1)[1].strip() for l in name.splitlines() if l.startswith("Model name")), "")
+        except Exception:
+            name = ""
+    import platform
+
+    return os.cpu_count() or 1, (name or platform.machine())
+
+
+def _oracles(tp, wl, threads):
     import oracle
 
-    o = oracle.Oracle(tp)
-    o.setup(wl)
+    orcs = [oracle.Oracle(tp) for _ in range(threads)]
+    for o in orcs:
+        o.setup(wl)
+    return orcs
+
+
+def _oracle_histories(orcs, wl, n_photons, h0, per_thread):
+    """Histories h0 .. h0 + threads x per_thread on all oracles at once (the
+    oracle's C calls release the GIL, so threads run in parallel)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(i):
+        a = h0 + i * per_thread
+        orcs[i].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], a, a + per_thread)
+
+    if len(orcs) == 1:
+        run(0)
+        return
+    with ThreadPoolExecutor(len(orcs)) as ex:
+        list(ex.map(run, range(len(orcs))))
+
+
+def oracle_rate(tp, wl, n_photons, budget_s, threads=1):
+    """Oracle histories/s on a bounded sample of the workload: the primary image
+    once (single thread), a single-thread calibration, then a sample of
+    histories split over `threads` threads, extrapolated to one projection."""
+    orcs = _oracles(tp, wl, threads)
     t0 = time.perf_counter()
-    o.primary(0.0, wl["step_mm"])
+    orcs[0].primary(0.0, wl["step_mm"])
     t_primary = time.perf_counter() - t0
-    n = 500
+    n = 300
     t0 = time.perf_counter()
-    o.scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n)
+    orcs[0].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n)
+    t1 = (time.perf_counter() - t0) / n
+    rate1 = n_photons / (t_primary + n_photons * t1)
+    left = max(2.0, budget_s - t_primary - n * t1)
+    per = int(max(100, min(5e6, left / t1)))
+    t0 = time.perf_counter()
+    _oracle_histories(orcs, wl, n_photons, n, per)
     dt = time.perf_counter() - t0
-    n2 = int(max(500, min(5e6, n * (budget_s - t_primary) / max(dt, 1e-6))))
-    t0 = time.perf_counter()
-    o.scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n2)
-    t_hist = (time.perf_counter() - t0) / n2
+    t_hist = dt / (per * threads)
     rate = n_photons / (t_primary + n_photons * t_hist)
-    sample = (f"oracle, 1 thread: primary image once ({t_primary:.2f} s) + histories 0..{n2} of the "
-              f"{int(n_photons)}-photon run ({t_hist * n2:.1f} s), extrapolated to one full projection")
-    return rate, sample, t_primary, t_hist
+    sample = (f"oracle, {threads} thread(s): primary image once, single thread ({t_primary:.2f} s) + histories "
+              f"{n}..{n + per * threads} of the {int(n_photons)}-photon run ({dt:.1f} s wall), extrapolated "
+              "to one full projection")
+    return rate, sample, rate1
 
 
 def make_inputs(tables_dir, photons, workload=WORKLOAD):
@@ -169,28 +223,30 @@ def make_inputs(tables_dir, photons, workload=WORKLOAD):
 
 
 def run_reference(args):
+    """The oracle as it stands, on all host cores (one oracle per thread, histories split between them)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     tdir = tempfile.mkdtemp(prefix="mcbench")
     tp, wl = make_inputs(tdir, args.photons, args.workload)
-    import oracle
-
-    o = oracle.Oracle(tp)
-    o.setup(wl)
+    cores, cpu_name = host_cpu()
+    orcs = _oracles(tp, wl, cores)
     N = wl["n_photons"]
     # size each step to ~ (budget / (K + W)) seconds
     per_step = max(2.0, min(20.0, 150.0 / (args.steps + args.warmup)))
     t0 = time.perf_counter()
-    o.scatter(0.0, N, wl["step_mm"], wl["seed"], 0, 300)
-    t_h = (time.perf_counter() - t0) / 300
-    n = int(max(300, per_step / max(t_h, 1e-7)))
+    _oracle_histories(orcs, wl, N, 0, 1000)  # calibration with every thread busy
+    t_h = (time.perf_counter() - t0) / 1000
+    per = int(max(100, per_step / max(t_h, 1e-7)))  # histories per thread per step
+    n = per * cores
+    h = 1000 * cores
     for k in range(args.warmup):
-        o.scatter(0.0, N, wl["step_mm"], wl["seed"], k * n, (k + 1) * n)
+        _oracle_histories(orcs, wl, N, h, per)
+        h += n
     t0 = time.perf_counter()
     for k in range(args.steps):
-        h0 = (args.warmup + k) * n
-        o.scatter(0.0, N, wl["step_mm"], wl["seed"], h0, h0 + n)
+        _oracle_histories(orcs, wl, N, h, per)
+        h += n
     el = time.perf_counter() - t0
     value = n * args.steps / el
     line = {
@@ -200,11 +256,41 @@ def run_reference(args):
         "config": {"workload": args.workload, "volume": "256^3 x 0.5 mm", "detector": "512^2 x 0.4 mm",
                    "photons_per_projection": N, "step_mm": wl["step_mm"], "n_split": 10,
                    "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n} scatter histories of the {N}-photon run per step, single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_name,
+                         "sample": f"{n} scatter histories of the {N}-photon run per step, {cores} threads "
+                                   f"x {per} histories"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def gather_roofline(mcx, torch, props, shape, steps_per_s, stream):
+    """Voxel-gather roofline of the transport: one 4-byte packed voxel word per
+    march step against the random-gather rate measured (mc_probe_gather) on a
+    buffer the size of the packed volume (one-voxel border), i.e. at the memory
+    level the volume lives in."""
+    nz, ny, nx = shape
+    n_bytes = (nx + 2) * (ny + 2) * (nz + 2) * 4
+    l2 = int(getattr(props, "L2_cache_size", 126 * 1024 * 1024))
+    buf = torch.ones(n_bytes // 4, dtype=torch.int32, device="cuda")
+    grid, block, rounds = props.multi_processor_count * 8, 256, 256
+    for _ in range(3):
+        mcx.probe_gather(buf, rounds, grid, block, stream=stream)
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mcx.probe_gather(buf, rounds, grid, block, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    peak = 8 * rounds * grid * block / float(np.median(ts))
+    del buf
+    return {"bound": "l2" if n_bytes <= 0.75 * l2 else "hbm", "unit": "gathers/s", "achieved": steps_per_s,
+            "peak": peak, "frac": steps_per_s / peak, "bytes_per_gather": 4,
+            "achieved_GBps": 4 * steps_per_s / 1e9, "peak_GBps": 4 * peak / 1e9,
+            "peak_basis": f"mc_probe_gather: random 4-byte loads over {n_bytes / 1e6:.1f} MB (packed volume size), "
+                          f"{grid}x{block} threads, 8 loads in flight each; L2 {l2 / 1e6:.0f} MB"}
 
 
 def run_ours(args):
@@ -318,11 +404,14 @@ def run_ours(args):
             "kernel": "k_transport", "steps_per_launch": float(np.mean(steps_per)),
             "kernel_ms": mean_ms, "steps_per_s": float(np.mean(steps_per)) / (mean_ms / 1e3),
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)"}
+    roof["gather"] = gather_roofline(mcx, torch, props, vol["mat"].shape, roof["steps_per_s"], stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample, _, _ = oracle_rate(tp, wl, N, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cores, cpu_name = host_cpu()
+        rate, sample, rate1 = oracle_rate(tp, wl, N, args.cpu_seconds, threads=cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "value_1_thread": rate1, "cpu": cpu_name}
 
     if rank == 0:
         line = {
@@ -475,10 +564,114 @@ def run_denoise_eval(args):
     print(json.dumps(line), flush=True)
 
 
+UNET_CONVS = [(16, 32, 0), (32, 32, 0), (32, 64, 1), (64, 64, 1), (64, 128, 2), (128, 128, 2), (128, 256, 3),
+              (256, 256, 3), (384, 128, 2), (128, 128, 2), (192, 64, 1), (64, 64, 1), (96, 32, 0), (32, 32, 0),
+              (32, 16, 0)]  # (C_in, C_out, level) of the denoiser's 15 convolutions
+
+
+def run_conv_bench(args):
+    """Tensor-core throughput of the denoiser's 3x3 convolutions: every layer
+    shape of the U-Net, forward (mc_nn_conv3x3) and weight gradient
+    (mc_nn_conv3x3_wgrad), on a batch of images, plus the inference latency of
+    the whole network (mc_denoise_infer).  Roofline: dense BF16 tensor peak."""
+    import ctypes as C
+
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+    from paper_2201_13191_gb300.binding import library
+
+    mcx.build()
+    L = library()
+    H = W = args.conv_size
+    B = args.conv_batch
+    stream = torch.cuda.current_stream()
+    sh = C.c_void_p(stream.cuda_stream)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    peaks = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1891.8))
+    reps = 10
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def ptr(t):
+        return C.c_void_p(t.data_ptr())
+
+    layers, fl_f, ms_f, fl_w, ms_w = [], 0.0, 0.0, 0.0, 0.0
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for i, (ci, co, lv) in enumerate(UNET_CONVS):
+        h, w = H >> lv, W >> lv
+        x = torch.randn((B, h, w, ci), device="cuda", generator=g).to(torch.bfloat16)
+        wt = (0.05 * torch.randn((co, 9, ci), device="cuda", generator=g)).to(torch.bfloat16)
+        bias = torch.zeros(co, device="cuda")
+        y = torch.empty((B, h, w, co), dtype=torch.bfloat16, device="cuda")
+        dy = torch.randn((B, h, w, co), device="cuda", generator=g).to(torch.bfloat16)
+        dw = torch.zeros((co, 9, ci), device="cuda")
+        npx = B * h * w
+        ktiles = (9 * ci + 127) // 128
+        splits = max(1, min(npx // 512, 2 * 152 // ktiles + 1))
+
+        def fwd():
+            if L.mc_nn_conv3x3(ptr(x), ptr(wt), ptr(bias), ptr(y), B, h, w, ci, co, 1, 0, ptr(err), sh):
+                raise RuntimeError("mc_nn_conv3x3 failed")
+
+        def wgrad():
+            if L.mc_nn_conv3x3_wgrad(ptr(x), ptr(dy), ptr(dw), B, h, w, ci, co, splits, ptr(err), sh):
+                raise RuntimeError("mc_nn_conv3x3_wgrad failed")
+
+        flop = 2.0 * 9 * ci * co * npx
+        tf, tw = timed(fwd), timed(wgrad)
+        layers.append({"layer": i, "cin": ci, "cout": co, "hw": f"{h}x{w}", "fwd_ms": tf, "fwd_tflops": flop / tf / 1e9,
+                       "wgrad_ms": tw, "wgrad_tflops": flop / tw / 1e9, "wgrad_splits": splits})
+        fl_f += flop
+        ms_f += tf
+        fl_w += flop
+        ms_w += tw
+    torch.cuda.synchronize()
+    if int(err.item()):
+        raise RuntimeError("a tensor-core wait gave up")
+    ctx = mcx.Context(0)
+    ctx.denoise_init(H, W, B, seed=1)
+    imgs = torch.rand((B, H, W), device="cuda", generator=g) + 0.5
+    out = torch.empty_like(imgs)
+    t_batch = timed(lambda: ctx.denoise_infer(imgs, out=out, stream=stream))
+    t_one = timed(lambda: ctx.denoise_infer(imgs[:1], out=out[:1], stream=stream))
+    net_flop = sum(2.0 * 9 * ci * co * (H >> lv) * (W >> lv) for ci, co, lv in UNET_CONVS)
+    best = max(layers, key=lambda r: r["fwd_tflops"])
+    line = {
+        "metric": "denoiser 3x3 convolution throughput (tcgen05 kind::f16, BF16 operands, FP32 accumulation)",
+        "value": fl_f / ms_f / 1e9, "unit": "TFLOP/s", "higher_is_better": True, "dtype": "bf16",
+        "config": {"workload": f"U-Net layer shapes at {H}x{W}, batch {B}", "reps": reps},
+        "roofline": {"bound": "tensor", "achieved": fl_f / ms_f / 1e9, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fl_f / ms_f / 1e9 / peak, "traffic": None,
+                     "kernel": "k_conv3x3_fwd over the 15 layer shapes (FLOP-weighted)",
+                     "peak_basis": "MEASURED_PEAKS bf16_tflops (cuBLAS burst)",
+                     "best_layer": {"layer": best["layer"], "tflops": best["fwd_tflops"],
+                                    "frac": best["fwd_tflops"] / peak}},
+        "wgrad": {"achieved": fl_w / ms_w / 1e9, "frac": fl_w / ms_w / 1e9 / peak},
+        "layers": layers,
+        "inference": {"batch": B, "batch_ms": t_batch, "one_image_ms": t_one,
+                      "net_gflop_per_image": net_flop / 1e9,
+                      "batch_tflops": B * net_flop / t_batch / 1e9, "one_image_tflops": net_flop / t_one / 1e9},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.denoise_eval:
         run_denoise_eval(args)
+    elif args.conv_bench:
+        run_conv_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

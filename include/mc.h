@@ -310,6 +310,16 @@ int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t pro
 int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm,
                               uint64_t seed, float *scatter_out, void *stream);
 
+/* Gather probe (measurement helper; no counterpart in the paper).  Launches
+ * grid x block threads (block a multiple of 32, <= 256); each performs
+ * 8 x rounds independent random 4-byte loads from buf[0 .. n_words) (device
+ * memory, n_words < 2^32) and writes one folded word to sink[thread] (device,
+ * grid x block words).  Timing it on a buffer the size of the packed voxel
+ * volume gives the random-gather rate at the memory level that volume lives in
+ * (L2 or HBM), the peak of the transport's voxel-gather roofline.  Asynchronous
+ * on `stream`.  Errors: INVALID_ARG, CUDA. */
+int mc_probe_gather(const void *buf, uint64_t n_words, int rounds, int grid, int block, uint32_t *sink, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ EXPORTED = [
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
     "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
+    "mc_probe_gather",
 ]
 
 
@@ -137,6 +138,7 @@ def library():
         L.mc_nn_conv3x3_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
         L.mc_correct_iter.argtypes = [P, vp, vp, i, vp, i, i, i, C.POINTER(CorrectParams), vp, vp, vp, vp]
         L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
+        L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
         _lib = L
     return _lib
 
@@ -184,6 +186,19 @@ def conv3x3_wgrad(x, dy, splits=8, stream=None):
     if int(err.item()):
         raise MCError(-5, "a tensor-core wait gave up")
     return dw
+
+
+def probe_gather(buf, rounds, grid, block=256, stream=None):
+    """Random 4-byte gathers from the device tensor `buf` (mc_probe_gather); returns the sink tensor.
+    Asynchronous: time it with events on `stream`.  Loads issued: 8 x rounds x grid x block."""
+    import torch
+
+    n_words = buf.numel() * buf.element_size() // 4
+    sink = torch.empty(grid * block, dtype=torch.int32, device=buf.device)
+    rc = library().mc_probe_gather(_t_ptr(buf), n_words, rounds, grid, block, _t_ptr(sink), _stream_handle(stream))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_probe_gather failed")
+    return sink
 
 
 def _stream_handle(stream):
