@@ -34,8 +34,8 @@ struct Layer {
   float *w = nullptr, *b = nullptr;    // FP32 master [cout][9][cin], [cout]
   float *gw = nullptr, *gb = nullptr;  // gradients
   float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;  // Adam moments
-  __nv_bfloat16* wb = nullptr;  // forward weights [cout][9 cin]
-  __nv_bfloat16* wt = nullptr;  // adjoint weights [cin][9 cout]
+  __nv_bfloat16* wb = nullptr;  // forward weights, tensor-core order [cin/8][9][cout][8]
+  __nv_bfloat16* wt = nullptr;  // adjoint weights, tensor-core order [cout/8][9][cin][8]
   size_t nw() const { return (size_t)cout * 9 * cin; }
 };
 
@@ -78,8 +78,11 @@ cudaError_t dalloc(Denoiser* d, T** p, size_t count) {
 
 size_t npix(const Denoiser* d, int n, int level) { return (size_t)n * (d->H >> level) * (d->W >> level); }
 
+// Output channels co0 .. co0 + cout of the operator whose packed weights `wts`
+// hold co_total output channels.
 cudaError_t conv(const Denoiser* d, const Layer& l, const __nv_bfloat16* x, const __nv_bfloat16* wts, const float* bias,
-                 void* y, int n, int level, int cin, int cout, bool relu, bool out_f32, cudaStream_t s) {
+                 void* y, int n, int level, int cin, int cout, int co_total, int co0, bool relu, bool out_f32,
+                 cudaStream_t s) {
   ConvParams p;
   p.x = x;
   p.wt = wts;
@@ -90,6 +93,8 @@ cudaError_t conv(const Denoiser* d, const Layer& l, const __nv_bfloat16* x, cons
   p.w = d->W >> level;
   p.cin = cin;
   p.cout = cout;
+  p.co_total = co_total;
+  p.co0 = co0;
   p.relu = relu ? 1 : 0;
   p.out_f32 = out_f32 ? 1 : 0;
   p.err = d->err;
@@ -109,7 +114,7 @@ cudaError_t forward(Denoiser* d, const float* img, int n, cudaStream_t s) {
   TRY(nn::pack_input(img, d->scale, n, hw, d->in0, s));
   const Layer* L = d->L;
   auto c = [&](int i, const __nv_bfloat16* x, void* y, bool f32 = false) {
-    return conv(d, L[i], x, L[i].wb, L[i].b, y, n, kLevel[i], L[i].cin, L[i].cout, L[i].relu, f32, s);
+    return conv(d, L[i], x, L[i].wb, L[i].b, y, n, kLevel[i], L[i].cin, L[i].cout, L[i].cout, 0, L[i].relu, f32, s);
   };
   TRY(c(0, d->in0, d->a0a));
   TRY(c(1, d->a0a, d->s0));
@@ -165,10 +170,8 @@ cudaError_t back(Denoiser* d, int i, int n, const __nv_bfloat16* x, const __nv_b
   TRY(launch_conv3x3_wgrad(wp, splits, s));
   if (gx) {
     const int c1 = split > 0 ? split : l.cin;
-    TRY(conv(d, l, d->gbuf, l.wt, nullptr, gx, n, lev, l.cout, c1, false, true, s));
-    if (gx2)
-      TRY(conv(d, l, d->gbuf, l.wt + (size_t)c1 * 9 * l.cout, nullptr, gx2, n, lev, l.cout, l.cin - c1, false, true,
-               s));
+    TRY(conv(d, l, d->gbuf, l.wt, nullptr, gx, n, lev, l.cout, c1, l.cin, 0, false, true, s));
+    if (gx2) TRY(conv(d, l, d->gbuf, l.wt, nullptr, gx2, n, lev, l.cout, l.cin - c1, l.cin, c1, false, true, s));
   }
   return cudaSuccess;
 }
@@ -202,10 +205,7 @@ cudaError_t backward(Denoiser* d, int n, cudaStream_t s) {
 
 cudaError_t refresh_weights(Denoiser* d, cudaStream_t s) {
   cudaError_t e;
-  for (auto& l : d->L) {
-    TRY(nn::to_bf16(l.w, l.nw(), l.wb, s));
-    TRY(nn::flip_transpose(l.w, l.cout, l.cin, l.wt, s));
-  }
+  for (auto& l : d->L) TRY(nn::pack_weights(l.w, l.cout, l.cin, l.wb, l.wt, s));
   return cudaSuccess;
 }
 
@@ -307,9 +307,9 @@ cudaError_t denoiser_train_step(Denoiser* d, const float* noisy, const float* cl
   d->step += 1;
   if (lr > 0.f) {
     for (auto& l : d->L) {
-      TRY(nn::adam(l.w, l.gw, l.mw, l.vw, l.nw(), lr, d->step, l.wb, s));
+      TRY(nn::adam(l.w, l.gw, l.mw, l.vw, l.nw(), lr, d->step, nullptr, s));
       TRY(nn::adam(l.b, l.gb, l.mb, l.vb, (size_t)l.cout, lr, d->step, nullptr, s));
-      TRY(nn::flip_transpose(l.w, l.cout, l.cin, l.wt, s));
+      TRY(nn::pack_weights(l.w, l.cout, l.cin, l.wb, l.wt, s));
     }
   }
   double loss = 0;
@@ -346,8 +346,7 @@ bool denoiser_set_layer(Denoiser* d, int i, const float* w, const float* b) {
   Layer& l = d->L[i];
   if (w) cudaMemcpy(l.w, w, l.nw() * 4, cudaMemcpyHostToDevice);
   if (b) cudaMemcpy(l.b, b, (size_t)l.cout * 4, cudaMemcpyHostToDevice);
-  nn::to_bf16(l.w, l.nw(), l.wb, 0);
-  nn::flip_transpose(l.w, l.cout, l.cin, l.wt, 0);
+  nn::pack_weights(l.w, l.cout, l.cin, l.wb, l.wt, 0);
   return cudaDeviceSynchronize() == cudaSuccess;
 }
 

@@ -1,20 +1,20 @@
 // 3x3 convolutions of the learned scatter denoiser on the tcgen05 tensor cores.
 //
 // Tensors are NHWC, BF16, with channel counts that are multiples of 16.
-//  - forward: implicit GEMM.  A CTA owns 128 output pixels (M) and all output
-//    channels (N <= 256, FP32 accumulators in tensor memory); K = 9 x C_in runs
-//    over (tap, channel) in stages of 64, gathered with zero padding into a
-//    shared-memory stage (two stages in flight), one thread issuing the MMAs
-//    and committing each stage to its mbarrier.  Epilogue: bias, optional ReLU,
-//    BF16 or FP32 store.
-//  - input gradient: the same kernel with the weights flipped in space and
-//    transposed in channels (a 3x3 'same' convolution's adjoint).
+//  - forward: implicit GEMM over shifted views of a halo tile fetched by the
+//    tensor memory accelerator (description at k_conv3x3_fwd); FP32
+//    accumulators in tensor memory; epilogue bias, optional ReLU, BF16 or FP32.
+//  - input gradient: the same kernel with the adjoint weights (flipped in space,
+//    transposed in channels: a 3x3 'same' convolution's adjoint).
 //  - weight gradient: dW[co][k] = sum_p dY[p][co] Xcol[p][k]; the tile is 128
 //    rows of k by N = C_out, the reduction over pixels runs in stages of 64
 //    pixels staged transposed into the K-major layout; CTAs split the pixels and
 //    add their FP32 partial tiles into dW.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "mc_internal.h"
 #include "mc_tc.cuh"
@@ -35,116 +35,204 @@ struct ConvSmem {
   static constexpr int bytes = 2 * stage_bytes + 1024;  // + alignment slack
 };
 
-__device__ __forceinline__ uint32_t tmem_cols(int n) { return n <= 32 ? 32u : (uint32_t)n; }
+// ---------------------------------------------------------------------------
+// Forward (and input-gradient) convolution.
+//
+// Tiling.  The image is cut into column strips of width ws = min(w, 128); a
+// strip with its one-pixel border (the neighbouring strips' columns, or zeros
+// at the image edge) and a zero row above and below is the "padded strip", of
+// width wp = ws + 2, linearised row-major.  A CTA computes A x 128 consecutive
+// positions q of one padded strip (A accumulators of 128 rows x N output
+// channels in tensor memory); positions on the border are computed and
+// discarded.  For tap (dy, dx) the input of position q sits at q + dy*wp + dx,
+// so with the input tile ("halo": the rows of the padded strip that cover
+// [q0 - wp - 1, q0 + 128A + wp]) stored as [8-channel group][position][8] --
+// 16-byte rows, consecutive positions 16 bytes apart -- every tap's A operand
+// is the same tile seen from a start address shifted by (dy*wp + dx) * 16
+// bytes.  Each 16-byte chunk of input is fetched once per CTA instead of nine
+// times, and the tensor memory accelerator fetches it: one tiled 4-D copy per
+// 8-channel group, zero-filled outside the image.
+//
+// Pipeline.  The reduction runs over the input channels in chunks of CC; a
+// chunk's stage holds its halo and its weights for all nine taps (the packed
+// operand order wm[ci/8][tap][co][ci%8] makes that one contiguous block).
+// Warp 0 lane 0 fills a ring of `stages` stages (mbarrier `full`), warp 1
+// lane 0 issues the MMAs (9 taps x CC/16 k-steps x A accumulators per stage)
+// and frees each stage with tcgen05.commit (mbarrier `empty`); after the last
+// stage all four warps read their accumulator rows (tensor-memory lanes) and
+// store bias + optional ReLU, BF16 or FP32.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 8;
+constexpr int kSmemBudget = 225 * 1024;
+
+struct FwdArgs {
+  const __nv_bfloat16* wm;  // packed weights [cin/8][9][co_total][8]
+  const float* bias;        // [cout] or null
+  void* y;                  // [n][h][w][cout]
+  int n, h, w, cin, cout, co_total, co0;
+  int ws, strips, wp, tiles;  // strip width, strips per row, padded width, tiles per strip
+  int A, CC, stages, rbox;    // accumulators, channels per stage, ring depth, halo rows per copy
+  uint32_t lbo_a;             // bytes of one 8-channel group of the halo (multiple of 128)
+  uint32_t halo_bytes, stage_bytes;
+  int relu, out_f32;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t tmem_cols(int n) {
+  uint32_t c = 32;
+  while (c < (uint32_t)n) c <<= 1;
+  return c;
+}
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_conv3x3_fwd(const ConvParams p) {
+__global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_constant__ CUtensorMap xmap, const FwdArgs a) {
   extern __shared__ unsigned char dyn_raw[];
-  unsigned char* dyn = reinterpret_cast<unsigned char*>(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
   __shared__ uint32_t tmem_holder;
-  __shared__ __align__(8) uint64_t mbar[2];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int K = 9 * p.cin;
-  const int n_stages = (K + kStageK - 1) / kStageK;
-  const long long npix = (long long)p.n * p.h * p.w;
-  const long long pix0 = (long long)blockIdx.x * kM;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) tc::tmem_alloc(&tmem_holder, tmem_cols(N));
+  int tile = blockIdx.x;
+  const int t = tile % a.tiles;
+  tile /= a.tiles;
+  const int strip = tile % a.strips;
+  const int img = tile / a.strips;
+  const int nb = blockIdx.y * N;  // first output channel of this CTA (within the launch's cout)
+  const int Mt = 128 * a.A;
+  const int q0 = a.wp + 1 + t * Mt;           // first position: row 1, column 1 of the padded strip
+  const int vr_lo = (q0 - a.wp - 1) / a.wp;   // first halo row (padded-strip row index)
+  const int o0 = q0 - vr_lo * a.wp;           // halo index of q0
+  const int n_chunks = a.cin / a.CC;
+  const uint32_t ncols = tmem_cols(a.A * N);
+
+  if (warp == 0) tc::tmem_alloc(&tmem_holder, ncols);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < a.stages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&done, 1);
+    abort_flag = 0;
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_holder;
 
-  // this thread's pixel (row of the A tile)
-  const long long pr = pix0 + tid;
-  const bool row_ok = pr < npix;
-  int py = 0, px = 0, pn = 0;
-  if (row_ok) {
-    px = (int)(pr % p.w);
-    const long long t = pr / p.w;
-    py = (int)(t % p.h);
-    pn = (int)(t / p.h);
-  }
-  bool ok = true;
-  for (int st = 0; st < n_stages; ++st) {
-    const int buf = st & 1;
-    unsigned char* sA = dyn + buf * ConvSmem<N>::stage_bytes;
-    unsigned char* sB = sA + ConvSmem<N>::a_bytes;
-    if (st >= 2) ok &= tc::mbar_wait(&mbar[buf], (uint32_t)((st >> 1) - 1) & 1u);
-    const int k0 = st * kStageK;
-    // A: row = tid, eight 8-channel groups of (tap, channel)
-#pragma unroll
-    for (int kg = 0; kg < kKG; ++kg) {
-      const int k = k0 + kg * 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (row_ok && k < K) {
-        const int tap = k / p.cin, c = k - tap * p.cin;
-        const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-        if (yy >= 0 && yy < p.h && xx >= 0 && xx < p.w)
-          v = __ldg(reinterpret_cast<const uint4*>(p.x + (((long long)pn * p.h + yy) * p.w + xx) * p.cin + c));
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: halo by tensor copies, weights by one bulk copy per chunk
+      const int rows = min(N, a.cout - nb);  // weight rows this CTA needs
+      const int r0 = a.co0 + nb;
+      const bool one_block = rows == N && N == a.co_total;
+      const uint32_t w_tx = (uint32_t)(a.CC / 8) * 9u * (uint32_t)rows * 16u;
+      const uint32_t halo_tx = (uint32_t)(a.CC / 8) * 16u * (uint32_t)a.wp * (uint32_t)a.rbox;
+      int issued = 0;
+      for (int st = 0; st < n_chunks; ++st) {
+        const int slot = st % a.stages;
+        if (st >= a.stages && !tc::mbar_wait(&empty[slot], (uint32_t)((st / a.stages) - 1) & 1u)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        unsigned char* hs = sm + (size_t)slot * a.stage_bytes;
+        unsigned char* wsm = hs + a.halo_bytes;
+        tc::mbar_expect_tx(&full[slot], halo_tx + w_tx);
+        const int g0 = st * (a.CC / 8);  // first 8-channel group of the chunk
+        for (int kc = 0; kc < a.CC / 8; ++kc)
+          tc::tma_load_4d(hs + (size_t)kc * a.lbo_a, &xmap, &full[slot], (g0 + kc) * 8, strip * a.ws - 1, vr_lo - 1,
+                          img);
+        if (one_block) {
+          tc::bulk_load(wsm, a.wm + (size_t)g0 * 9 * a.co_total * 8, w_tx, &full[slot]);
+        } else {
+          for (int kc = 0; kc < a.CC / 8; ++kc)
+            for (int tap = 0; tap < 9; ++tap)
+              tc::bulk_load(wsm + (size_t)((kc * 9 + tap) * N) * 16,
+                            a.wm + ((size_t)((g0 + kc) * 9 + tap) * a.co_total + r0) * 8, (uint32_t)rows * 16u,
+                            &full[slot]);
+        }
+        ++issued;
       }
-      *reinterpret_cast<uint4*>(sA + tc::canon_off(tid, kg * 8, kKG)) = v;
-    }
-    // B: N rows of the weights, K-major
-    for (int q = tid; q < N * kKG; q += kThreads) {
-      const int row = q / kKG, kg = q - row * kKG;
-      const int k = k0 + kg * 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (k < K && row < p.cout) v = __ldg(reinterpret_cast<const uint4*>(p.wt + (long long)row * K + k));
-      *reinterpret_cast<uint4*>(sB + tc::canon_off(row, kg * 8, kKG)) = v;
-    }
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const int nks = min(kStageK, K - k0) / 16;
-      const uint32_t idesc = tc::idesc_bf16(kM, N);
-      for (int ks = 0; ks < nks; ++ks) {
-        const uint64_t da = tc::sdesc(tc::saddr(sA) + ks * 256, 128, kKG * 128);
-        const uint64_t db = tc::sdesc(tc::saddr(sB) + ks * 256, 128, kKG * 128);
-        tc::mma_bf16(tmem, da, db, idesc, (st > 0 || ks > 0) ? 1u : 0u);
+      if (abort_flag) {
+        // let the copies still in flight land before the CTA can exit
+        for (int st = max(0, issued - a.stages); st < issued; ++st)
+          tc::mbar_wait(&full[st % a.stages], (uint32_t)(st / a.stages) & 1u);
       }
-      tc::commit(&mbar[buf]);
     }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t idesc = tc::idesc_bf16(128, N);
+      const uint32_t lbo_b = 9u * N * 16u;
+      for (int st = 0; st < n_chunks; ++st) {
+        const int slot = st % a.stages;
+        if (!tc::mbar_wait(&full[slot], (uint32_t)(st / a.stages) & 1u)) {
+          abort_flag = 1;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t hb = tc::saddr(sm + (size_t)slot * a.stage_bytes);
+        const uint32_t wb = hb + a.halo_bytes;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int shift = (tap / 3 - 1) * a.wp + (tap % 3 - 1);
+          for (int ks = 0; ks < a.CC / 16; ++ks) {
+            const uint64_t db = tc::sdesc(wb + (uint32_t)((2 * ks * 9 + tap) * N) * 16u, lbo_b, 128);
+            const uint32_t abase = hb + (uint32_t)(2 * ks) * a.lbo_a;
+            for (int acc = 0; acc < a.A; ++acc) {
+              const uint64_t da = tc::sdesc(abase + (uint32_t)(o0 + 128 * acc + shift) * 16u, a.lbo_a, 128);
+              tc::mma_bf16(tmem + (uint32_t)(acc * N), da, db, idesc, (st | tap | ks) ? 1u : 0u);
+            }
+          }
+        }
+        tc::commit(&empty[slot]);
+      }
+      tc::commit(&done);
+    }
+    __syncwarp();
   }
-  const int last = n_stages - 1;
-  ok &= tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u);
-  // the other buffer's last commit precedes the final one, so it is complete too
+  bool ok = tc::mbar_wait(&done, 0);
   tc::fence_after();
-  if (!ok && tid == 0) atomicOr(p.err, 1);
+  ok = ok && !abort_flag;
+  if (!ok && tid == 0) atomicOr(a.err, 1);
   if (ok) {
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int acc = 0; acc < a.A; ++acc) {
+      const int q = q0 + 128 * acc + tid;
+      const int vr = q / a.wp, vc = q - vr * a.wp;
+      const int y = vr - 1, x = strip * a.ws + vc - 1;
+      const bool valid = vr >= 1 && vr <= a.h && vc >= 1 && vc <= a.ws && x < a.w;
+      const long long pix = ((long long)img * a.h + y) * a.w + x;
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 8) {
-      float v[8];
-      tc::tmem_ld8(lane_base + (uint32_t)c0, v);
-      if (row_ok && c0 < p.cout) {
+      for (int c0 = 0; c0 < N; c0 += 8) {
+        float v[8];
+        tc::tmem_ld8(lane_base + (uint32_t)(acc * N + c0), v);
+        const int co = nb + c0;
+        if (valid && co < a.cout) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (p.bias) v[j] += __ldg(p.bias + c0 + j);
-          if (p.relu) v[j] = fmaxf(v[j], 0.f);
-        }
-        if (p.out_f32) {
-          float* dst = reinterpret_cast<float*>(p.y) + pr * p.cout + c0;
-          *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-          *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
-        } else {
-          __nv_bfloat162 b[4];
+          for (int j = 0; j < 8; ++j) {
+            if (a.bias) v[j] += __ldg(a.bias + co + j);
+            if (a.relu) v[j] = fmaxf(v[j], 0.f);
+          }
+          if (a.out_f32) {
+            float* dst = reinterpret_cast<float*>(a.y) + pix * a.cout + co;
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
+          } else {
+            __nv_bfloat162 b[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-          *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.y) + pr * p.cout + c0) =
-              *reinterpret_cast<uint4*>(b);
+            for (int j = 0; j < 4; ++j) b[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + pix * a.cout + co) =
+                *reinterpret_cast<uint4*>(b);
+          }
         }
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, tmem_cols(N));
+  if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
 // Weight gradient.  CTA (blockIdx.x = k tile, blockIdx.y = pixel split).
@@ -247,13 +335,128 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p)
   if (warp == 0) tc::tmem_free(tmem, tmem_cols(N));
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// Tiling of one launch.  For each accumulator count A (A x N tensor-memory
+// columns <= 512): the channel chunk CC and ring depth that fit shared memory
+// (prefer >= 3 stages or every chunk resident, then larger chunks); then the A
+// with the smallest estimated time, waves x (positions per CTA + halo rows +
+// a fixed per-CTA cost), waves counted with the CTAs that fit on one SM.
+bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int& grid_y, int& smem) {
+  a.ws = p.w < 128 ? p.w : 128;
+  a.strips = (p.w + a.ws - 1) / a.ws;
+  a.wp = a.ws + 2;
+  grid_y = (p.cout + N - 1) / N;
+  double best_cost = -1.0;
+  for (int A = 8; A >= 1; A >>= 1) {
+    if (A * N > 512) continue;
+    const int Mt = 128 * A;
+    const int rbox = (Mt + 2 * a.wp + 1) / a.wp + 2;
+    if (rbox > 256) continue;
+    const int tiles = ((p.h - 1) * a.wp + a.ws + Mt - 1) / Mt;
+    const long long grid = (long long)p.n * a.strips * tiles * grid_y;
+    if (grid / grid_y > 0x7FFFFFFF) continue;
+    const uint32_t lbo = ((uint32_t)rbox * a.wp * 16u + 127u) & ~127u;
+    int bestCC = 0, bestStages = 0, bestScore = -1;
+    uint32_t bestStage = 0;
+    for (int CC = 64; CC >= 16; CC >>= 1) {
+      if (p.cin % CC) continue;
+      const uint32_t stage = (((uint32_t)(CC / 8) * lbo + (uint32_t)CC * 9u * N * 2u) + 1023u) & ~1023u;
+      const int chunks = p.cin / CC;
+      int stages = (int)((kSmemBudget - 1024) / stage);
+      if (stages > kMaxStages) stages = kMaxStages;
+      if (stages > chunks) stages = chunks;
+      if (stages < 1 || (stages < 2 && chunks > 1)) continue;
+      const int score = (stages >= 3 || stages == chunks ? 100 : 0) + CC;
+      if (score > bestScore) {
+        bestScore = score;
+        bestCC = CC;
+        bestStages = stages;
+        bestStage = stage;
+      }
+    }
+    if (bestScore < 0) continue;
+    const int bytes = (int)(bestStage * bestStages) + 1024;
+    int per_sm = (228 * 1024) / (bytes + 1024);
+    const int by_tmem = 512 / (int)(A * N <= 32 ? 32 : A * N);
+    if (per_sm > by_tmem) per_sm = by_tmem;
+    if (per_sm < 1) per_sm = 1;
+    const long long slots = (long long)sms * per_sm;
+    const double waves = (double)((grid + slots - 1) / slots);
+    const double cost = waves * (Mt + 2.0 * a.wp + 256.0);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      a.A = A;
+      a.CC = bestCC;
+      a.stages = bestStages;
+      a.rbox = rbox;
+      a.tiles = tiles;
+      a.lbo_a = lbo;
+      a.halo_bytes = (uint32_t)(bestCC / 8) * lbo;
+      a.stage_bytes = bestStage;
+      grid_x = (int)(grid / grid_y);
+      smem = bytes;
+    }
+  }
+  return best_cost >= 0;
+}
+
 template <int N>
 cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
-  const int smem = ConvSmem<N>::bytes;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  FwdArgs a{};
+  int gx = 0, gy = 0, smem = 0;
+  if (!plan_fwd(p, N, sms, a, gx, gy, smem)) return cudaErrorInvalidValue;
+  a.wm = p.wt;
+  a.bias = p.bias;
+  a.y = p.y;
+  a.n = p.n;
+  a.h = p.h;
+  a.w = p.w;
+  a.cin = p.cin;
+  a.cout = p.cout;
+  a.co_total = p.co_total;
+  a.co0 = p.co0;
+  a.relu = p.relu;
+  a.out_f32 = p.out_f32;
+  a.err = p.err;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)p.cin, (cuuint64_t)p.w, (cuuint64_t)p.h, (cuuint64_t)p.n};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.cin * 2, (cuuint64_t)p.cin * 2 * p.w, (cuuint64_t)p.cin * 2 * p.w * p.h};
+  const cuuint32_t box[4] = {8u, (cuuint32_t)a.wp, (cuuint32_t)a.rbox, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p.x, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_conv3x3_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const long long npix = (long long)p.n * p.h * p.w;
-  k_conv3x3_fwd<N><<<(unsigned)((npix + kM - 1) / kM), kThreads, smem, s>>>(p);
+  k_conv3x3_fwd<N><<<dim3((unsigned)gx, (unsigned)gy), kThreads, smem, s>>>(map, a);
   return cudaGetLastError();
 }
 
@@ -269,9 +472,13 @@ cudaError_t launch_wgrad_n(const WgradParams& p, int splits, cudaStream_t s) {
 
 }  // namespace
 
-// N = cout rounded up to the tile widths 16/32/64/128/256 (cout multiple of 16).
+// N = the launch's cout rounded up to the tile widths 16/32/64/128/256 (cout a
+// multiple of 16; wider outputs are split over blockIdx.y).  x must be 16-byte
+// aligned; wt is the packed operand order [cin/8][9][co_total][8].
 cudaError_t launch_conv3x3_fwd(const ConvParams& p, cudaStream_t s) {
-  if (p.cin % 16 || p.cout % 16 || p.cout > 256 || p.cin < 16) return cudaErrorInvalidValue;
+  if (p.cin % 16 || p.cout % 16 || p.cin < 16 || p.cout < 16 || p.co_total < p.co0 + p.cout || p.n < 1 || p.h < 1 ||
+      p.w < 1 || ((uintptr_t)p.x & 15) || ((uintptr_t)p.wt & 15))
+    return cudaErrorInvalidValue;
   if (p.cout <= 16) return launch_fwd_n<16>(p, s);
   if (p.cout <= 32) return launch_fwd_n<32>(p, s);
   if (p.cout <= 64) return launch_fwd_n<64>(p, s);

@@ -11,6 +11,8 @@ namespace {
 
 __device__ __forceinline__ size_t gtid() { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ size_t gstride() { return (size_t)gridDim.x * blockDim.x; }
+__device__ __forceinline__ __nv_bfloat16 to_bf(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __nv_bfloat16 to_bf(__nv_bfloat16 v) { return v; }
 
 int blocks_for(size_t n) {
   const size_t b = (n + 255) / 256;
@@ -209,18 +211,24 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   }
 }
 
-__global__ void k_to_bf16(const float* __restrict__ x, size_t n, __nv_bfloat16* __restrict__ y) {
-  for (size_t i = gtid(); i < n; i += gstride()) y[i] = __float2bfloat16_rn(x[i]);
-}
-
-// Adjoint weights of a 3x3 'same' convolution: wt[ci][tap][co] = w[co][8 - tap][ci].
-__global__ void k_flip_transpose(const float* __restrict__ w, int cout, int cin, __nv_bfloat16* __restrict__ wt) {
+// Weights in the operand order of the tensor-core convolution (k_conv.cu):
+// wm[ci / 8][tap][co][ci % 8], i.e. for every 8-channel input group and tap a
+// column of 16-byte rows, one per output channel.  wf: the forward operator
+// from w[co][tap][ci].  wa: the adjoint (input gradient of a 3x3 'same'
+// convolution), the operator with C_in' = cout, C_out' = cin and weights
+// w'[ci][tap][co] = w[co][8 - tap][ci], in the same order:
+// wa[co / 8][tap][ci][co % 8].  Either output may be null.
+template <class T>
+__global__ void k_pack_weights(const T* __restrict__ w, int cout, int cin, __nv_bfloat16* __restrict__ wf,
+                               __nv_bfloat16* __restrict__ wa) {
   const size_t n = (size_t)cout * 9 * cin;
   for (size_t i = gtid(); i < n; i += gstride()) {
-    const int co = (int)(i % cout);
-    size_t t = i / cout;
-    const int tap = (int)(t % 9), ci = (int)(t / 9);
-    wt[i] = __float2bfloat16_rn(w[((size_t)co * 9 + (8 - tap)) * cin + ci]);
+    const int ci = (int)(i % cin);
+    const size_t t = i / cin;
+    const int tap = (int)(t % 9), co = (int)(t / 9);
+    const __nv_bfloat16 v = to_bf(w[i]);
+    if (wf) wf[(((size_t)(ci >> 3) * 9 + tap) * cout + co) * 8 + (ci & 7)] = v;
+    if (wa) wa[(((size_t)(co >> 3) * 9 + (8 - tap)) * cin + ci) * 8 + (co & 7)] = v;
   }
 }
 
@@ -281,9 +289,11 @@ cudaError_t adam(float* w, const float* g, float* m, float* v, size_t n, float l
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
   NN_LAUNCH(k_adam, n, w, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2, wb);
 }
-cudaError_t to_bf16(const float* x, size_t n, __nv_bfloat16* y, cudaStream_t s) { NN_LAUNCH(k_to_bf16, n, x, n, y); }
-cudaError_t flip_transpose(const float* w, int cout, int cin, __nv_bfloat16* wt, cudaStream_t s) {
-  NN_LAUNCH(k_flip_transpose, (size_t)cout * 9 * cin, w, cout, cin, wt);
+cudaError_t pack_weights(const float* w, int cout, int cin, __nv_bfloat16* wf, __nv_bfloat16* wa, cudaStream_t s) {
+  NN_LAUNCH(k_pack_weights<float>, (size_t)cout * 9 * cin, w, cout, cin, wf, wa);
+}
+cudaError_t pack_weights_bf16(const __nv_bfloat16* w, int cout, int cin, __nv_bfloat16* wf, cudaStream_t s) {
+  NN_LAUNCH(k_pack_weights<__nv_bfloat16>, (size_t)cout * 9 * cin, w, cout, cin, wf, nullptr);
 }
 
 }  // namespace nn

@@ -15,6 +15,7 @@
 
 #include "mc_device.cuh"
 #include "mc_internal.h"
+#include "mc_nn.h"
 
 using namespace mcx;
 
@@ -1177,17 +1178,29 @@ int mc_nn_conv3x3(const void* x, const void* w, const float* bias, void* y, int 
                   int relu, int out_f32, int* err, void* stream) {
   if (!x || !w || !y || !err || n < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256)
     return MC_ERR_INVALID_ARG;
-  ConvParams p;
-  p.x = (const __nv_bfloat16*)x;
-  p.wt = (const __nv_bfloat16*)w;
-  p.bias = bias;
-  p.y = y;
-  p.n = n; p.h = h; p.w = wd; p.cin = cin; p.cout = cout;
-  p.relu = relu; p.out_f32 = out_f32;
-  p.err = err;
+  if ((uintptr_t)x & 15) return MC_ERR_INVALID_ARG;
   (void)cudaGetLastError();
-  const cudaError_t e = launch_conv3x3_fwd(p, (cudaStream_t)stream);
-  return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+  const cudaStream_t st = (cudaStream_t)stream;
+  // the kernel reads the weights in tensor-core operand order: repack them
+  // into a stream-ordered temporary
+  __nv_bfloat16* wm = nullptr;
+  if (cudaMallocAsync((void**)&wm, (size_t)cout * 9 * cin * 2, st) != cudaSuccess) return MC_ERR_OOM;
+  cudaError_t e = nn::pack_weights_bf16((const __nv_bfloat16*)w, cout, cin, wm, st);
+  if (e == cudaSuccess) {
+    ConvParams p;
+    p.x = (const __nv_bfloat16*)x;
+    p.wt = wm;
+    p.bias = bias;
+    p.y = y;
+    p.n = n; p.h = h; p.w = wd; p.cin = cin; p.cout = cout;
+    p.co_total = cout; p.co0 = 0;
+    p.relu = relu; p.out_f32 = out_f32;
+    p.err = err;
+    e = launch_conv3x3_fwd(p, st);
+  }
+  const cudaError_t ef = cudaFreeAsync(wm, st);
+  if (e == cudaSuccess) e = ef;
+  return e == cudaSuccess ? MC_OK : (e == cudaErrorInvalidValue ? MC_ERR_INVALID_ARG : MC_ERR_CUDA);
 }
 
 int mc_nn_conv3x3_wgrad(const void* x, const void* dy, float* dw, int n, int h, int wd, int cin, int cout, int splits,

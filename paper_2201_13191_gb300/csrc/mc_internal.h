@@ -139,11 +139,12 @@ cudaError_t launch_lerp_upsample(const float* in, int nv, int nu, float* out, in
 // ---------------------------------------------------------------------------
 // Denoiser convolutions (k_conv.cu): NHWC BF16, channels multiples of 16.
 struct ConvParams {
-  const __nv_bfloat16* x;   // [n][h][w][cin]
-  const __nv_bfloat16* wt;  // [cout][9 * cin], k = tap * cin + c, tap = 3 * (dy + 1) + (dx + 1)
+  const __nv_bfloat16* x;   // [n][h][w][cin], 16-byte aligned
+  const __nv_bfloat16* wt;  // packed [cin/8][9][co_total][8], tap = 3 * (dy + 1) + (dx + 1)
   const float* bias;        // [cout] or null
   void* y;                  // [n][h][w][cout], BF16 or FP32
-  int n, h, w, cin, cout;
+  int n, h, w, cin, cout;   // cout: output channels of this launch, rows co0 .. co0 + cout of wt
+  int co_total, co0;
   int relu, out_f32;
   int* err;                 // set to 1 if a bounded wait gave up
 };

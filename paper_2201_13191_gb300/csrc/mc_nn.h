@@ -25,8 +25,10 @@ cudaError_t add_channels(const float* g, size_t npix, int ctot, int c_off, int c
 cudaError_t bias_grad(const __nv_bfloat16* gb, size_t npix, int c, float* db, cudaStream_t s);
 cudaError_t adam(float* w, const float* g, float* m, float* v, size_t n, float lr, int step, __nv_bfloat16* wb,
                  cudaStream_t s);
-cudaError_t to_bf16(const float* x, size_t n, __nv_bfloat16* y, cudaStream_t s);
-cudaError_t flip_transpose(const float* w, int cout, int cin, __nv_bfloat16* wt, cudaStream_t s);
+// Tensor-core operand order of the convolution weights (forward wf and adjoint
+// wa, either nullable): wf[ci/8][tap][co][ci%8], wa[co/8][8-tap][ci][co%8].
+cudaError_t pack_weights(const float* w, int cout, int cin, __nv_bfloat16* wf, __nv_bfloat16* wa, cudaStream_t s);
+cudaError_t pack_weights_bf16(const __nv_bfloat16* w, int cout, int cin, __nv_bfloat16* wf, cudaStream_t s);
 
 }  // namespace nn
 }  // namespace mcx

@@ -71,6 +71,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return done != 0;
 }
 
+// The next phase of `mbar` completes after one arrival (this one) and `bytes`
+// of asynchronous copies signalled on it.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(mbar)), "r"(bytes) : "memory");
+}
+// Tiled 4-D tensor copy global -> shared through the tensor memory accelerator
+// (coordinates innermost first; out-of-range elements are filled with zeros).
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, uint64_t* mbar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(saddr(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(mbar))
+      : "memory");
+}
+// Contiguous copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(mbar))
+               : "memory");
+}
+
 // 8 consecutive FP32 accumulator columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
