@@ -25,5 +25,6 @@ from .phantoms import (  # noqa: F401
     fp16_bits,
     fp16_values,
 )
-from .spectrum import kramers_spectrum, mono_spectrum  # noqa: F401
+from .spectrum import filtered_spectra, kramers_spectrum, mono_spectrum  # noqa: F401
+from .detector import flat_panel_response, table_response  # noqa: F401
 from .workloads import WORKLOADS, make_workload  # noqa: F401

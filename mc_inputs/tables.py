@@ -52,13 +52,16 @@ K_PE = 31.5  # barn keV^3, photoelectric constant
 # Element data: Z, standard atomic weight.
 ELEMENTS = {
     "H": (1, 1.008),
+    "Be": (4, 9.0122),
     "C": (6, 12.011),
     "N": (7, 14.007),
     "O": (8, 15.999),
     "Al": (13, 26.9815),
     "P": (15, 30.9738),
     "Ar": (18, 39.948),
+    "S": (16, 32.06),
     "Ca": (20, 40.078),
+    "Gd": (64, 157.25),
 }
 
 # Materials: name, nominal density (g/cm^3), elemental mass fractions.
@@ -149,6 +152,34 @@ def material_components(fracs):
         Z, A = ELEMENTS[el]
         rows.append((float(Z), frac / A, C_F * Z ** (-2.0 / 3.0)))
     return np.array(rows, dtype=np.float64)
+
+
+def composition_attenuation(fracs, E_keV):
+    """Mass attenuation (cm^2/g) of an elemental composition by the same closed
+    forms as the tables: (photoelectric, incoherent, coherent) at E_keV.  For
+    materials outside the table file (source window, detector layers)."""
+    E = np.atleast_1d(np.asarray(E_keV, dtype=np.float64))
+    kn = kn_sigma_per_electron(E)
+    pe = np.zeros_like(E)
+    inc = np.zeros_like(E)
+    coh = np.zeros_like(E)
+    for Z, wmol, b in material_components(fracs):
+        n_atoms = wmol * N_A
+        pe += n_atoms * K_PE * 1e-24 * Z**4 / E**3
+        inc += n_atoms * Z * kn
+        coh += np.pi * R0_CM**2 * N_A * wmol * Z**2 * coherent_integral(Z, b, E)
+    return pe, inc, coh
+
+
+def kn_energy_transfer_fraction(E_keV):
+    """Mean fraction of the photon energy given to the electron in a free-electron
+    Klein-Nishina scatter: int (1 - E'/E) dsigma / int dsigma (Gauss-Legendre in mu)."""
+    E = np.atleast_1d(np.asarray(E_keV, dtype=np.float64))
+    x, w = _gl()
+    a = E[:, None] / MEC2_KEV
+    ratio = 1.0 / (1.0 + a * (1.0 - x[None, :]))
+    ds = ratio**2 * (ratio + 1.0 / ratio - (1.0 - x[None, :] ** 2))
+    return ((1.0 - ratio) * ds * w[None, :]).sum(axis=1) / (ds * w[None, :]).sum(axis=1)
 
 
 def build_tables(n_E=150, E0=1.0, dE=1.0, materials=None, variant="full"):

@@ -53,6 +53,7 @@ def lib():
         L.orc_load_volume.argtypes = [P, P, P, i, i, i, d, d, d]
         L.orc_set_spectrum.argtypes = [P, P, P, i]
         L.orc_set_geometry.argtypes = [P, d, d, i, i, d, d]
+        L.orc_set_detector_response.argtypes = [P, P, i]
         L.orc_set_options.argtypes = [P, i, d, i, d]
         L.orc_primary.argtypes = [P, d, d, P, P]
         L.orc_scatter.argtypes = [P, d, u32, u64, u64, u64, d, u64, P, P, P, P, P]
@@ -115,6 +116,14 @@ class Oracle:
         w = np.ascontiguousarray(weights, dtype=np.float64)
         _chk(self.L.orc_set_spectrum(self.h, _ptr(w), _ptr(E), len(E)), "set_spectrum")
 
+    def set_detector_response(self, eta):
+        """eta at the table's energy nodes (keV per photon), or None for eta(E) = E."""
+        if eta is None:
+            _chk(self.L.orc_set_detector_response(self.h, None, 0), "set_detector_response")
+            return
+        e = np.ascontiguousarray(eta, dtype=np.float64)
+        _chk(self.L.orc_set_detector_response(self.h, _ptr(e), len(e)), "set_detector_response")
+
     def set_geometry(self, sod, sdd, nu, nv, pu, pv):
         self.nu, self.nv = nu, nv
         _chk(self.L.orc_set_geometry(self.h, sod, sdd, nu, nv, pu, pv), "set_geometry")
@@ -126,6 +135,8 @@ class Oracle:
         self.load_volume(wl["volume"])
         self.set_spectrum(wl["energies"], wl["weights"])
         self.set_geometry(**wl["geometry"])
+        if wl.get("detector_response") is not None:
+            self.set_detector_response(wl["detector_response"])
 
     def primary(self, angle, step):
         Ip = np.zeros((self.nv, self.nu))

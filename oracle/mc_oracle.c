@@ -22,8 +22,9 @@
  *     roulette, summed per eq. (Is).
  *
  * Readings of the paper that it implements (all listed in the design notes):
- * lengths in mm, energies in keV, eta(E) = E, images in expected detector
- * energy per pixel per source photon emitted into 4 pi; step rule = equal
+ * lengths in mm, energies in keV, eta(E) = E unless a detector response
+ * table is set (orc_set_detector_response, Sec. II-D.2), images in expected
+ * detector signal per pixel per source photon emitted into 4 pi; step rule = equal
  * subdivision of the clipped chord, nearest voxel at each step midpoint;
  * cross-section tables linear in E between their 1 keV nodes; counter-based
  * Philox4x32-10 random numbers (Salmon et al., SC'11) with a fixed draw order.
@@ -63,6 +64,8 @@ typedef struct {
   /* spectrum */
   int have_spectrum, n_bins;
   double *S, *Ebin;
+  /* detector response eta(E) at the table nodes (NULL: eta(E) = E) */
+  double *eta;
   /* geometry */
   int have_geometry, nu, nv;
   double sod, sdd, pu, pv;
@@ -144,11 +147,13 @@ int orc_create(orc_ctx **out) {
 void orc_destroy(orc_ctx *c) {
   if (!c) return;
   free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh);
-  free(c->mat); free(c->rho); free(c->S); free(c->Ebin);
+  free(c->mat); free(c->rho); free(c->S); free(c->Ebin); free(c->eta);
   free(c);
 }
 
 int orc_load_tables(orc_ctx *c, const char *path) {
+  free(c->eta); /* a response belongs to the previous tables' nodes */
+  c->eta = NULL;
   FILE *f = fopen(path, "rb");
   if (!f) return ORC_EIO;
   char magic[8];
@@ -249,6 +254,26 @@ int orc_set_spectrum(orc_ctx *c, const double *w, const float *E, int n) {
   return ORC_OK;
 }
 
+/* eta[n_E]: detector response at the table's energy nodes (keV per photon), or
+ * NULL for eta(E) = E.  Values must be finite and >= 0. */
+int orc_set_detector_response(orc_ctx *c, const double *eta, int n) {
+  if (!c->have_tables) return ORC_ESTATE;
+  if (!eta) {
+    free(c->eta);
+    c->eta = NULL;
+    return ORC_OK;
+  }
+  if (n != c->n_E) return ORC_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!(eta[i] >= 0.0) || !isfinite(eta[i])) return ORC_EINVAL;
+  double *e = malloc((size_t)n * sizeof(double));
+  if (!e) return ORC_EINVAL;
+  memcpy(e, eta, (size_t)n * sizeof(double));
+  free(c->eta);
+  c->eta = e;
+  return ORC_OK;
+}
+
 int orc_set_geometry(orc_ctx *c, double sod, double sdd, int nu, int nv, double pu, double pv) {
   if (!(sod > 0) || !(sdd > sod) || nu < 1 || nv < 1 || !(pu > 0) || !(pv > 0)) return ORC_EINVAL;
   c->sod = sod; c->sdd = sdd; c->nu = nu; c->nv = nv; c->pu = pu; c->pv = pv;
@@ -282,6 +307,17 @@ static double tab(const orc_ctx *c, const double *a, int m, double E) {
   const double *row = a + (size_t)m * c->n_E;
   return row[i] + f * (row[i + 1] - row[i]);
 }
+/* Detector response (Sec. II-D.2): the signal of a photon of energy E reaching
+ * the panel; eta(E) = E (energy integrating) unless a response table was set,
+ * which is then interpolated linearly between the table's nodes. */
+static double det_eta(const orc_ctx *c, double E) {
+  if (!c->eta) return E;
+  int i;
+  double f;
+  interp_idx(c, E, &i, &f);
+  return c->eta[i] + f * (c->eta[i + 1] - c->eta[i]);
+}
+
 /* total mass attenuation, cm^2/g */
 static double mu_rho_tot(const orc_ctx *c, int m, double E) {
   return tab(c, c->mu_pe, m, E) + tab(c, c->mu_in, m, E) + tab(c, c->mu_co, m, E);
@@ -563,7 +599,7 @@ static double primary_sum(const orc_ctx *c, const double *rhoL, double *tau_mean
     double tau = 0;
     for (int m = 0; m < c->n_mat; ++m)
       if (rhoL[m] != 0) tau += mu_rho_tot(c, m, c->Ebin[n]) * 0.1 * rhoL[m];
-    double e = c->S[n] * c->Ebin[n] * exp(-tau);
+    double e = c->S[n] * det_eta(c, c->Ebin[n]) * exp(-tau);
     sum += e;
     wtau += e * tau;
   }
@@ -762,7 +798,8 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
             double y[3] = {x[0] + t * w[0] - P.c[0], x[1] + t * w[1] - P.c[1], x[2] + t * w[2] - P.c[2]};
             double a = (y[0] * P.eu[0] + y[1] * P.eu[1] + y[2] * P.eu[2]) / c->pu + 0.5 * c->nu;
             double b = (y[0] * P.ev[0] + y[1] * P.ev[1] + y[2] * P.ev[2]) / c->pv + 0.5 * c->nv;
-            if (a >= 0 && a < c->nu && b >= 0 && b < c->nv) img[(size_t)floor(b) * c->nu + (size_t)floor(a)] += E * W;
+            if (a >= 0 && a < c->nu && b >= 0 && b < c->nv)
+              img[(size_t)floor(b) * c->nu + (size_t)floor(a)] += det_eta(c, E) * W;
           }
         }
         break;
@@ -794,7 +831,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
         double Ep;
         double p = orc_nee_pdf(c, type, mint, E, lam, &Ep);
-        double x0 = W * Ep * p * A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
+        double x0 = W * det_eta(c, Ep) * p * A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
         st[ST_NEE_RAYS] += 1;
         if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
           if (vr >= x0 / c->rr_threshold) {

@@ -326,11 +326,13 @@ BOX = dict(n=16, dv=4.0)
 BOX_GEO = dict(sod=100.0, sdd=250.0, nu=8, nv=8, pu=4.0, pv=4.0)
 
 
-def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=None):
+def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=None, eta=None):
     """Expected order-1 NEE image, integrated deterministically over source
     direction (detector-area Gauss-Legendre), depth along the source ray and
-    the target pixel area, with exact exponential attenuation in the box."""
+    the target pixel area, with exact exponential attenuation in the box.
+    eta: detector response (callable of E in keV); None for eta(E) = E."""
     T = tables if variant_tab is None else variant_tab
+    e_of = (lambda E: E) if eta is None else eta
     o = oracle_lib.Oracle(table_path)
     h = BOX["n"] * BOX["dv"] / 2.0
     rho = float(np.float16(1.0))
@@ -386,12 +388,12 @@ def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=N
                 r = 1.0 / (1.0 + alpha * (1.0 - lam))
                 Ep = E0 * r
                 p_c = r * r * (r + 1.0 / r - 1.0 + lam * lam) / oracle_lib.kn_norm(E0)
-                contrib = mu_in * Ep * p_c * np.exp(-mu_of(Ep) * ex) * geo_f
+                contrib = mu_in * e_of(Ep) * p_c * np.exp(-mu_of(Ep) * ex) * geo_f
                 # Rayleigh
                 K = (E0 / HC_KEVA) ** 2
                 f2 = _ff2(T.comps[MAT_WATER], 0.5 * K * (1.0 - lam))
                 p_r = (1.0 + lam * lam) * f2 / np.interp(E0, T.energies, T.I_coh[MAT_WATER])
-                contrib = contrib + mu_co * E0 * p_r * np.exp(-mu0 * ex) * geo_f
+                contrib = contrib + mu_co * e_of(E0) * p_r * np.exp(-mu0 * ex) * geo_f
                 img += wsrc * att * contrib.sum(axis=(-1, -2))
     return img
 
