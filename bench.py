@@ -51,10 +51,35 @@ def parse():
     p.add_argument("--per-angle", action="store_true", help="one mc_project call per angle instead of one batch")
     p.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--detector", default="energy", choices=["energy", "panel"],
+                   help="detector response: energy integrating (eta = E) or the flat-panel Gd2O2S model")
+    p.add_argument("--autotune", action="store_true",
+                   help="pick step (within --tune-step-min..max at --tune-tol primary error) and launch shape first")
+    p.add_argument("--tune-step-min", type=float, default=0.1)
+    p.add_argument("--tune-step-max", type=float, default=0.4)
+    p.add_argument("--tune-tol", type=float, default=0.005)
     p.add_argument("--denoise-eval", action="store_true",
                    help="seconds per projection at <= 2%% scatter error: plain MC vs smoothing vs learned denoiser")
     p.add_argument("--conv-bench", action="store_true",
                    help="tensor-core throughput of the denoiser's convolutions and its inference latency")
+    p.add_argument("--correct-eval", action="store_true", help="iterative scatter correction on a large flat panel")
+    p.add_argument("--cor-detector", type=int, default=2048)
+    p.add_argument("--cor-pixel", type=float, default=0.1)
+    p.add_argument("--cor-proj", type=int, default=1024)
+    p.add_argument("--cor-volume", type=int, default=512)
+    p.add_argument("--cor-voxel", type=float, default=0.2)
+    p.add_argument("--cor-seed", type=int, default=4242)
+    p.add_argument("--cor-phantom", default="cylinder", choices=["cylinder", "ellipsoids"],
+                   help="water cylinder with inserts (cupping) or the ellipsoid generator")
+    p.add_argument("--cor-step", type=float, default=0.2)
+    p.add_argument("--cor-meas-grid", type=int, default=256)
+    p.add_argument("--cor-meas-angles", type=int, default=32)
+    p.add_argument("--cor-meas-photons", type=float, default=1e8)
+    p.add_argument("--cor-total-photons", type=float, default=1e10)
+    p.add_argument("--cor-sim-grid", type=int, default=256)
+    p.add_argument("--cor-sim-angles", type=int, default=180)
+    p.add_argument("--cor-sim-photons", type=float, default=1e6)
+    p.add_argument("--cor-iters", type=int, default=3)
     p.add_argument("--conv-size", type=int, default=256)
     p.add_argument("--conv-batch", type=int, default=8)
     p.add_argument("--train-phantoms", type=int, default=96)
@@ -314,7 +339,19 @@ def run_ours(args):
     ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph))
     ctx.load_tables(tp)
     ctx.setup(wl)
+    if args.detector == "panel":
+        from mc_inputs import read_tables, table_response
+
+        ctx.set_detector_response(table_response(read_tables(tp)))
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        probe = angles[:: max(1, n_ang // 8)][:8]
+        tuned = ctx.autotune(probe, 2_000_000, args.tune_step_min, args.tune_step_max, args.tune_tol, stream=stream)
+        tuned["seconds"] = time.perf_counter() - t0
+        tuned["probe_angles"] = int(len(probe))
+        wl["step_mm"] = float(tuned["step_mm"])
     out = {"primary": ctx.empty_images(n_ang), "scatter": ctx.empty_images(n_ang)}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
@@ -424,7 +461,8 @@ def run_ours(args):
                        "photons_per_projection": N, "angles_per_step": n_ang,
                        "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
                        "step_mm": wl["step_mm"], "n_split": 10, "spectrum": f"{len(wl['weights'])} bins",
-                       "l2_flush": True, "parallelism": "replicas" if world > 1 else "single"},
+                       "l2_flush": True, "parallelism": "replicas" if world > 1 else "single",
+                       "autotune": tuned, "voxel_layout": args.voxel_layout, "detector": args.detector},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -666,12 +704,148 @@ def run_conv_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_correct_eval(args):
+    """Iterative scatter correction (Sec. II-E, eq. Correction) on a
+    high-resolution flat panel: per-iteration time and the cupping error of the
+    corrected reconstruction against the scatter-free one.
+
+    Measurements: exact primary (eq. Ip) on the full panel at every angle plus
+    Monte Carlo scatter simulated at a subset of angles on a coarse grid,
+    smoothed and interpolated to all angles and the full panel (the paper's own
+    interpolation step), with Poisson noise of the stated photon budget."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+    from mc_inputs import cylinder_variant_phantom, default_table_path, ellipsoid_phantom, mono_spectrum
+
+    mcx.build()
+    tp = default_table_path("full", tempfile.mkdtemp(prefix="mccor"))
+    NU = NV = args.cor_detector
+    P = args.cor_pixel
+    n_proj = args.cor_proj
+    nvx, dv = args.cor_volume, args.cor_voxel
+    SOD, SDD = 300.0, 600.0
+    step = args.cor_step
+    angles = (2.0 * np.pi * np.arange(n_proj) / n_proj).astype(np.float32)
+    if args.cor_phantom == "cylinder":
+        vol = cylinder_variant_phantom(args.cor_seed, n=nvx, dv=dv)
+    else:
+        vol = ellipsoid_phantom(n=nvx, dv=dv, seed=args.cor_seed)
+    E, w = mono_spectrum(60.0)
+    ctx = mcx.Context(0)
+    ctx.load_tables(tp)
+    ctx.set_spectrum(E, w)
+    ctx.set_geometry(SOD, SDD, NU, NV, P, P)
+    dev = torch.device("cuda")
+    t_meas = time.perf_counter()
+    # flat field: the primary of an empty volume
+    empty = np.zeros_like(vol["rho"])
+    ctx.load_volume(vol["mat"], empty, vol["spacing"])
+    I0 = ctx.project([0.0], 1, step, 1, scatter=False)["primary"][0].clone()
+    ctx.load_volume(vol["mat"], vol["rho"], vol["spacing"])
+    ip = torch.empty((n_proj, NV, NU), dtype=torch.float32, device=dev)
+    chunk = 64
+    for k in range(0, n_proj, chunk):
+        ctx.project(angles[k : k + chunk], 1, step, 1, scatter=False, out={"primary": ip[k : k + chunk]})
+    g = args.cor_meas_grid
+    meas_angles = angles[:: n_proj // args.cor_meas_angles]
+    ctx.set_geometry(SOD, SDD, g, g, P * NU / g, P * NV / g)
+    is_meas = ctx.project(meas_angles, int(args.cor_meas_photons), step, 77, primary=False)["scatter"]
+    ctx.set_geometry(SOD, SDD, NU, NV, P, P)
+    # measured intensity with Poisson noise: N0 photons per unattenuated pixel
+    N0 = args.cor_total_photons / (NU * NV)
+    raw = torch.empty_like(ip)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    for k in range(0, n_proj, chunk):
+        sl = slice(k, k + chunk)
+        isk = ctx.smooth_upsample(is_meas, meas_angles, angles[sl], NU, NV)
+        lam = N0 * (ip[sl] + isk) / I0
+        raw[sl] = torch.poisson(lam, generator=gen).clamp_min_(0.5) / N0 * I0
+        del isk, lam
+    torch.cuda.synchronize()
+    t_meas = time.perf_counter() - t_meas
+    grid = (nvx, nvx, nvx, dv, dv, dv)
+    # scatter-free and uncorrected reconstructions (line integrals computed in place)
+    sub = slice(0, n_proj, max(1, n_proj // 64))
+    a_ref_sub = -torch.log(ip[sub] / I0)
+    for k in range(0, n_proj, chunk):
+        ip[k : k + chunk] = -torch.log(ip[k : k + chunk] / I0)
+    v_ref = ctx.fdk(ip, angles, NU, NV, grid)
+    for k in range(0, n_proj, chunk):
+        ip[k : k + chunk] = -torch.log(raw[k : k + chunk] / I0)
+    a_raw_sub = ip[sub].clone()
+    v_raw = ctx.fdk(ip, angles, NU, NV, grid)
+    del ip
+    torch.cuda.empty_cache()
+    stride = max(1, int(round(n_proj / args.cor_sim_angles)))
+    prm = mcx.CorrectParams(nx=nvx, ny=nvx, nz=nvx, dx=dv, dy=dv, dz=dv, sim_nu=args.cor_sim_grid,
+                            sim_nv=args.cor_sim_grid, sim_angle_stride=stride, photons=int(args.cor_sim_photons),
+                            step_mm=step, seed=11, classes=3, class_material=(0, 1, 3), class_density0=0.001205,
+                            e_eff_keV=60.0, mu_lo=-0.01, mu_hi=0.12, primary_full_res=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, v_cor, secs = ctx.correct_iter(raw, I0, angles, NU, NV, args.cor_iters, prm)
+    torch.cuda.synchronize()
+    t_total = time.perf_counter() - t0
+    obj = torch.from_numpy(vol["mat"] != 0).to(dev)
+    soft = torch.from_numpy((vol["mat"] == 1) | (vol["mat"] == 2)).to(dev)
+
+    def verr(v, mask):
+        return float((v - v_ref)[mask].abs().mean() / v_ref[mask].abs().mean())
+
+    def aerr(a):
+        return float(torch.linalg.norm(a - a_ref_sub) / torch.linalg.norm(a_ref_sub))
+
+    def cupping(v):
+        """Radial profile of the central slice over water voxels: (ring - centre) / ring, in per cent,
+        with the centre r < 0.2 R and the ring 0.7 R < r < 0.9 R (R the water extent)."""
+        zc = nvx // 2
+        sl = v[zc]
+        water = torch.from_numpy(vol["mat"][zc] == 1).to(dev)
+        yy, xx = torch.meshgrid(torch.arange(nvx, device=dev), torch.arange(nvx, device=dev), indexing="ij")
+        r = torch.sqrt((xx - (nvx - 1) / 2.0) ** 2 + (yy - (nvx - 1) / 2.0) ** 2)
+        R = float(r[water].max()) if bool(water.any()) else 1.0
+        centre = water & (r < 0.2 * R)
+        ring = water & (r > 0.7 * R) & (r < 0.9 * R)
+        if not bool(centre.any()) or not bool(ring.any()):
+            return None
+        mc, mr = float(sl[centre].mean()), float(sl[ring].mean())
+        return 100.0 * (mr - mc) / mr
+
+    line = {
+        "metric": "iterative scatter correction: seconds per iteration and cupping error vs the scatter-free "
+                  "reconstruction",
+        "unit": "s/iteration", "higher_is_better": False, "dtype": "f32",
+        "value": float(np.mean(secs)) if secs else None,
+        "config": {"workload": f"{n_proj} projections of {NU}x{NV} at {P} mm, {nvx}^3 x {dv} mm {args.cor_phantom} "
+                               f"phantom (seed {args.cor_seed}), 60 keV, SOD/SDD {SOD:.0f}/{SDD:.0f}",
+                   "measurements": f"exact primary + Monte Carlo scatter at {len(meas_angles)} angles x "
+                                   f"{args.cor_meas_photons:.0e} photons on {g}^2, smoothed and interpolated; Poisson "
+                                   f"noise with {args.cor_total_photons:.0e} photons per projection",
+                   "iteration": f"FDK to {nvx}^3, Otsu 3 classes, primary on the full panel, scatter at "
+                                f"{len(range(0, n_proj, stride))} angles x {args.cor_sim_photons:.0e} photons on "
+                                f"{args.cor_sim_grid}^2, Savitzky-Golay, angular lerp + cubic up-sampling, eq. Correction",
+                   "iterations": args.cor_iters, "step_mm": step},
+        "seconds_per_iteration": secs, "seconds_total": t_total, "seconds_measurements": t_meas,
+        "cupping_error": {"uncorrected": verr(v_raw, obj), "corrected": verr(v_cor, obj),
+                          "uncorrected_soft_tissue": verr(v_raw, soft), "corrected_soft_tissue": verr(v_cor, soft),
+                          "definition": "mean |mu - mu_scatter_free| / mean |mu_scatter_free| over object voxels"},
+        "line_integral_rel_l2": {"uncorrected": aerr(a_raw_sub), "corrected": aerr(out[sub])},
+        "cupping_percent": {"scatter_free": cupping(v_ref), "uncorrected": cupping(v_raw), "corrected": cupping(v_cor),
+                            "definition": "central slice, water voxels: 100 (ring - centre) / ring, centre r < 0.2 R, "
+                                          "ring 0.7 R < r < 0.9 R"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.denoise_eval:
         run_denoise_eval(args)
     elif args.conv_bench:
         run_conv_bench(args)
+    elif args.correct_eval:
+        run_correct_eval(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

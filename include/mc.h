@@ -310,6 +310,16 @@ int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t pro
 int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm,
                               uint64_t seed, float *scatter_out, void *stream);
 
+/* Detector response (Sec. II-D.2: the model maps each detected photon energy
+ * through the panel's energy-response curve).  eta[n]: the expected signal
+ * (keV) of a photon of energy E reaching the panel, at the table's n_E energy
+ * nodes E0 + i dE (host FP64, n == n_E, finite, >= 0), linear between nodes.
+ * It replaces the default eta(E) = E (energy integrating) in eq. (Ip) --
+ * S(E_n) eta(E_n) per bin -- and in the point-detector score of eq. (Is) at the
+ * scattered energy E'.  eta == NULL restores the default; loading tables
+ * clears it.  Errors: STATE (no tables), INVALID_ARG. */
+int mc_set_detector_response(mc_ctx *ctx, const double *eta, int n);
+
 /* Gather probe (measurement helper; no counterpart in the paper).  Launches
  * grid x block threads (block a multiple of 32, <= 256); each performs
  * 8 x rounds independent random 4-byte loads from buf[0 .. n_words) (device

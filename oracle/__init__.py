@@ -54,6 +54,7 @@ def lib():
         L.orc_set_spectrum.argtypes = [P, P, P, i]
         L.orc_set_geometry.argtypes = [P, d, d, i, i, d, d]
         L.orc_set_detector_response.argtypes = [P, P, i]
+        L.orc_set_nee_mode.argtypes = [P, i]
         L.orc_set_options.argtypes = [P, i, d, i, d]
         L.orc_primary.argtypes = [P, d, d, P, P]
         L.orc_scatter.argtypes = [P, d, u32, u64, u64, u64, d, u64, P, P, P, P, P]
@@ -115,6 +116,10 @@ class Oracle:
         E = np.ascontiguousarray(energies, dtype=np.float32)
         w = np.ascontiguousarray(weights, dtype=np.float64)
         _chk(self.L.orc_set_spectrum(self.h, _ptr(w), _ptr(E), len(E)), "set_spectrum")
+
+    def set_nee_mode(self, mode):
+        """0: score the sampled scatter type (the paper's); 1: expected value over both types."""
+        _chk(self.L.orc_set_nee_mode(self.h, int(mode)), "set_nee_mode")
 
     def set_detector_response(self, eta):
         """eta at the table's energy nodes (keV per photon), or None for eta(E) = E."""

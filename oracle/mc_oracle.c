@@ -71,6 +71,7 @@ typedef struct {
   double sod, sdd, pu, pv;
   /* options */
   int n_split, max_order;
+  int nee_mode; /* 0: score the sampled scatter type; 1: expected value over both types */
   double rr_threshold, eps_face;
 } orc_ctx;
 
@@ -278,6 +279,19 @@ int orc_set_geometry(orc_ctx *c, double sod, double sdd, int nu, int nv, double 
   if (!(sod > 0) || !(sdd > sod) || nu < 1 || nv < 1 || !(pu > 0) || !(pv > 0)) return ORC_EINVAL;
   c->sod = sod; c->sdd = sdd; c->nu = nu; c->nv = nv; c->pu = pu; c->pv = pv;
   c->have_geometry = 1;
+  return ORC_OK;
+}
+
+/* Point-detector scoring mode.  0 (the paper's): at a Compton or Rayleigh
+ * interaction, score that type's scatter-toward-detector pdf.  1 (expected
+ * value over the interaction type): at every interaction, whatever type is
+ * then sampled for the photon's own continuation, score
+ * (mu_incoh/mu) x Compton term at E' + (mu_coh/mu) x Rayleigh term at E --
+ * the expectation of mode 0's score over the type draw, so the same mean with
+ * less variance. */
+int orc_set_nee_mode(orc_ctx *c, int mode) {
+  if (mode != 0 && mode != 1) return ORC_EINVAL;
+  c->nee_mode = mode;
   return ORC_OK;
 }
 
@@ -809,12 +823,12 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       double pe = tab(c, c->mu_pe, mint, E), in = tab(c, c->mu_in, mint, E), co = tab(c, c->mu_co, mint, E);
       double ut = rng_u(&g) * (pe + in + co);
       int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
-      if (type == 0) {
+      if (type == 0 && c->nee_mode == 0) {
         st[ST_PHOTO] += 1;
         e_dep += E * W;
         break;
       }
-      st[type == 1 ? ST_COMPTON : ST_RAYLEIGH] += 1;
+      if (type != 0) st[type == 1 ? ST_COMPTON : ST_RAYLEIGH] += 1;
       /* point-detector scoring, split into n_split pseudo-particles, eq. (Th) */
       rng_align(&g);
       for (int s = 0; s < c->n_split; ++s) {
@@ -829,23 +843,54 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         double dir[3] = {DD[0] / dd, DD[1] / dd, DD[2] / dd};
         double lam = w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2];
         double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
-        double Ep;
-        double p = orc_nee_pdf(c, type, mint, E, lam, &Ep);
-        double x0 = W * det_eta(c, Ep) * p * A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
+        const double geo = A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
+        double sc;
         st[ST_NEE_RAYS] += 1;
-        if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
-          if (vr >= x0 / c->rr_threshold) {
-            st[ST_RR_KILLED] += 1;
-            continue;
+        if (c->nee_mode == 0) {
+          double Ep;
+          double p = orc_nee_pdf(c, type, mint, E, lam, &Ep);
+          double x0 = W * det_eta(c, Ep) * p * geo;
+          if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
+            if (vr >= x0 / c->rr_threshold) {
+              st[ST_RR_KILLED] += 1;
+              continue;
+            }
+            x0 = c->rr_threshold;
           }
-          x0 = c->rr_threshold;
+          long ns = 0;
+          double tp = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
+          st[ST_NEE_STEPS] += ns;
+          sc = x0 * exp(-tp);
+        } else {
+          /* expected value over the interaction type */
+          double Ep;
+          const double mu = pe + in + co;
+          double pc = orc_nee_pdf(c, 1, mint, E, lam, &Ep);
+          double pr = orc_nee_pdf(c, 2, mint, E, lam, NULL);
+          double xc = W * (in / mu) * det_eta(c, Ep) * pc * geo;
+          double xr = W * (co / mu) * det_eta(c, E) * pr * geo;
+          const double x0 = xc + xr;
+          if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
+            if (vr >= x0 / c->rr_threshold) {
+              st[ST_RR_KILLED] += 1;
+              continue;
+            }
+            xc *= c->rr_threshold / x0;
+            xr *= c->rr_threshold / x0;
+          }
+          long ns = 0, ns2 = 0;
+          double tc = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
+          double tr = march_tau(c, x, dir, 0.0, dd, step, E, &ns2);
+          st[ST_NEE_STEPS] += ns; /* one march's steps: both walk the same midpoints */
+          sc = xc * exp(-tc) + xr * exp(-tr);
         }
-        long ns = 0;
-        double tp = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
-        st[ST_NEE_STEPS] += ns;
-        double sc = x0 * exp(-tp);
         Is[pix] += sc;
         if (Is_order) Is_order[(size_t)(order < 2 ? order : 2) * npix + pix] += sc;
+      }
+      if (type == 0) { /* expected-value mode scored the absorption site; the photon ends */
+        st[ST_PHOTO] += 1;
+        e_dep += E * W;
+        break;
       }
       /* new direction */
       int fail = 0;

@@ -35,7 +35,7 @@ EXPORTED = [
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
     "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
-    "mc_probe_gather",
+    "mc_probe_gather", "mc_set_detector_response",
 ]
 
 
@@ -139,6 +139,7 @@ def library():
         L.mc_correct_iter.argtypes = [P, vp, vp, i, vp, i, i, i, C.POINTER(CorrectParams), vp, vp, vp, vp]
         L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
         L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
+        L.mc_set_detector_response.argtypes = [P, vp, i]
         _lib = L
     return _lib
 
@@ -282,11 +283,21 @@ class Context:
         self.nu, self.nv = nu, nv
         self._check(self.L.mc_set_geometry(self.h, sod, sdd, nu, nv, pu, pv))
 
+    def set_detector_response(self, eta):
+        """eta at the table's energy nodes (keV per photon, host), or None for eta(E) = E."""
+        if eta is None:
+            self._check(self.L.mc_set_detector_response(self.h, None, 0))
+            return
+        e = np.ascontiguousarray(eta, dtype=np.float64)
+        self._check(self.L.mc_set_detector_response(self.h, _np_ptr(e), len(e)))
+
     def setup(self, wl):
         v = wl["volume"]
         self.load_volume(v["mat"], v["rho"], v["spacing"])
         self.set_spectrum(wl["energies"], wl["weights"])
         self.set_geometry(**wl["geometry"])
+        if wl.get("detector_response") is not None:
+            self.set_detector_response(wl["detector_response"])
 
     def empty_images(self, n_angles):
         return self.torch.empty((n_angles, self.nv, self.nu), dtype=self.torch.float32, device=self.device)

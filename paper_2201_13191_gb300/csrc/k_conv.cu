@@ -420,13 +420,10 @@ bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int&
 
 template <int N>
 cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 1;
-  }
+  int dev0 = 0, sms = 0;
+  cudaGetDevice(&dev0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev0);
+  if (sms < 1) sms = 1;
   FwdArgs a{};
   int gx = 0, gy = 0, smem = 0;
   if (!plan_fwd(p, N, sms, a, gx, gy, smem)) return cudaErrorInvalidValue;
@@ -454,8 +451,16 @@ cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3x3_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static unsigned long long smem_set = 0;  // devices on which the attribute was raised
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(smem_set & bit)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_conv3x3_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 1024);
+    if (e != cudaSuccess) return e;
+    smem_set |= bit;
+  }
   k_conv3x3_fwd<N><<<dim3((unsigned)gx, (unsigned)gy), kThreads, smem, s>>>(map, a);
   return cudaGetLastError();
 }

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
 #pragma unroll
     for (int m = 0; m < kMaxMat; ++m)
       if (m < nm) tau = fmaf(s_mub[n * nm + m], rl[m], tau);
-    sum = fmaf(S * __ldg(P.spec.energy + n), expf(-tau), sum);
+    sum = fmaf(S * __ldg(P.spec.eta + n), expf(-tau), sum);
   }
   const float cosg = G.sdd / d;
   P.out[(size_t)a * npix + pix] = sum * (G.pu * G.pv) * cosg / (4.f * kPi * d * d);

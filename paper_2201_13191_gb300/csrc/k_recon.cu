@@ -28,31 +28,76 @@ __global__ void k_log_norm(const float* __restrict__ I, const float* __restrict_
   }
 }
 
-// FDK pre-weighting and ramp filtering of one detector row per block:
+// FDK pre-weighting and ramp filtering of detector rows:
 //   q(u_i) = du * sum_j h(i - j) * w(u_j, v) p(u_j),  w = D / sqrt(D^2 + u^2 + v^2)
 // with u, v the pixel-centre offsets scaled to the isocentre plane, D = SOD,
 // du the isocentre pixel pitch and h the discrete Ram-Lak kernel
 // h(0) = 1/(4 du^2), h(odd n) = -1/(n pi du)^2, h(even n != 0) = 0.
-__global__ void k_fdk_filter(const float* __restrict__ p, int nu, int nv, float du_iso, float dv_iso, float sod,
-                             float* __restrict__ q) {
-  extern __shared__ float row[];
-  const int r = blockIdx.x;  // row index over all projections: proj * nv + v
-  const int v = r % nv;
-  const float vv = ((float)v - 0.5f * (float)(nv - 1)) * dv_iso;
-  const float* src = p + (size_t)r * nu;
-  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-    const float uu = ((float)i - 0.5f * (float)(nu - 1)) * du_iso;
-    row[i] = src[i] * sod * rsqrtf(sod * sod + uu * uu + vv * vv);
+// A block filters kFiltRows rows; a warp owns 256 consecutive outputs (8 per
+// lane) of each of them.  Walking j, lane l needs the taps h(i0 + m - j),
+// m = 0..7, i0 = 8 l + warp base: one step in j shifts that window by one, so
+// the new first tap is the previous lane's last one (a shuffle) and only lane 0
+// reads a tap from shared memory.  The taps are shared by the rows, so each
+// tap register feeds kFiltRows x 8 FMAs.
+constexpr int kFiltOut = 8;
+constexpr int kFiltRows = 4;
+constexpr int kFiltThreads = 256;
+
+__global__ void __launch_bounds__(kFiltThreads) k_fdk_filter(const float* __restrict__ p, int nu, int nv, int rows_total,
+                                                             float du_iso, float dv_iso, float sod,
+                                                             float* __restrict__ q) {
+  extern __shared__ float fsh[];
+  const int span = kFiltThreads * kFiltOut;               // outputs per pass of the block
+  const int npad = (nu + span - 1) / span * span;
+  const int H0 = npad + kFiltOut;                          // hs[d + H0] = h(d), |d| <= H0
+  float* hs = fsh;
+  float* rows = fsh + 2 * H0 + 1;                          // [kFiltRows][nu]
+  const float h0 = 0.25f / (du_iso * du_iso), c = 1.f / (9.8696044f * du_iso * du_iso);
+  for (int k = threadIdx.x; k <= 2 * H0; k += blockDim.x) {
+    const int d = k - H0;
+    hs[k] = d == 0 ? h0 : ((d & 1) ? -c / ((float)d * (float)d) : 0.f);
+  }
+  const int r0 = blockIdx.x * kFiltRows;
+  for (int rr = 0; rr < kFiltRows; ++rr) {
+    const int r = r0 + rr;
+    const float vv = ((float)((r < rows_total ? r : 0) % nv) - 0.5f * (float)(nv - 1)) * dv_iso;
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+      const float uu = ((float)i - 0.5f * (float)(nu - 1)) * du_iso;
+      rows[rr * nu + i] = r < rows_total ? p[(size_t)r * nu + i] * sod * rsqrtf(sod * sod + uu * uu + vv * vv) : 0.f;
+    }
   }
   __syncthreads();
-  const float inv_pi2 = 1.f / (9.8696044f * du_iso * du_iso);
-  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-    float acc = row[i] * (0.25f / (du_iso * du_iso));
-    for (int j = (i & 1) ? 0 : 1; j < nu; j += 2) {  // only odd offsets i - j contribute
-      const float n = (float)(i - j);
-      acc -= row[j] * inv_pi2 / (n * n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = warp * 256; base < npad; base += span) {
+    const int i0 = base + lane * kFiltOut;
+    float w[kFiltOut], acc[kFiltRows][kFiltOut];
+#pragma unroll
+    for (int m = 0; m < kFiltOut; ++m) {
+      w[m] = hs[i0 + m + H0];
+#pragma unroll
+      for (int rr = 0; rr < kFiltRows; ++rr) acc[rr][m] = 0.f;
     }
-    q[(size_t)r * nu + i] = acc * du_iso;
+#pragma unroll 4
+    for (int j = 0; j < nu; ++j) {
+#pragma unroll
+      for (int rr = 0; rr < kFiltRows; ++rr) {
+        const float x = rows[rr * nu + j];
+#pragma unroll
+        for (int m = 0; m < kFiltOut; ++m) acc[rr][m] = fmaf(x, w[m], acc[rr][m]);
+      }
+      const float carry = __shfl_up_sync(0xffffffffu, w[kFiltOut - 1], 1);
+#pragma unroll
+      for (int m = kFiltOut - 1; m > 0; --m) w[m] = w[m - 1];
+      w[0] = lane == 0 ? hs[base - j - 1 + H0] : carry;
+    }
+#pragma unroll
+    for (int rr = 0; rr < kFiltRows; ++rr) {
+      const int r = r0 + rr;
+      if (r >= rows_total) continue;
+#pragma unroll
+      for (int m = 0; m < kFiltOut; ++m)
+        if (i0 + m < nu) q[(size_t)r * nu + i0 + m] = acc[rr][m] * du_iso;
+    }
   }
 }
 
@@ -197,10 +242,15 @@ cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const floa
                       float pv, float sod, float sdd, int nx, int ny, int nz, float dx, float dy, float dz, float* q_tmp,
                       float* vol, cudaStream_t s) {
   const float du = pu * sod / sdd, dv = pv * sod / sdd;  // pixel pitch at the isocentre
-  if ((size_t)nu * 4 > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, nu * 4);
+  const int span = kFiltThreads * kFiltOut;
+  const size_t npad = ((size_t)nu + span - 1) / span * span;
+  const size_t smem = ((2 * (npad + kFiltOut) + 1) + (size_t)kFiltRows * nu) * 4;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_fdk_filter<<<n_proj * nv, 256, nu * 4, s>>>(p, nu, nv, du, dv, sod, q_tmp);
+  const int rows_total = n_proj * nv;
+  k_fdk_filter<<<(rows_total + kFiltRows - 1) / kFiltRows, kFiltThreads, smem, s>>>(p, nu, nv, rows_total, du, dv, sod,
+                                                                                    q_tmp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // full orbit: (dbeta / 2) with dbeta = 2 pi / n_proj

@@ -66,11 +66,14 @@ struct Counters {
 
 // Fill this thread's column of the per-material total attenuation (mm^-1 per
 // g/cm^3) at energy E.
+__device__ __forceinline__ void fill_mu(const SmemTables& T, int i, float f, float* smu, int stride) {
+  for (int m = 0; m < T.n_mat; ++m) smu[m * stride] = 0.1f * T.at(TAB_TOT, m, i, f);
+}
 __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu, int stride) {
   int i;
   float f;
   T.locate(E, i, f);
-  for (int m = 0; m < T.n_mat; ++m) smu[m * stride] = 0.1f * T.at(TAB_TOT, m, i, f);
+  fill_mu(T, i, f, smu, stride);
 }
 
 // Gathers of the next MC_LOOKAHEAD midpoints are issued before any of them is
@@ -311,13 +314,16 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
     }
     p = (1.f + lam * lam) * F2 * R.norm[r];
   }
-  float x0 = R.W[r] * Ep * p * cosg * nee_scale / dd2;
+  int ei;
+  float ef;
+  T.locate(Ep, ei, ef);
+  float x0 = R.W[r] * T.response(ei, ef, Ep) * p * cosg * nee_scale / dd2;
   ++C.nee_rays;
   if (P.rr_threshold > 0.f && x0 < P.rr_threshold) {
     if (vr >= x0 / P.rr_threshold) return;
     x0 = P.rr_threshold;
   }
-  fill_mu(T, Ep, my_mu, stride);
+  fill_mu(T, ei, ef, my_mu, stride);
   const float tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
   const unsigned long long h = ((unsigned long long)hhi << 32) | hlo;
   const int b = P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0;
@@ -382,6 +388,8 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   SmemTables T;
   T.tab = s_blob;
   T.jkn = reinterpret_cast<const float2*>(smem + tab_off_jkn(nm, ns));
+  T.eta = reinterpret_cast<const float2*>(smem + tab_off_eta(nm, ns));
+  T.use_eta = P.tab.use_eta;
   T.comp = reinterpret_cast<const float2*>(smem + tab_off_comp(nm, ns));
   T.ncomp = reinterpret_cast<const int*>(smem + tab_off_ncomp(nm, ns));
   T.n_mat = nm;

@@ -31,6 +31,8 @@ struct mc_ctx {
   std::vector<double> pe, in, co, icoh;  // [n_mat][n_E]
   int n_comp[kMaxMat] = {};
   double comp[kMaxMat][kMaxComp][3] = {};
+  // detector response eta(E) at the table nodes (empty: eta(E) = E)
+  std::vector<double> eta;
   // staged FP32 blob (device)
   float2* d_blob = nullptr;
   int blob_bytes = 0, blob_stage = 0;
@@ -46,7 +48,7 @@ struct mc_ctx {
   bool have_spectrum = false;
   std::vector<double> S;
   std::vector<float> Ebin;
-  void* d_spec = nullptr;  // prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n]
+  void* d_spec = nullptr;  // prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n] | eta f32[n]
   size_t d_spec_cap = 0;
   // geometry
   bool have_geometry = false;
@@ -130,40 +132,50 @@ double kn_norm(double E, double mec2) {
   return 2.0 * (a + l / (2.0 * k) - (1.0 + 3.0 * k) / ((1.0 + 2.0 * k) * (1.0 + 2.0 * k)));
 }
 
-// Build and upload the FP32 shared-memory blob for the nodes the spectrum can reach.
-int stage_tables(mc_ctx* ctx) {
-  if (!ctx->blob_dirty && ctx->d_blob) return MC_OK;
+// Number of table nodes the spectrum can reach (staged into shared memory).
+int stage_nodes(const mc_ctx* ctx) {
   double Emax = ctx->E0 + 1.0;
   for (size_t n = 0; n < ctx->S.size(); ++n) Emax = std::max(Emax, (double)ctx->Ebin[n]);
-  int ns = (int)std::floor((Emax - ctx->E0) / ctx->dE) + 2;
-  ns = std::max(2, std::min(ns, ctx->n_E));
+  const int ns = (int)std::floor((Emax - ctx->E0) / ctx->dE) + 2;
+  return std::max(2, std::min(ns, ctx->n_E));
+}
+
+// The FP32 shared-memory blob for the first ns nodes: per kind and material
+// (v_i, v_{i+1} - v_i), the Klein-Nishina normalisation, the detector response
+// (eta(E_i) = E_i when none is set), the form-factor components.
+void write_blob(const mc_ctx* ctx, int ns, unsigned char* dst) {
   const int nm = ctx->n_mat;
-  const int bytes = tab_blob_bytes(nm, ns);
-  std::vector<unsigned char> blob(bytes, 0);
-  float2* tab = reinterpret_cast<float2*>(blob.data());
-  const std::vector<double>* src[kTabKinds] = {nullptr, &ctx->pe, &ctx->in, &ctx->co, &ctx->icoh};
-  for (int kind = 0; kind < kTabKinds; ++kind) {
-    for (int m = 0; m < nm; ++m) {
+  std::memset(dst, 0, tab_blob_bytes(nm, ns));
+  float2* tab = reinterpret_cast<float2*>(dst);
+  for (int kind = 0; kind < kTabKinds; ++kind)
+    for (int m = 0; m < nm; ++m)
       for (int i = 0; i < ns; ++i) {
         auto val = [&](int j) {
           const size_t q = (size_t)m * ctx->n_E + j;
-          if (kind == TAB_TOT) return ctx->pe[q] + ctx->in[q] + ctx->co[q];
-          return (*src[kind])[q];
+          switch (kind) {
+            case TAB_TOT: return ctx->pe[q] + ctx->in[q] + ctx->co[q];
+            case TAB_PE: return ctx->pe[q];
+            case TAB_IN: return ctx->in[q];
+            case TAB_CO: return ctx->co[q];
+            default: return ctx->icoh[q];
+          }
         };
-        const double v0 = val(i);
-        const double v1 = val(std::min(i + 1, ctx->n_E - 1));
+        const double v0 = val(i), v1 = val(std::min(i + 1, ctx->n_E - 1));
         tab[(kind * nm + m) * ns + i] = make_float2((float)v0, (float)(v1 - v0));
       }
-    }
-  }
-  float2* jkn = reinterpret_cast<float2*>(blob.data() + tab_off_jkn(nm, ns));
+  float2* jkn = reinterpret_cast<float2*>(dst + tab_off_jkn(nm, ns));
+  float2* eta = reinterpret_cast<float2*>(dst + tab_off_eta(nm, ns));
   for (int i = 0; i < ns; ++i) {
     const double E = ctx->E0 + ctx->dE * i;
     const double j0 = kn_norm(E, ctx->mec2), j1 = kn_norm(E + ctx->dE, ctx->mec2);
     jkn[i] = make_float2((float)j0, (float)(j1 - j0));
+    const int i1 = std::min(i + 1, ctx->n_E - 1);
+    const double e0 = ctx->eta.empty() ? E : ctx->eta[i];
+    const double e1 = ctx->eta.empty() ? ctx->E0 + ctx->dE * i1 : ctx->eta[i1];
+    eta[i] = make_float2((float)e0, (float)(e1 - e0));
   }
-  float2* comp = reinterpret_cast<float2*>(blob.data() + tab_off_comp(nm, ns));
-  int* ncomp = reinterpret_cast<int*>(blob.data() + tab_off_ncomp(nm, ns));
+  float2* comp = reinterpret_cast<float2*>(dst + tab_off_comp(nm, ns));
+  int* ncomp = reinterpret_cast<int*>(dst + tab_off_ncomp(nm, ns));
   for (int m = 0; m < nm; ++m) {
     ncomp[m] = ctx->n_comp[m];
     for (int i = 0; i < kMaxComp; ++i) {
@@ -171,6 +183,24 @@ int stage_tables(mc_ctx* ctx) {
       comp[m * kMaxComp + i] = i < ctx->n_comp[m] ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
     }
   }
+}
+
+// Detector response at energy E (linear between the table nodes), or E.
+double response_at(const mc_ctx* ctx, double E) {
+  if (ctx->eta.empty()) return E;
+  const double x = (E - ctx->E0) / ctx->dE;
+  const int i = std::max(0, std::min((int)std::floor(x), ctx->n_E - 2));
+  const double f = x - i;
+  return ctx->eta[i] + f * (ctx->eta[i + 1] - ctx->eta[i]);
+}
+
+// Build and upload the FP32 shared-memory blob for the nodes the spectrum can reach.
+int stage_tables(mc_ctx* ctx) {
+  if (!ctx->blob_dirty && ctx->d_blob) return MC_OK;
+  const int ns = stage_nodes(ctx);
+  const int bytes = tab_blob_bytes(ctx->n_mat, ns);
+  std::vector<unsigned char> blob(bytes, 0);
+  write_blob(ctx, ns, blob.data());
   if (ctx->d_blob) cudaFree(ctx->d_blob);
   ctx->d_blob = nullptr;
   CK(cudaMalloc((void**)&ctx->d_blob, bytes), "table blob allocation");
@@ -192,6 +222,7 @@ TableView table_view(const mc_ctx* c) {
   t.inv_dE = (float)(1.0 / c->dE);
   t.mec2 = (float)c->mec2;
   t.inv_hc = (float)(1.0 / c->hc);
+  t.use_eta = c->eta.empty() ? 0 : 1;
   return t;
 }
 
@@ -214,7 +245,7 @@ GeomView geom_view(const mc_ctx* c) {
 // Stratified counts (largest remainder, at least one photon per non-empty bin)
 // written into the host block that mirrors the device spectrum block:
 //   seed u64 | prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n]
-size_t spectrum_block_bytes(int n) { return 8 + (size_t)(n + 1) * 8 + (size_t)n * 12; }
+size_t spectrum_block_bytes(int n) { return 8 + (size_t)(n + 1) * 8 + (size_t)n * 16; }
 
 int fill_spectrum(mc_ctx* ctx, uint64_t N, uint64_t seed, unsigned char* host) {
   const int n = (int)ctx->S.size();
@@ -251,12 +282,14 @@ int fill_spectrum(mc_ctx* ctx, uint64_t N, uint64_t seed, unsigned char* host) {
   float* en = reinterpret_cast<float*>(pre + n + 1);
   float* wb = en + n;
   float* sn = wb + n;
+  float* eb = sn + n;
   pre[0] = 0;
   for (int i = 0; i < n; ++i) {
     pre[i + 1] = pre[i] + M[i];
     en[i] = ctx->Ebin[i];
     wb[i] = M[i] ? (float)(ctx->S[i] / (double)M[i]) : 0.f;
     sn[i] = (float)ctx->S[i];
+    eb[i] = (float)response_at(ctx, (double)ctx->Ebin[i]);
   }
   return MC_OK;
 }
@@ -269,6 +302,7 @@ SpectrumView spectrum_view(const mc_ctx* ctx) {
   sv.energy = reinterpret_cast<const float*>(base + (size_t)(n + 1) * 8);
   sv.wbin = sv.energy + n;
   sv.sn = sv.wbin + n;
+  sv.eta = sv.sn + n;
   sv.n_bins = n;
   return sv;
 }
@@ -665,6 +699,7 @@ int mc_load_tables(mc_ctx* ctx, const char* path) {
     std::memcpy(ctx->comp[m], comp[m], sizeof(comp[m]));
   }
   ctx->have_tables = true;
+  ctx->eta.clear();  // a response belongs to the previous tables' nodes
   ctx->blob_dirty = true;
   return MC_OK;
 }
@@ -761,6 +796,21 @@ int mc_set_spectrum(mc_ctx* ctx, const double* weights, const float* energies, i
   ctx->Ebin.assign(energies, energies + n);
   for (int i = 0; i < n; ++i) ctx->S[i] = weights[i] / sum;
   ctx->have_spectrum = true;
+  ctx->blob_dirty = true;
+  return MC_OK;
+}
+
+int mc_set_detector_response(mc_ctx* ctx, const double* eta, int n) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "load tables before the detector response");
+  if (!eta) {
+    ctx->eta.clear();
+  } else {
+    if (n != ctx->n_E) return fail(ctx, MC_ERR_INVALID_ARG, "the response needs one value per table energy node");
+    for (int i = 0; i < n; ++i)
+      if (!(eta[i] >= 0.0) || !std::isfinite(eta[i])) return fail(ctx, MC_ERR_INVALID_ARG, "response values must be >= 0");
+    ctx->eta.assign(eta, eta + n);
+  }
   ctx->blob_dirty = true;
   return MC_OK;
 }
@@ -1325,46 +1375,10 @@ int static_cuda_fail(mc_ctx* ctx, cudaError_t e, const char* where) { return cud
 // FP32 shared-memory table blob for the nodes the spectrum reaches, written
 // into dst (capacity cap bytes); same layout as the context's own blob.
 int static_build_blob(mc_ctx* ctx, unsigned char* dst, int cap, int* bytes_out, int* n_stage_out) {
-  double Emax = ctx->E0 + 1.0;
-  for (size_t n = 0; n < ctx->S.size(); ++n) Emax = std::max(Emax, (double)ctx->Ebin[n]);
-  int ns = (int)std::floor((Emax - ctx->E0) / ctx->dE) + 2;
-  ns = std::max(2, std::min(ns, ctx->n_E));
-  const int nm = ctx->n_mat;
-  const int bytes = tab_blob_bytes(nm, ns);
+  const int ns = stage_nodes(ctx);
+  const int bytes = tab_blob_bytes(ctx->n_mat, ns);
   if (bytes > cap) return fail(ctx, MC_ERR_INVALID_ARG, "cross-section tables exceed the static table area");
-  std::memset(dst, 0, bytes);
-  float2* tab = reinterpret_cast<float2*>(dst);
-  for (int kind = 0; kind < kTabKinds; ++kind)
-    for (int m = 0; m < nm; ++m)
-      for (int i = 0; i < ns; ++i) {
-        auto val = [&](int j) {
-          const size_t q = (size_t)m * ctx->n_E + j;
-          switch (kind) {
-            case TAB_TOT: return ctx->pe[q] + ctx->in[q] + ctx->co[q];
-            case TAB_PE: return ctx->pe[q];
-            case TAB_IN: return ctx->in[q];
-            case TAB_CO: return ctx->co[q];
-            default: return ctx->icoh[q];
-          }
-        };
-        const double v0 = val(i), v1 = val(std::min(i + 1, ctx->n_E - 1));
-        tab[(kind * nm + m) * ns + i] = make_float2((float)v0, (float)(v1 - v0));
-      }
-  float2* jkn = reinterpret_cast<float2*>(dst + tab_off_jkn(nm, ns));
-  for (int i = 0; i < ns; ++i) {
-    const double E = ctx->E0 + ctx->dE * i;
-    const double j0 = kn_norm(E, ctx->mec2), j1 = kn_norm(E + ctx->dE, ctx->mec2);
-    jkn[i] = make_float2((float)j0, (float)(j1 - j0));
-  }
-  float2* comp = reinterpret_cast<float2*>(dst + tab_off_comp(nm, ns));
-  int* ncomp = reinterpret_cast<int*>(dst + tab_off_ncomp(nm, ns));
-  for (int m = 0; m < nm; ++m) {
-    ncomp[m] = ctx->n_comp[m];
-    for (int i = 0; i < kMaxComp; ++i) {
-      const double Z = ctx->comp[m][i][0], w = ctx->comp[m][i][1], b = ctx->comp[m][i][2];
-      comp[m * kMaxComp + i] = i < ctx->n_comp[m] ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
-    }
-  }
+  write_blob(ctx, ns, dst);
   *bytes_out = bytes;
   *n_stage_out = ns;
   return MC_OK;

@@ -65,9 +65,10 @@ struct Rng {
 struct SmemTables {
   const float2* tab;   // [kTabKinds][n_mat][n_stage]
   const float2* jkn;   // [n_stage]
+  const float2* eta;   // [n_stage] detector response (used when use_eta)
   const float2* comp;  // [n_mat][kMaxComp]
   const int* ncomp;    // [n_mat]
-  int n_mat, n_stage;
+  int n_mat, n_stage, use_eta;
   float E0, inv_dE, mec2, inv_hc;
 
   __device__ __forceinline__ void locate(float E, int& i, float& f) const {
@@ -85,12 +86,20 @@ struct SmemTables {
     const float2 v = jkn[i];
     return fmaf(f, v.y, v.x);
   }
+  // Detector response eta(E) at the located energy (Sec. II-D.2); E itself
+  // (energy integrating) unless a response table was set.
+  __device__ __forceinline__ float response(int i, float f, float E) const {
+    if (!use_eta) return E;
+    const float2 v = eta[i];
+    return fmaf(f, v.y, v.x);
+  }
 };
 
 // Byte offsets of the blob sections (all multiples of 8; total padded to 16).
 __host__ __device__ inline int tab_off_jkn(int n_mat, int n_stage) { return kTabKinds * n_mat * n_stage * 8; }
+__host__ __device__ inline int tab_off_eta(int n_mat, int n_stage) { return tab_off_jkn(n_mat, n_stage) + n_stage * 8; }
 __host__ __device__ inline int tab_off_comp(int n_mat, int n_stage) {
-  return tab_off_jkn(n_mat, n_stage) + n_stage * 8;
+  return tab_off_eta(n_mat, n_stage) + n_stage * 8;
 }
 __host__ __device__ inline int tab_off_ncomp(int n_mat, int n_stage) {
   return tab_off_comp(n_mat, n_stage) + n_mat * kMaxComp * 8;

@@ -32,6 +32,7 @@ struct TableView {
   int blob_bytes;      // multiple of 16
   float E0, inv_dE, dE;
   float mec2, inv_hc;
+  int use_eta;         // the blob's detector-response row replaces eta(E) = E
 };
 
 // Voxel word: bits 0-15 the FP16 density (g/cm^3), bits 16-23 the material id.
@@ -66,6 +67,7 @@ struct SpectrumView {
   const float* energy;               // [n_bins]
   const float* wbin;                 // [n_bins] S_n / M_n
   const float* sn;                   // [n_bins] S_n
+  const float* eta;                  // [n_bins] detector response at each bin energy (primary)
   int n_bins;
 };
 
