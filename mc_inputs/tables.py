@@ -15,17 +15,27 @@ module tabulates closed-form stand-ins, in FP64:
   normalisation of the Rayleigh scatter-toward-detector pdf, with w_i the
   moles of atoms of element i per gram.
 
+Variant "bound" replaces the free-electron incoherent model by one with an
+incoherent scattering function (the S(q,Z) of Sec. II-A, eq. pmueforIncoherent):
+d(sigma)/d(Omega) = KN x S_mol(x), S_mol = sum_i w_i S_i, and, consistent with
+the form factor above (Z_i electrons sharing one orbital factor
+f_i = (1 + b_i x^2)^-2), the Waller-Hartree form S_i(x) = Z_i (1 - f_i(x)^2)
+= Z_i (1 - (1 + b_i x^2)^-4).  Its normalisation
+I_incoh(E) = sum_i w_i int_{-1}^{1} KN_shape(mu) S_i(x(mu)) dmu, with
+KN_shape = r^2 (r + 1/r - 1 + mu^2), r = E'/E, gives mu_incoh = pi r0^2 N_A I_incoh.
+
 File layout (little endian), read independently by the oracle (C) and by the
 CUDA library (C++):
 
   char[8]  magic "MCXTAB01"
-  int32    version (1), n_mat, n_E, max_comp (8)
+  int32    version (1, or 2 for the bound incoherent model), n_mat, n_E, max_comp (8)
   float64  E0_keV, dE_keV
   float64  r0_cm, mec2_keV, hc_keVA, N_A, c_F (A^2), K_pe (barn keV^3)
   n_mat x { char[16] name; float64 density; int32 n_comp; int32 pad;
             max_comp x { float64 Z, w (mol/g), b (A^2) } }
   float64  mu_pe[n_mat][n_E], mu_incoh[n_mat][n_E], mu_coh[n_mat][n_E]  (cm^2/g)
   float64  I_coh[n_mat][n_E]
+  version 2 only: float64 I_incoh[n_mat][n_E]
 """
 
 from __future__ import annotations
@@ -87,6 +97,7 @@ class Tables:
     mu_coh: np.ndarray
     I_coh: np.ndarray
     consts: dict = field(default_factory=dict)
+    I_incoh: np.ndarray = None  # bound incoherent model only (version 2)
 
     @property
     def n_mat(self):
@@ -146,6 +157,35 @@ def coherent_integral(Z, b, E_keV):
     return 0.5 * smax * (f * w[None, :]).sum(axis=1)
 
 
+def kn_shape_integral(E_keV):
+    """int_{-1}^{1} r^2 (r + 1/r - 1 + mu^2) dmu (the free-electron KN total / (pi r0^2))."""
+    E = np.atleast_1d(np.asarray(E_keV, dtype=np.float64))
+    return kn_sigma_per_electron(E) / (np.pi * R0_CM**2)
+
+
+def incoherent_deficit(Z, b, E_keV):
+    """J = int_{-1}^{1} KN_shape(mu) (1 + b x^2)^(-4) dmu, x^2 = K (1-mu)/2: what the
+    bound-electron factor S_i/Z_i = 1 - (1 + b x^2)^-4 removes from the
+    free-electron integral.  Same substitution s = ln(1 + b u) as the coherent
+    integral, so the forward peak is resolved at every energy."""
+    E = np.atleast_1d(np.asarray(E_keV, dtype=np.float64))
+    K = (E / HC_KEVA) ** 2
+    x, w = _gl()
+    smax = np.log1p(b * K)
+    s = 0.5 * smax[:, None] * (x[None, :] + 1.0)
+    u = np.expm1(s) / b
+    mu = 1.0 - 2.0 * u / K[:, None]
+    r = 1.0 / (1.0 + (E[:, None] / MEC2_KEV) * (1.0 - mu))
+    shape = r * r * (r + 1.0 / r - 1.0 + mu * mu)
+    f = shape * np.exp(-3.0 * s) / b * (2.0 / K[:, None])
+    return 0.5 * smax * (f * w[None, :]).sum(axis=1)
+
+
+def incoherent_integral(Z, b, E_keV):
+    """int_{-1}^{1} KN_shape(mu) S_i(x(mu)) dmu = Z (I_KN - J) for S_i = Z (1 - (1 + b x^2)^-4)."""
+    return Z * (kn_shape_integral(E_keV) - incoherent_deficit(Z, b, E_keV))
+
+
 def material_components(fracs):
     rows = []
     for el, frac in fracs.items():
@@ -185,8 +225,9 @@ def kn_energy_transfer_fraction(E_keV):
 def build_tables(n_E=150, E0=1.0, dE=1.0, materials=None, variant="full"):
     """Tabulate all materials at nodes E0 + k dE.
 
-    variant: "full", or one of "compton", "rayleigh", "photo" to keep only
-    that interaction (the others zeroed) -- used for single-process tests."""
+    variant: "full"; "bound" (all interactions, incoherent with the scattering
+    function S); or one of "compton", "rayleigh", "photo" to keep only that
+    interaction (the others zeroed) -- used for single-process tests."""
     materials = MATERIALS if materials is None else materials
     E = E0 + dE * np.arange(n_E)
     kn = kn_sigma_per_electron(E)
@@ -195,6 +236,7 @@ def build_tables(n_E=150, E0=1.0, dE=1.0, materials=None, variant="full"):
     mu_in = np.zeros_like(mu_pe)
     mu_co = np.zeros_like(mu_pe)
     icoh = np.zeros_like(mu_pe)
+    iinc = np.zeros_like(mu_pe) if variant == "bound" else None
     for m, (name, rho, fracs) in enumerate(materials):
         c = material_components(fracs)
         names.append(name)
@@ -203,10 +245,15 @@ def build_tables(n_E=150, E0=1.0, dE=1.0, materials=None, variant="full"):
         for Z, wmol, b in c:
             n_atoms = wmol * N_A  # atoms per gram
             mu_pe[m] += n_atoms * K_PE * 1e-24 * Z**4 / E**3
-            mu_in[m] += n_atoms * Z * kn
+            if iinc is None:
+                mu_in[m] += n_atoms * Z * kn
+            else:
+                iinc[m] += wmol * incoherent_integral(Z, b, E)
             ci = Z**2 * coherent_integral(Z, b, E)
             icoh[m] += wmol * ci
         mu_co[m] = np.pi * R0_CM**2 * N_A * icoh[m]
+        if iinc is not None:
+            mu_in[m] = np.pi * R0_CM**2 * N_A * iinc[m]
     if variant == "compton":
         mu_pe[:] = 0.0
         mu_co[:] = 0.0
@@ -216,16 +263,16 @@ def build_tables(n_E=150, E0=1.0, dE=1.0, materials=None, variant="full"):
     elif variant == "photo":
         mu_in[:] = 0.0
         mu_co[:] = 0.0
-    elif variant != "full":
+    elif variant not in ("full", "bound"):
         raise ValueError(variant)
     consts = dict(r0=R0_CM, mec2=MEC2_KEV, hc=HC_KEVA, N_A=N_A, c_F=C_F, K_pe=K_PE)
-    return Tables(E0, dE, names, np.array(dens), comps, mu_pe, mu_in, mu_co, icoh, consts)
+    return Tables(E0, dE, names, np.array(dens), comps, mu_pe, mu_in, mu_co, icoh, consts, I_incoh=iinc)
 
 
 def write_tables(t: Tables, path):
     with open(path, "wb") as f:
         f.write(MAGIC)
-        f.write(struct.pack("<4i", VERSION, t.n_mat, t.n_E, MAX_COMP))
+        f.write(struct.pack("<4i", VERSION if t.I_incoh is None else 2, t.n_mat, t.n_E, MAX_COMP))
         f.write(struct.pack("<2d", t.E0, t.dE))
         c = t.consts
         f.write(struct.pack("<6d", c["r0"], c["mec2"], c["hc"], c["N_A"], c["c_F"], c["K_pe"]))
@@ -240,6 +287,8 @@ def write_tables(t: Tables, path):
             f.write(buf.astype("<f8").tobytes())
         for arr in (t.mu_pe, t.mu_incoh, t.mu_coh, t.I_coh):
             f.write(np.ascontiguousarray(arr, dtype="<f8").tobytes())
+        if t.I_incoh is not None:
+            f.write(np.ascontiguousarray(t.I_incoh, dtype="<f8").tobytes())
 
 
 def read_tables(path) -> Tables:
@@ -261,11 +310,12 @@ def read_tables(path) -> Tables:
         dens.append(rho)
         off += 32 + max_comp * 24
     arrs = []
-    for _ in range(4):
+    for _ in range(5 if ver == 2 else 4):
         arrs.append(np.frombuffer(data, "<f8", n_mat * n_E, off).reshape(n_mat, n_E).copy())
         off += n_mat * n_E * 8
     consts = dict(r0=r0, mec2=mec2, hc=hc, N_A=na, c_F=cf, K_pe=kpe)
-    return Tables(E0, dE, names, np.array(dens), comps, *arrs, consts=consts)
+    iinc = arrs.pop() if ver == 2 else None
+    return Tables(E0, dE, names, np.array(dens), comps, *arrs, consts=consts, I_incoh=iinc)
 
 
 def default_table_path(variant="full", directory=None):

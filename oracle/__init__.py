@@ -65,6 +65,7 @@ def lib():
         L.orc_kn_norm.restype = d
         L.orc_sample_compton.argtypes = [d, d, u64, u64, P, P]
         L.orc_sample_rayleigh.argtypes = [P, i, d, u64, u64, P]
+        L.orc_sample_incoherent.argtypes = [P, i, d, u64, u64, P]
         L.orc_philox.argtypes = [P, P, P]
         L.orc_philox.restype = None
         L.orc_stream.argtypes = [u64, u32, u64, i, P]
@@ -191,6 +192,12 @@ class Oracle:
     def sample_rayleigh(self, mat, E, n, seed):
         out = np.zeros(n)
         _chk(self.L.orc_sample_rayleigh(self.h, mat, E, n, seed, _ptr(out)), "sample_rayleigh")
+        return out
+
+    def sample_incoherent(self, mat, E, n, seed):
+        """cos(theta) of n incoherent scatters (with the scattering function when the tables have it)."""
+        out = np.zeros(n)
+        _chk(self.L.orc_sample_incoherent(self.h, mat, E, n, seed, _ptr(out)), "sample_incoherent")
         return out
 
     def table(self, which, mat, E):

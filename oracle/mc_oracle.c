@@ -56,6 +56,8 @@ typedef struct {
   int n_comp[ORC_MAXMAT];
   double comp[ORC_MAXMAT][ORC_MAXCOMP][3]; /* Z, w (mol/g), b (A^2) */
   double *mu_pe, *mu_in, *mu_co, *icoh;    /* [n_mat][n_E] */
+  int bound;                               /* incoherent scattering function S(x,Z) in use (table version 2) */
+  double *iincoh;                          /* [n_mat][n_E] its normalisation (version 2) */
   /* volume */
   int have_volume, nx, ny, nz;
   double dx, dy, dz;
@@ -147,7 +149,7 @@ int orc_create(orc_ctx **out) {
 }
 void orc_destroy(orc_ctx *c) {
   if (!c) return;
-  free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh);
+  free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh); free(c->iincoh);
   free(c->mat); free(c->rho); free(c->S); free(c->Ebin); free(c->eta);
   free(c);
 }
@@ -166,7 +168,7 @@ int orc_load_tables(orc_ctx *c, const char *path) {
     return ORC_EIO;
   }
   int n_mat = hdr[1], n_E = hdr[2], maxc = hdr[3];
-  if (hdr[0] != 1 || n_mat < 1 || n_mat > ORC_MAXMAT || n_E < 2 || maxc != ORC_MAXCOMP) {
+  if ((hdr[0] != 1 && hdr[0] != 2) || n_mat < 1 || n_mat > ORC_MAXMAT || n_E < 2 || maxc != ORC_MAXCOMP) {
     fclose(f);
     return ORC_EIO;
   }
@@ -194,6 +196,17 @@ int orc_load_tables(orc_ctx *c, const char *path) {
       fread(c->icoh, 8, n, f) != n) {
     fclose(f);
     return ORC_EIO;
+  }
+  free(c->iincoh);
+  c->iincoh = NULL;
+  c->bound = hdr[0] == 2;
+  if (c->bound) {
+    c->iincoh = malloc(n * 8);
+    if (fread(c->iincoh, 8, n, f) != n) {
+      fclose(f);
+      c->bound = 0;
+      return ORC_EIO;
+    }
   }
   fclose(f);
   c->have_tables = 1;
@@ -365,6 +378,26 @@ static double ff2(const orc_ctx *c, int m, double u) {
   return s;
 }
 
+/* Molecular incoherent scattering function at x^2 = u (A^-2), per gram in
+ * moles of electrons: sum_i w_i Z_i (1 - (1 + b_i u)^-4) -- the Waller-Hartree
+ * form for Z_i electrons sharing the orbital factor of the form factor above.
+ * Its large-u limit is sum_i w_i Z_i. */
+static double smol(const orc_ctx *c, int m, double u) {
+  double s = 0;
+  for (int i = 0; i < c->n_comp[m]; ++i) {
+    double Z = c->comp[m][i][0], w = c->comp[m][i][1], b = c->comp[m][i][2];
+    double q = 1.0 + b * u;
+    double q2 = q * q;
+    s += w * Z * (1.0 - 1.0 / (q2 * q2));
+  }
+  return s;
+}
+static double smol_max(const orc_ctx *c, int m) {
+  double s = 0;
+  for (int i = 0; i < c->n_comp[m]; ++i) s += c->comp[m][i][1] * c->comp[m][i][0];
+  return s;
+}
+
 /* Scatter-toward-detector pdf over lambda in [-1, 1] (integrates to one):
  * type 1 Compton, eq. (pmueforIncoherent) with S = 1, normalised by the KN total;
  * type 2 Rayleigh, eq. (pmueforcoherent), normalised by the tabulated I_coh(E).
@@ -374,7 +407,12 @@ double orc_nee_pdf(const orc_ctx *c, int type, int m, double E, double lam, doub
     double a = E / c->mec2;
     double ratio = 1.0 / (1.0 + a * (1.0 - lam));
     if (Eout) *Eout = E * ratio;
-    return ratio * ratio * (ratio + 1.0 / ratio - 1.0 + lam * lam) / orc_kn_norm(E, c->mec2);
+    double shape = ratio * ratio * (ratio + 1.0 / ratio - 1.0 + lam * lam);
+    if (c->bound) { /* KN x S_mol, normalised by I_incoh(E) */
+      double K = (E / c->hc) * (E / c->hc);
+      return shape * smol(c, m, 0.5 * K * (1.0 - lam)) / tab(c, c->iincoh, m, E);
+    }
+    return shape / orc_kn_norm(E, c->mec2);
   }
   if (Eout) *Eout = E;
   double K = (E / c->hc) * (E / c->hc);
@@ -402,6 +440,23 @@ static double sample_compton(rng_t *g, double E, double mec2, double *ratio, int
       *ratio = r;
       return 1.0 - (r - 1.0) / a;
     }
+  }
+  *fail = 1;
+  *ratio = 1.0;
+  return 1.0;
+}
+
+/* Incoherent scattering with the scattering function: Kahn's method for the
+ * Klein-Nishina factor, then acceptance with probability S_mol(x)/S_mol(inf)
+ * (one more draw per try); a rejected angle restarts Kahn's method. */
+static double sample_incoherent(const orc_ctx *c, rng_t *g, int m, double E, double *ratio, int *fail) {
+  if (!c->bound) return sample_compton(g, E, c->mec2, ratio, fail);
+  const double K = (E / c->hc) * (E / c->hc);
+  const double smax = smol_max(c, m);
+  for (int it = 0; it < 100000; ++it) {
+    double mu = sample_compton(g, E, c->mec2, ratio, fail);
+    if (*fail) return mu;
+    if (rng_u(g) * smax <= smol(c, m, 0.5 * K * (1.0 - mu))) return mu;
   }
   *fail = 1;
   *ratio = 1.0;
@@ -897,7 +952,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       double ct, Enew = E;
       if (type == 1) {
         double rr;
-        ct = sample_compton(&g, E, c->mec2, &rr, &fail);
+        ct = sample_incoherent(c, &g, mint, E, &rr, &fail);
         Enew = E / rr;
       } else {
         ct = sample_rayleigh(c, &g, mint, E, &fail);
@@ -941,6 +996,19 @@ int orc_sample_compton(double E, double mec2, uint64_t n, uint64_t seed, double 
     double r;
     cos_out[i] = sample_compton(&g, E, mec2, &r, &fail);
     if (ratio_out) ratio_out[i] = r;
+    if (fail) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+int orc_sample_incoherent(const orc_ctx *c, int m, double E, uint64_t n, uint64_t seed, double *cos_out) {
+  if (!c->have_tables || m < 0 || m >= c->n_mat) return ORC_ESTATE;
+  for (uint64_t i = 0; i < n; ++i) {
+    rng_t g;
+    rng_init(&g, i, 0, seed);
+    int fail = 0;
+    double r;
+    cos_out[i] = sample_incoherent(c, &g, m, E, &r, &fail);
     if (fail) return ORC_EINVAL;
   }
   return ORC_OK;

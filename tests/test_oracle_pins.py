@@ -387,7 +387,13 @@ def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=N
                 alpha = E0 / MEC2_KEV
                 r = 1.0 / (1.0 + alpha * (1.0 - lam))
                 Ep = E0 * r
-                p_c = r * r * (r + 1.0 / r - 1.0 + lam * lam) / oracle_lib.kn_norm(E0)
+                if T.I_incoh is None:
+                    p_c = r * r * (r + 1.0 / r - 1.0 + lam * lam) / oracle_lib.kn_norm(E0)
+                else:  # bound electrons: KN x S_mol / I_incoh(E)
+                    Ku = 0.5 * (E0 / HC_KEVA) ** 2 * (1.0 - lam)
+                    smol = sum(w * Z * (1.0 - (1.0 + b * Ku) ** -4) for Z, w, b in T.comps[MAT_WATER])
+                    p_c = r * r * (r + 1.0 / r - 1.0 + lam * lam) * smol / np.interp(
+                        E0, T.energies, T.I_incoh[MAT_WATER])
                 contrib = mu_in * e_of(Ep) * p_c * np.exp(-mu_of(Ep) * ex) * geo_f
                 # Rayleigh
                 K = (E0 / HC_KEVA) ** 2
