@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--conv-bench", action="store_true",
                    help="tensor-core throughput of the denoiser's convolutions and its inference latency")
     p.add_argument("--correct-eval", action="store_true", help="iterative scatter correction on a large flat panel")
+    p.add_argument("--vr-eval", action="store_true", help="expected-value vs sampled-type point-detector scoring")
+    p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
     p.add_argument("--cor-detector", type=int, default=2048)
     p.add_argument("--cor-pixel", type=float, default=0.1)
     p.add_argument("--cor-proj", type=int, default=1024)
@@ -336,7 +338,7 @@ def run_ours(args):
     n_ang = max(1, args.angles)
     angles = (2.0 * np.pi * np.arange(n_ang) / n_ang).astype(np.float32)
     seed = wl["seed"] + 1000 * rank
-    ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph))
+    ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph), nee_mode=args.nee_mode)
     ctx.load_tables(tp)
     ctx.setup(wl)
     if args.detector == "panel":
@@ -462,7 +464,8 @@ def run_ours(args):
                        "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
                        "step_mm": wl["step_mm"], "n_split": 10, "spectrum": f"{len(wl['weights'])} bins",
                        "l2_flush": True, "parallelism": "replicas" if world > 1 else "single",
-                       "autotune": tuned, "voxel_layout": args.voxel_layout, "detector": args.detector},
+                       "autotune": tuned, "voxel_layout": args.voxel_layout, "detector": args.detector,
+                       "nee_mode": args.nee_mode},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -758,7 +761,8 @@ def run_correct_eval(args):
     gen = torch.Generator(device=dev).manual_seed(5)
     for k in range(0, n_proj, chunk):
         sl = slice(k, k + chunk)
-        isk = ctx.smooth_upsample(is_meas, meas_angles, angles[sl], NU, NV)
+        # per-pixel values scale with the pixel area: (coarse pixel -> panel pixel)
+        isk = ctx.smooth_upsample(is_meas, meas_angles, angles[sl], NU, NV) * ((g / NU) * (g / NV))
         lam = N0 * (ip[sl] + isk) / I0
         raw[sl] = torch.poisson(lam, generator=gen).clamp_min_(0.5) / N0 * I0
         del isk, lam
@@ -838,6 +842,46 @@ def run_correct_eval(args):
     print(json.dumps(line), flush=True)
 
 
+def run_vr_eval(args):
+    """Variance reduction of the expected-value point-detector scoring against
+    the paper's sampled-type scoring on the bench workload: transport time,
+    relative L2 noise of the scatter image (batch estimate) and the figure of
+    merit 1 / (noise^2 x time) of each mode."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    tp, wl = make_inputs(tempfile.mkdtemp(prefix="mcvr"), args.photons or 1e7, args.workload)
+    N = wl["n_photons"]
+    res = {}
+    for mode in (0, 1):
+        ctx = mcx.Context(0, n_batches=20, nee_mode=mode)
+        ctx.load_tables(tp)
+        ctx.setup(wl)
+        ms, noise = [], []
+        for k in range(args.warmup + args.steps):
+            out = ctx.project([0.0], N, wl["step_mm"], 100 + k, primary=False, variance=True)
+            st = ctx.last_stats()
+            if k >= args.warmup:
+                img = out["scatter"][0].double()
+                var = out["variance"][0].double()
+                ms.append(st["transport_ms"])
+                noise.append(float(torch.sqrt(var.sum()) / torch.linalg.norm(img)))
+        t = float(np.mean(ms)) / 1e3
+        n2 = float(np.mean(np.square(noise)))
+        res[mode] = {"transport_s": t, "histories_per_s": N / t, "rel_l2_noise": float(np.sqrt(n2)),
+                     "figure_of_merit": 1.0 / (n2 * t)}
+    line = {
+        "metric": "figure of merit 1/(relative L2 noise^2 x transport time) of the scatter image",
+        "unit": "1/s", "higher_is_better": True,
+        "config": {"workload": args.workload, "photons": N, "batches": 20, "steps": args.steps},
+        "paper_scoring": res[0], "expected_value_scoring": res[1],
+        "fom_gain": res[1]["figure_of_merit"] / res[0]["figure_of_merit"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.denoise_eval:
@@ -846,6 +890,8 @@ def main():
         run_conv_bench(args)
     elif args.correct_eval:
         run_correct_eval(args)
+    elif args.vr_eval:
+        run_vr_eval(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -73,6 +73,11 @@ typedef struct mc_options {
   int voxel_layout;      /* device volume layout: 1 = x fastest, 2 = 4x4x4 Morton bricks, 0 = default:
                             x fastest while the packed volume fits in 3/4 of L2, bricks beyond */
   int use_graph;         /* 1: mc_project replays one captured CUDA graph while its launch shape is unchanged */
+  int nee_mode;          /* point-detector scoring (Sec. II-C.1): 0 = the sampled scatter type's pdf (the
+                            paper's, default); 1 = expected value over the interaction type: every
+                            interaction, absorptions included, scores (mu_incoh/mu) x Compton term at E'
+                            + (mu_coh/mu) x Rayleigh term at E, both attenuations from one shared march;
+                            same mean, less variance */
 } mc_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -184,7 +189,9 @@ int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_a
  *   4. smoothing (options.denoise_mode) of the scatter, linear interpolation
  *      to every angle and cubic up-sampling to NU x NV (of the primary too
  *      unless it was computed at full resolution);
- *   5. c = a - ln(Ip / (Ip + Is)).
+ *   5. c = a - ln(Ip / (Ip + Is)); images are per pixel, so with the primary
+ *      on the panel the up-sampled scatter is scaled by the pixel-area ratio
+ *      (panel pixel / simulation pixel) first.
  * corrected_a_out (device, like raw_I) receives the final c; volume_out
  * (device [nz][ny][nx] FP32, nullable) the last reconstruction (of the last
  * corrected projections when n_iter >= 1); iter_seconds (host [n_iter],

@@ -89,6 +89,7 @@ class Options(C.Structure):
         ("denoise_mode", C.c_int),
         ("voxel_layout", C.c_int),
         ("use_graph", C.c_int),
+        ("nee_mode", C.c_int),
     ]
 
 

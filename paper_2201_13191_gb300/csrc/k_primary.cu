@@ -148,6 +148,8 @@ void padded_dims(int nx, int ny, int nz, int layout, VolumeView* v) {
   const size_t words = layout == VOX_BRICK ? (size_t)v->nbx * v->nby * ((v->pz + 3) / 4) * 64
                                            : (size_t)v->px * v->py * v->pz;
   v->words = (int)words;
+  v->pxy = v->px * v->py;
+  v->lin_bias = (int)(0x4B000000u * (1u + (uint32_t)v->px + (uint32_t)v->pxy));
 }
 
 size_t packed_words(int nx, int ny, int nz, int layout) {

@@ -224,9 +224,9 @@ __global__ void k_segment(const float* __restrict__ vol, size_t n, float lo, flo
 
 // c = a - ln(Ip / (Ip + Is)) (eq. Correction).
 __global__ void k_correct(const float* __restrict__ a, const float* __restrict__ ip, const float* __restrict__ is,
-                          size_t n, float* __restrict__ c) {
+                          float is_scale, size_t n, float* __restrict__ c) {
   for (size_t i = gtid(); i < n; i += gstride()) {
-    const float p = fmaxf(ip[i], 1e-30f), sc = fmaxf(is[i], 0.f);
+    const float p = fmaxf(ip[i], 1e-30f), sc = fmaxf(is[i], 0.f) * is_scale;
     c[i] = a[i] - logf(p / (p + sc));
   }
 }
@@ -274,8 +274,9 @@ cudaError_t recon_otsu_segment(const float* vol, size_t n, float lo, float hi, i
   return cudaGetLastError();
 }
 
-cudaError_t recon_correct(const float* a, const float* ip, const float* is, size_t n, float* c, cudaStream_t s) {
-  k_correct<<<blocks_for(n), 256, 0, s>>>(a, ip, is, n, c);
+cudaError_t recon_correct(const float* a, const float* ip, const float* is, float is_scale, size_t n, float* c,
+                          cudaStream_t s) {
+  k_correct<<<blocks_for(n), 256, 0, s>>>(a, ip, is, is_scale, n, c);
   return cudaGetLastError();
 }
 

@@ -158,6 +158,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   tp.step = step_mm;
   tp.seed = seed;
   tp.n_split = opt.n_split;
+  tp.nee_mode = opt.nee_mode;
   tp.rr_threshold = opt.rr_threshold;
   tp.max_order = opt.max_scatter_order;
   tp.n_batches = 1;

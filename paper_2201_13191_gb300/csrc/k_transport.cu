@@ -139,6 +139,46 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   return acc * h;
 }
 
+// Optical depths at two energies along the same march (the expected-value
+// score's Compton term at E' and Rayleigh term at E share the midpoints, so
+// they share the gathers); material attenuation read from the tables at the
+// located energies (ia, fa) and (ib, fb) when the material changes.
+template <int LAYOUT>
+__device__ __forceinline__ float2 march_tau2(const VolumeView& V, float3 x, float3 w, float t1, float step,
+                                             const SmemTables& T, int ia, float fa, int ib, float fb,
+                                             unsigned long long& nsteps) {
+  float ta, tb;
+  if (!clip_box(V, x, w, 0.f, t1, ta, tb)) return make_float2(0.f, 0.f);
+  const float L = tb - ta;
+  const int n = step_count(L, step);
+  const float h = L / (float)n;
+  VoxRay r;
+  r.set(V, x, w);
+  float acc_a = 0.f, acc_b = 0.f, mu_a = 0.f, mu_b = 0.f;
+  int cur = -1, vprev = -1;
+  uint32_t wprev = 0;
+  for (int k0 = 0; k0 < n; k0 += kLook) {
+    uint32_t wd[kLook];
+    gather_ahead<LAYOUT>(V, r, k0, n, h, ta, vprev, wprev, wd);
+#pragma unroll
+    for (int u = 0; u < kLook; ++u) {
+      if (k0 + u < n) {
+        const int m = vox_mat(wd[u]);
+        if (m != cur) {
+          cur = m;
+          mu_a = 0.1f * T.at(TAB_TOT, m, ia, fa);
+          mu_b = 0.1f * T.at(TAB_TOT, m, ib, fb);
+        }
+        const float rho = vox_rho(wd[u]);
+        acc_a = fmaf(mu_a, rho, acc_a);
+        acc_b = fmaf(mu_b, rho, acc_b);
+      }
+    }
+  }
+  nsteps += (unsigned long long)n;
+  return make_float2(acc_a * h, acc_b * h);
+}
+
 // Kahn's rejection method for the Klein-Nishina distribution; returns
 // r = E/E' (cos theta = 1 - (r-1)/a).
 __device__ __forceinline__ float kahn(Rng& g, float a, bool& fail) {
@@ -265,7 +305,7 @@ __device__ __forceinline__ void tally_add<true>(const TransportParams& P, float*
   tally_combine(P, s_img, off, v);
 }
 
-template <int LAYOUT, bool COMBINE>
+template <int LAYOUT, bool COMBINE, bool EV>
 __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
                                                 int r, int s, float* my_mu, int stride, float nee_scale,
                                                 uint32_t npix, size_t img, Counters& C, float* s_img,
@@ -295,11 +335,54 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   const int tm = R.tm[r];
   const int type = tm >> 8, mint = tm & 255;
   const float E = R.E[r];
+  const unsigned long long hh = ((unsigned long long)hhi << 32) | hlo;
+  const int bt = P.n_batches > 1 ? (int)(hh % (unsigned long long)P.n_batches) : 0;
+  if (EV) {
+    // expected value over the interaction type: (mu_incoh/mu) Compton term at
+    // E' + (mu_coh/mu) Rayleigh term at E, attenuations from one shared march
+    int i0, i1;
+    float f0, f1;
+    T.locate(E, i0, f0);
+    const float pe = T.at(TAB_PE, mint, i0, f0), in = T.at(TAB_IN, mint, i0, f0), co = T.at(TAB_CO, mint, i0, f0);
+    const float imu = 1.f / (pe + in + co);
+    const float ratio = 1.f / fmaf(E / T.mec2, 1.f - lam, 1.f);
+    const float Ep = E * ratio;
+    const float K = (E * T.inv_hc) * (E * T.inv_hc);
+    const float u = 0.5f * K * (1.f - lam);
+    const float pc = ratio * ratio * (ratio + 1.f / ratio - 1.f + lam * lam) *
+                     (T.bound ? T.smol(mint, u) / T.at(TAB_IINC, mint, i0, f0) : 1.f / T.kn_norm(i0, f0));
+    float F2 = 0.f;
+    const int nc = T.ncomp[mint];
+    const float2* cp = T.comp + mint * kMaxComp;
+    for (int i = 0; i < nc; ++i) {
+      const float q = fmaf(cp[i].y, u, 1.f);
+      const float q2 = q * q;
+      F2 += cp[i].x / (q2 * q2);
+    }
+    const float pr = (1.f + lam * lam) * F2 * (1.f / T.at(TAB_ICOH, mint, i0, f0));
+    T.locate(Ep, i1, f1);
+    const float gw = R.W[r] * cosg * nee_scale / dd2;
+    float xc = gw * (in * imu) * T.response(i1, f1, Ep) * pc;
+    float xr = gw * (co * imu) * T.response(i0, f0, E) * pr;
+    ++C.nee_rays;
+    const float x0 = xc + xr;
+    if (P.rr_threshold > 0.f && x0 < P.rr_threshold) {
+      if (vr >= x0 / P.rr_threshold) return;
+      const float sc = P.rr_threshold / x0;
+      xc *= sc;
+      xr *= sc;
+    }
+    const float2 tp = march_tau2<LAYOUT>(V, x, dir, dd2 * idd, P.step, T, i1, f1, i0, f0, C.nee_steps);
+    tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix,
+                       xc * __expf(-tp.x) + xr * __expf(-tp.y));
+    return;
+  }
   float Ep, p;
   if (type == 1) {
     const float ratio = 1.f / fmaf(E / T.mec2, 1.f - lam, 1.f);
     Ep = E * ratio;
     p = ratio * ratio * (ratio + 1.f / ratio - 1.f + lam * lam) * R.norm[r];
+    if (T.bound) p *= T.smol(mint, 0.5f * (E * T.inv_hc) * (E * T.inv_hc) * (1.f - lam));
   } else {
     Ep = E;
     const float K = (E * T.inv_hc) * (E * T.inv_hc);
@@ -325,9 +408,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   }
   fill_mu(T, ei, ef, my_mu, stride);
   const float tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
-  const unsigned long long h = ((unsigned long long)hhi << 32) | hlo;
-  const int b = P.n_batches > 1 ? (int)(h % (unsigned long long)P.n_batches) : 0;
-  tally_add<COMBINE>(P, s_img, ((size_t)b * P.n_angles + a) * img + pix, x0 * __expf(-tp));
+  tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix, x0 * __expf(-tp));
 }
 
 #ifndef MC_MIN_BLOCKS
@@ -341,7 +422,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 #endif
 constexpr int kBuckets = 16;
 
-template <int LAYOUT, bool COMBINE>
+template <int LAYOUT, bool COMBINE, bool EV>
 __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -391,6 +472,8 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   T.eta = reinterpret_cast<const float2*>(smem + tab_off_eta(nm, ns));
   T.use_eta = P.tab.use_eta;
   T.comp = reinterpret_cast<const float2*>(smem + tab_off_comp(nm, ns));
+  T.compz = reinterpret_cast<const float*>(smem + tab_off_compz(nm, ns));
+  T.bound = P.tab.bound;
   T.ncomp = reinterpret_cast<const int*>(smem + tab_off_ncomp(nm, ns));
   T.n_mat = nm;
   T.n_stage = ns;
@@ -504,19 +587,21 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
                     co = T.at(TAB_CO, mint, ti, tf);
         const float ut = g.u() * (pe + in + co);
         const int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
-        if (type == 0) {
-          ++C.photo;
+        if (type == 0) ++C.photo;
+        else if (type == 1) ++C.compton;
+        else ++C.rayleigh;
+        // absorption sites score only in expected-value mode
+        if (type == 0 && !EV) {
           alive = false;
         } else {
-          if (type == 1) ++C.compton;
-          else ++C.rayleigh;
           // queue the interaction; its pseudo-particles use the next n_split counter blocks
           g.align();
           const int r = atomicAdd(&s_nrec, 1);
           R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
           R.wx[r] = w.x; R.wy[r] = w.y; R.wz[r] = w.z;
           R.E[r] = E; R.W[r] = W; R.cb[r] = cb; R.sb[r] = sb;
-          R.norm[r] = type == 1 ? 1.f / T.kn_norm(ti, tf) : 1.f / T.at(TAB_ICOH, mint, ti, tf);
+          R.norm[r] = type == 1 ? 1.f / (T.bound ? T.at(TAB_IINC, mint, ti, tf) : T.kn_norm(ti, tf))
+                                : 1.f / T.at(TAB_ICOH, mint, ti, tf);
           R.tm[r] = (type << 8) | mint;
           R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
           R.k0[r] = g.ctr.x;
@@ -530,13 +615,27 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
             R.len[r] = clip_box(V, x, make_float3(toc.x * il, toc.y * il, toc.z * il), 0.f,
                                 __int_as_float(0x7f800000), ca, cbb) ? cbb : 0.f;
           }
-          // new direction
+          // new direction (an absorption ends the photon)
+          if (type == 0) alive = false;
+        }
+        if (alive) {
           bool fail = false;
           float ct, Enew = E;
           if (type == 1) {
             const float alpha = E / T.mec2;
-            const float rk = kahn(g, alpha, fail);
+            float rk = kahn(g, alpha, fail);
             ct = 1.f - (rk - 1.f) / alpha;
+            if (T.bound) {
+              // scattering function: accept Kahn's angle with probability S_mol(x) / S_mol(inf)
+              const float K = (E * T.inv_hc) * (E * T.inv_hc);
+              const float smax = T.smol_max(mint);
+              for (int it = 0; it < 100000 && !fail; ++it) {
+                if (g.u() * smax <= T.smol(mint, 0.5f * K * (1.f - ct))) break;
+                rk = kahn(g, alpha, fail);
+                ct = 1.f - (rk - 1.f) / alpha;
+                if (it == 99999) fail = true;
+              }
+            }
             Enew = E / rk;
           } else {
             ct = rayleigh(g, T, mint, E, fail);
@@ -586,14 +685,14 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         const int j = base + lane;
         if (j < n_jobs) {
           const int q = j / n_split;
-          pseudo_particle<LAYOUT, COMBINE>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+          pseudo_particle<LAYOUT, COMBINE, EV>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
         }
       }
     }
 #else
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
-      pseudo_particle<LAYOUT, COMBINE>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+      pseudo_particle<LAYOUT, COMBINE, EV>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
     }
 #endif
     const bool more = alive || next < total;
@@ -650,28 +749,38 @@ int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_p
 }
 
 namespace {
-template <int LAYOUT, bool COMBINE>
+template <int LAYOUT, bool COMBINE, bool EV>
 cudaError_t launch_one(const TransportParams& p, int grid, int block, int smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<LAYOUT, COMBINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_transport<LAYOUT, COMBINE, EV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_transport<LAYOUT, COMBINE><<<grid, block, smem, s>>>(p);
+  k_transport<LAYOUT, COMBINE, EV><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false, false>, block, smem);
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
   const int simg = p.tally_mode == TALLY_SHARED ? (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv) : 0;
   const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, simg);
   const bool combine = p.tally_mode != TALLY_GLOBAL;
-  if (p.vol.layout == VOX_BRICK)
-    return combine ? launch_one<VOX_BRICK, true>(p, grid, block, smem, s) : launch_one<VOX_BRICK, false>(p, grid, block, smem, s);
-  return combine ? launch_one<VOX_LIN, true>(p, grid, block, smem, s) : launch_one<VOX_LIN, false>(p, grid, block, smem, s);
+  const bool ev = p.nee_mode == 1;
+  if (p.vol.layout == VOX_BRICK) {
+    if (ev)
+      return combine ? launch_one<VOX_BRICK, true, true>(p, grid, block, smem, s)
+                     : launch_one<VOX_BRICK, false, true>(p, grid, block, smem, s);
+    return combine ? launch_one<VOX_BRICK, true, false>(p, grid, block, smem, s)
+                   : launch_one<VOX_BRICK, false, false>(p, grid, block, smem, s);
+  }
+  if (ev)
+    return combine ? launch_one<VOX_LIN, true, true>(p, grid, block, smem, s)
+                   : launch_one<VOX_LIN, false, true>(p, grid, block, smem, s);
+  return combine ? launch_one<VOX_LIN, true, false>(p, grid, block, smem, s)
+                 : launch_one<VOX_LIN, false, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s) {

@@ -29,6 +29,8 @@ struct mc_ctx {
   int n_mat = 0, n_E = 0;
   double E0 = 0, dE = 1, r0 = 0, mec2 = 0, hc = 0;
   std::vector<double> pe, in, co, icoh;  // [n_mat][n_E]
+  bool bound = false;                    // incoherent scattering function in use (table version 2)
+  std::vector<double> iincoh;            // [n_mat][n_E] its normalisation
   int n_comp[kMaxMat] = {};
   double comp[kMaxMat][kMaxComp][3] = {};
   // detector response eta(E) at the table nodes (empty: eta(E) = E)
@@ -119,6 +121,7 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->denoise_mode < 0 || o->denoise_mode > 2) return why = "denoise_mode must be 0, 1 or 2", -1;
   if (o->voxel_layout < 0 || o->voxel_layout > 2) return why = "voxel_layout must be 0, 1 or 2", -1;
   if (o->use_graph < 0 || o->use_graph > 1) return why = "use_graph must be 0 or 1", -1;
+  if (o->nee_mode < 0 || o->nee_mode > 1) return why = "nee_mode must be 0 or 1", -1;
   return 0;
 }
 
@@ -157,7 +160,8 @@ void write_blob(const mc_ctx* ctx, int ns, unsigned char* dst) {
             case TAB_PE: return ctx->pe[q];
             case TAB_IN: return ctx->in[q];
             case TAB_CO: return ctx->co[q];
-            default: return ctx->icoh[q];
+            case TAB_ICOH: return ctx->icoh[q];
+            default: return ctx->bound ? ctx->iincoh[q] : 0.0;
           }
         };
         const double v0 = val(i), v1 = val(std::min(i + 1, ctx->n_E - 1));
@@ -175,12 +179,15 @@ void write_blob(const mc_ctx* ctx, int ns, unsigned char* dst) {
     eta[i] = make_float2((float)e0, (float)(e1 - e0));
   }
   float2* comp = reinterpret_cast<float2*>(dst + tab_off_comp(nm, ns));
+  float* compz = reinterpret_cast<float*>(dst + tab_off_compz(nm, ns));
   int* ncomp = reinterpret_cast<int*>(dst + tab_off_ncomp(nm, ns));
   for (int m = 0; m < nm; ++m) {
     ncomp[m] = ctx->n_comp[m];
     for (int i = 0; i < kMaxComp; ++i) {
       const double Z = ctx->comp[m][i][0], w = ctx->comp[m][i][1], b = ctx->comp[m][i][2];
-      comp[m * kMaxComp + i] = i < ctx->n_comp[m] ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
+      const bool on = i < ctx->n_comp[m];
+      comp[m * kMaxComp + i] = on ? make_float2((float)(w * Z * Z), (float)b) : make_float2(0.f, 1.f);
+      compz[m * kMaxComp + i] = on ? (float)(w * Z) : 0.f;
     }
   }
 }
@@ -223,6 +230,7 @@ TableView table_view(const mc_ctx* c) {
   t.mec2 = (float)c->mec2;
   t.inv_hc = (float)(1.0 / c->hc);
   t.use_eta = c->eta.empty() ? 0 : 1;
+  t.bound = c->bound ? 1 : 0;
   return t;
 }
 
@@ -414,6 +422,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     tp.seed = 0;
     tp.seed_dev = reinterpret_cast<const unsigned long long*>(ctx->d_spec);
     tp.n_split = ctx->opt.n_split;
+    tp.nee_mode = ctx->opt.nee_mode;
     tp.rr_threshold = ctx->opt.rr_threshold;
     tp.max_order = ctx->opt.max_scatter_order;
     tp.n_batches = nb_img;
@@ -579,6 +588,7 @@ void mc_default_options(mc_options* o) {
   o->denoise_mode = 0;
   o->voxel_layout = 0;
   o->use_graph = 0;
+  o->nee_mode = 0;
 }
 
 int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {
@@ -647,7 +657,7 @@ int mc_load_tables(mc_ctx* ctx, const char* path) {
   double e2[2], k6[6];
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MCXTAB01", 8) == 0 &&
             std::fread(hdr, 4, 4, f) == 4 && std::fread(e2, 8, 2, f) == 2 && std::fread(k6, 8, 6, f) == 6;
-  if (!ok || hdr[0] != 1 || hdr[3] != kMaxComp || hdr[2] < 2) {
+  if (!ok || (hdr[0] != 1 && hdr[0] != 2) || hdr[3] != kMaxComp || hdr[2] < 2) {
     std::fclose(f);
     return fail(ctx, MC_ERR_IO, "malformed table header");
   }
@@ -678,9 +688,9 @@ int mc_load_tables(mc_ctx* ctx, const char* path) {
       }
   }
   const size_t n = (size_t)nm * nE;
-  std::vector<double> a(n), b(n), c(n), d(n);
+  std::vector<double> a(n), b(n), c(n), d(n), e(hdr[0] == 2 ? n : 0);
   ok = std::fread(a.data(), 8, n, f) == n && std::fread(b.data(), 8, n, f) == n && std::fread(c.data(), 8, n, f) == n &&
-       std::fread(d.data(), 8, n, f) == n;
+       std::fread(d.data(), 8, n, f) == n && (hdr[0] != 2 || std::fread(e.data(), 8, n, f) == n);
   std::fclose(f);
   if (!ok) return fail(ctx, MC_ERR_IO, "truncated table arrays");
   ctx->n_mat = nm;
@@ -694,6 +704,8 @@ int mc_load_tables(mc_ctx* ctx, const char* path) {
   ctx->in.swap(b);
   ctx->co.swap(c);
   ctx->icoh.swap(d);
+  ctx->iincoh.swap(e);
+  ctx->bound = hdr[0] == 2;
   for (int m = 0; m < nm; ++m) {
     ctx->n_comp[m] = ncomp[m];
     std::memcpy(ctx->comp[m], comp[m], sizeof(comp[m]));
@@ -1098,7 +1110,11 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
       ctx->opt.denoise_mode = saved_mode;
     }
     if (rc) return release(rc);
-    e = recon_correct(a, ip, is, nall, c, s);
+    // per-pixel images scale with the pixel area: the scatter simulated on the
+    // coarse grid is converted to the panel's pixels when the primary was
+    // computed there (with the paper's up-sampled primary the factor cancels)
+    const float area = P.primary_full_res ? (PU * PV) / (spu * spv) : 1.f;
+    e = recon_correct(a, ip, is, area, nall, c, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return release(cuda_fail(ctx, e, "correction"));
     if (iter_seconds) iter_seconds[it] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

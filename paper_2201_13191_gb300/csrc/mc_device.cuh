@@ -66,9 +66,10 @@ struct SmemTables {
   const float2* tab;   // [kTabKinds][n_mat][n_stage]
   const float2* jkn;   // [n_stage]
   const float2* eta;   // [n_stage] detector response (used when use_eta)
-  const float2* comp;  // [n_mat][kMaxComp]
+  const float2* comp;  // [n_mat][kMaxComp] (w Z^2, b)
+  const float* compz;  // [n_mat][kMaxComp] w Z
   const int* ncomp;    // [n_mat]
-  int n_mat, n_stage, use_eta;
+  int n_mat, n_stage, use_eta, bound;
   float E0, inv_dE, mec2, inv_hc;
 
   __device__ __forceinline__ void locate(float E, int& i, float& f) const {
@@ -86,6 +87,26 @@ struct SmemTables {
     const float2 v = jkn[i];
     return fmaf(f, v.y, v.x);
   }
+  // Molecular incoherent scattering function at x^2 = u (moles of electrons
+  // per gram): sum_i w_i Z_i (1 - (1 + b_i u)^-4), written as
+  // b u (2 + b u) (q^2 + 1) / q^4 (q = 1 + b u) to avoid cancellation near u = 0.
+  __device__ __forceinline__ float smol(int m, float u) const {
+    float s = 0.f;
+    const int nc = ncomp[m];
+    for (int i = 0; i < nc; ++i) {
+      const float bu = comp[m * kMaxComp + i].y * u;
+      const float q = 1.f + bu;
+      const float q2 = q * q;
+      s += compz[m * kMaxComp + i] * (bu * (2.f + bu) * (q2 + 1.f)) / (q2 * q2);
+    }
+    return s;
+  }
+  __device__ __forceinline__ float smol_max(int m) const {
+    float s = 0.f;
+    const int nc = ncomp[m];
+    for (int i = 0; i < nc; ++i) s += compz[m * kMaxComp + i];
+    return s;
+  }
   // Detector response eta(E) at the located energy (Sec. II-D.2); E itself
   // (energy integrating) unless a response table was set.
   __device__ __forceinline__ float response(int i, float f, float E) const {
@@ -101,8 +122,11 @@ __host__ __device__ inline int tab_off_eta(int n_mat, int n_stage) { return tab_
 __host__ __device__ inline int tab_off_comp(int n_mat, int n_stage) {
   return tab_off_eta(n_mat, n_stage) + n_stage * 8;
 }
-__host__ __device__ inline int tab_off_ncomp(int n_mat, int n_stage) {
+__host__ __device__ inline int tab_off_compz(int n_mat, int n_stage) {
   return tab_off_comp(n_mat, n_stage) + n_mat * kMaxComp * 8;
+}
+__host__ __device__ inline int tab_off_ncomp(int n_mat, int n_stage) {
+  return tab_off_compz(n_mat, n_stage) + n_mat * kMaxComp * 4;
 }
 __host__ __device__ inline int tab_blob_bytes(int n_mat, int n_stage) {
   return (tab_off_ncomp(n_mat, n_stage) + n_mat * 4 + 15) & ~15;
@@ -190,6 +214,17 @@ struct VoxRay {
   // guards the array bounds).
   template <int LAYOUT>
   __device__ __forceinline__ int voxel(const VolumeView& vol, float t) const {
+    if (LAYOUT == VOX_LIN) {
+      // (bx - C) + px (by - C) + px py (bz - C) with b the bit patterns of the
+      // round-down adds (C = 0x4B000000, see floor_pos): the offsets fold into
+      // one precomputed bias (exact in 32-bit wraparound arithmetic); the
+      // unsigned min only guards the array bounds
+      const unsigned bx = __float_as_uint(__fadd_rd(fmaf(t, vw.x, v0.x), 8388608.0f));
+      const unsigned by = __float_as_uint(__fadd_rd(fmaf(t, vw.y, v0.y), 8388608.0f));
+      const unsigned bz = __float_as_uint(__fadd_rd(fmaf(t, vw.z, v0.z), 8388608.0f));
+      const unsigned idx = bx + (unsigned)vol.px * by + (unsigned)vol.pxy * bz - (unsigned)vol.lin_bias;
+      return (int)min(idx, (unsigned)(vol.words - 1));
+    }
     const int ix = floor_pos(fmaf(t, vw.x, v0.x));
     const int iy = floor_pos(fmaf(t, vw.y, v0.y));
     const int iz = floor_pos(fmaf(t, vw.z, v0.z));

@@ -11,8 +11,8 @@ namespace mcx {
 
 constexpr int kMaxMat = MC_MAX_MATERIALS;
 constexpr int kMaxComp = 8;
-constexpr int kTabKinds = 5;  // tot, pe, incoh, coh, I_coh
-enum TabKind { TAB_TOT = 0, TAB_PE = 1, TAB_IN = 2, TAB_CO = 3, TAB_ICOH = 4 };
+constexpr int kTabKinds = 6;  // tot, pe, incoh, coh, I_coh, I_incoh (bound model; zero otherwise)
+enum TabKind { TAB_TOT = 0, TAB_PE = 1, TAB_IN = 2, TAB_CO = 3, TAB_ICOH = 4, TAB_IINC = 5 };
 
 // Statistic slots (uint64 counters on the device, doubles at the ABI).
 enum Stat {
@@ -23,7 +23,9 @@ enum Stat {
 // Staged table blob (device global, copied per block into shared memory):
 //   float2 tab[kTabKinds][n_mat][n_stage]   (v_i, v_{i+1} - v_i)
 //   float2 jkn[n_stage]                      Klein-Nishina normalisation J(E)
+//   float2 eta[n_stage]                      detector response
 //   float2 comp[n_mat][kMaxComp]             (w Z^2, b) of the form factor
+//   float  compz[n_mat][kMaxComp]            w Z (electrons, for the scattering function)
 //   int    ncomp[n_mat] (padded to 16 bytes)
 struct TableView {
   const float2* blob;  // device
@@ -33,6 +35,7 @@ struct TableView {
   float E0, inv_dE, dE;
   float mec2, inv_hc;
   int use_eta;         // the blob's detector-response row replaces eta(E) = E
+  int bound;           // incoherent scattering with the scattering function S(x, Z)
 };
 
 // Voxel word: bits 0-15 the FP16 density (g/cm^3), bits 16-23 the material id.
@@ -51,6 +54,8 @@ struct VolumeView {
   int nbx, nby;    // bricks along x, y (BRICK layout, padded dims)
   int px, py, pz;  // padded dims
   int words;       // words in the packed array (last index + 1)
+  int pxy;         // px * py
+  int lin_bias;    // 0x4B000000 (1 + px + px py) mod 2^32: folds the round-down floors' offsets into the index
   int nx, ny, nz;
   float dx, dy, dz;
   float inv_dx, inv_dy, inv_dz;
@@ -82,6 +87,7 @@ struct TransportParams {
   float step;
   unsigned long long seed;
   int n_split;
+  int nee_mode;  // 0: sampled type's pdf; 1: expected value over the type (both terms, one march)
   float rr_threshold;
   int max_order;
   int n_batches;
@@ -168,7 +174,10 @@ cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const floa
 cudaError_t recon_otsu_segment(const float* vol, size_t n, float lo, float hi, int classes, const int* d_cls_mat,
                                const float* d_cls_murho, const float* d_cls_rho0, float rho_max, unsigned int* d_hist,
                                int* d_thr, uint8_t* mat, uint16_t* rho, cudaStream_t s);
-cudaError_t recon_correct(const float* a, const float* ip, const float* is, size_t n, float* c, cudaStream_t s);
+// c = a - ln(ip / (ip + is_scale * is)): is_scale converts the scatter image's
+// per-pixel values to the panel's pixel area when it was simulated on another grid.
+cudaError_t recon_correct(const float* a, const float* ip, const float* is, float is_scale, size_t n, float* c,
+                          cudaStream_t s);
 
 // Learned denoiser (denoiser.cu)
 struct Denoiser;

@@ -48,7 +48,7 @@ def test_scatter_correction_end_to_end(gpu, table_path, tables):
     c.set_geometry(SOD, SDD, 48, 48, 2.4, 2.4)
     is48 = c.project(angles, 2_000_000, 0.5, 3, primary=False)["scatter"]
     c.set_geometry(SOD, SDD, NU, NV, 1.2, 1.2)
-    is_true = c.smooth_upsample(is48, angles, angles, NU, NV)
+    is_true = c.smooth_upsample(is48, angles, angles, NU, NV) * (48.0 / NU) ** 2  # per-pixel values scale with area
     vac = dict(truth, rho=np.zeros_like(truth["rho"]))
     c.load_volume(vac["mat"], vac["rho"], vac["spacing"])
     I0 = c.project([0.0], 1, 0.5, 1, scatter=False)["primary"][0]
