@@ -337,6 +337,16 @@ int mc_set_detector_response(mc_ctx *ctx, const double *eta, int n);
  * on `stream`.  Errors: INVALID_ARG, CUDA. */
 int mc_probe_gather(const void *buf, uint64_t n_words, int rounds, int grid, int block, uint32_t *sink, void *stream);
 
+/* Tensor-core probe (measurement helper; no counterpart in the paper).  grid
+ * CTAs (one per SM) each issue 4 x rounds tcgen05.mma of shape M = 128,
+ * N = n (16, 32, 64, 128 or 256), K = 16 on BF16 operands resident in shared
+ * memory, then wait for them; *err (device int) is set to 1 if a bounded wait
+ * gave up.  Timing it gives the sustained rate of the instruction shape the
+ * convolution kernels issue, which falls with N (the denoiser's layers have
+ * N = C_out from 16 to 256).  FLOPs per launch: grid x rounds x 4 x 2 x 128 x
+ * n x 16.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int mc_probe_mma(int n, int grid, int rounds, int *err, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

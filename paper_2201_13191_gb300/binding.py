@@ -35,7 +35,7 @@ EXPORTED = [
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
     "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
-    "mc_probe_gather", "mc_set_detector_response",
+    "mc_probe_gather", "mc_set_detector_response", "mc_probe_mma",
 ]
 
 
@@ -141,6 +141,7 @@ def library():
         L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
         L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
         L.mc_set_detector_response.argtypes = [P, vp, i]
+        L.mc_probe_mma.argtypes = [i, i, i, vp, vp]
         _lib = L
     return _lib
 

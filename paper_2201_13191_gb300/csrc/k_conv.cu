@@ -46,12 +46,12 @@ struct ConvSmem {
 // channels in tensor memory); positions on the border are computed and
 // discarded.  For tap (dy, dx) the input of position q sits at q + dy*wp + dx,
 // so with the input tile ("halo": the rows of the padded strip that cover
-// [q0 - wp - 1, q0 + 128A + wp]) stored as [8-channel group][position][8] --
-// 16-byte rows, consecutive positions 16 bytes apart -- every tap's A operand
-// is the same tile seen from a start address shifted by (dy*wp + dx) * 16
-// bytes.  Each 16-byte chunk of input is fetched once per CTA instead of nine
-// times, and the tensor memory accelerator fetches it: one tiled 4-D copy per
-// 8-channel group, zero-filled outside the image.
+// [q0 - wp - 1, q0 + 128A + wp]) stored position-major -- one row of CC
+// channels (2 CC bytes, swizzled 32/64/128B) per position, the canonical
+// K-major swizzled layout -- every tap's A operand is the same tile seen from
+// a start address shifted by (dy*wp + dx) rows.  Each input chunk is fetched
+// once per CTA instead of nine times, by one tiled 4-D tensor copy per stage
+// (zero-filled outside the image).
 //
 // Pipeline.  The reduction runs over the input channels in chunks of CC; a
 // chunk's stage holds its halo and its weights for all nine taps (the packed
@@ -72,8 +72,8 @@ struct FwdArgs {
   int n, h, w, cin, cout, co_total, co0;
   int ws, strips, wp, tiles;  // strip width, strips per row, padded width, tiles per strip
   int A, CC, stages, rbox;    // accumulators, channels per stage, ring depth, halo rows per copy
-  uint32_t lbo_a;             // bytes of one 8-channel group of the halo (multiple of 128)
   uint32_t halo_bytes, stage_bytes;
+  int rb;                     // halo bytes per position row (2 CC), swizzled in 8-row groups
   int relu, out_f32;
   int* err;
 };
@@ -140,9 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
         unsigned char* wsm = hs + a.halo_bytes;
         tc::mbar_expect_tx(&full[slot], halo_tx + w_tx);
         const int g0 = st * (a.CC / 8);  // first 8-channel group of the chunk
-        for (int kc = 0; kc < a.CC / 8; ++kc)
-          tc::tma_load_4d(hs + (size_t)kc * a.lbo_a, &xmap, &full[slot], (g0 + kc) * 8, strip * a.ws - 1, vr_lo - 1,
-                          img);
+        tc::tma_load_4d(hs, &xmap, &full[slot], g0 * 8, strip * a.ws - 1, vr_lo - 1, img);
         if (one_block) {
           tc::bulk_load(wsm, a.wm + (size_t)g0 * 9 * a.co_total * 8, w_tx, &full[slot]);
         } else {
@@ -179,9 +177,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
           const int shift = (tap / 3 - 1) * a.wp + (tap % 3 - 1);
           for (int ks = 0; ks < a.CC / 16; ++ks) {
             const uint64_t db = tc::sdesc(wb + (uint32_t)((2 * ks * 9 + tap) * N) * 16u, lbo_b, 128);
-            const uint32_t abase = hb + (uint32_t)(2 * ks) * a.lbo_a;
             for (int acc = 0; acc < a.A; ++acc) {
-              const uint64_t da = tc::sdesc(abase + (uint32_t)(o0 + 128 * acc + shift) * 16u, a.lbo_a, 128);
+              // rows of 2 CC bytes, 8-row groups 8 rb apart; k-step = 32 bytes within the row.  The
+              // tensor core applies the swizzle on absolute shared-memory address bits, like the TMA
+              // that wrote the tile, so a start shifted by any number of rows needs no phase field.
+              const uint32_t sa = hb + (uint32_t)(o0 + 128 * acc + shift) * (uint32_t)a.rb + (uint32_t)ks * 32u;
+              const uint64_t da = tc::sdesc_swz(sa, 8u * (uint32_t)a.rb, a.rb);
               tc::mma_bf16(tmem + (uint32_t)(acc * N), da, db, idesc, (st | tap | ks) ? 1u : 0u);
             }
           }
@@ -359,6 +360,12 @@ EncodeTiledFn encode_tiled() {
 // (prefer >= 3 stages or every chunk resident, then larger chunks); then the A
 // with the smallest estimated time, waves x (positions per CTA + halo rows +
 // a fixed per-CTA cost), waves counted with the CTAs that fit on one SM.
+// Shared memory of one stage's halo: swizzled rows of 2 CC bytes per position,
+// one 1024-byte-aligned region.
+uint32_t halo_bytes_for(int CC, int rbox, int wp) {
+  return ((uint32_t)rbox * (uint32_t)wp * (uint32_t)(2 * CC) + 1023u) & ~1023u;
+}
+
 bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int& grid_y, int& smem) {
   a.ws = p.w < 128 ? p.w : 128;
   a.strips = (p.w + a.ws - 1) / a.ws;
@@ -373,12 +380,12 @@ bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int&
     const int tiles = ((p.h - 1) * a.wp + a.ws + Mt - 1) / Mt;
     const long long grid = (long long)p.n * a.strips * tiles * grid_y;
     if (grid / grid_y > 0x7FFFFFFF) continue;
-    const uint32_t lbo = ((uint32_t)rbox * a.wp * 16u + 127u) & ~127u;
     int bestCC = 0, bestStages = 0, bestScore = -1;
     uint32_t bestStage = 0;
     for (int CC = 64; CC >= 16; CC >>= 1) {
       if (p.cin % CC) continue;
-      const uint32_t stage = (((uint32_t)(CC / 8) * lbo + (uint32_t)CC * 9u * N * 2u) + 1023u) & ~1023u;
+      const uint32_t halo = halo_bytes_for(CC, rbox, a.wp);
+      const uint32_t stage = ((halo + (uint32_t)CC * 9u * N * 2u) + 1023u) & ~1023u;
       const int chunks = p.cin / CC;
       int stages = (int)((kSmemBudget - 1024) / stage);
       if (stages > kMaxStages) stages = kMaxStages;
@@ -408,8 +415,8 @@ bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int&
       a.stages = bestStages;
       a.rbox = rbox;
       a.tiles = tiles;
-      a.lbo_a = lbo;
-      a.halo_bytes = (uint32_t)(bestCC / 8) * lbo;
+      a.halo_bytes = halo_bytes_for(bestCC, rbox, a.wp);
+      a.rb = 2 * bestCC;
       a.stage_bytes = bestStage;
       grid_x = (int)(grid / grid_y);
       smem = bytes;
@@ -445,10 +452,13 @@ cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
   CUtensorMap map;
   const cuuint64_t dims[4] = {(cuuint64_t)p.cin, (cuuint64_t)p.w, (cuuint64_t)p.h, (cuuint64_t)p.n};
   const cuuint64_t strides[3] = {(cuuint64_t)p.cin * 2, (cuuint64_t)p.cin * 2 * p.w, (cuuint64_t)p.cin * 2 * p.w * p.h};
-  const cuuint32_t box[4] = {8u, (cuuint32_t)a.wp, (cuuint32_t)a.rbox, 1u};
+  const cuuint32_t box[4] = {(cuuint32_t)a.CC, (cuuint32_t)a.wp, (cuuint32_t)a.rbox, 1u};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUtensorMapSwizzle swz = a.rb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : a.rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                              : CU_TENSOR_MAP_SWIZZLE_32B;
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p.x, dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   static unsigned long long smem_set = 0;  // devices on which the attribute was raised

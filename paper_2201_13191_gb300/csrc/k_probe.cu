@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "mc_internal.h"
+#include "mc_tc.cuh"
 
 namespace {
 
@@ -45,7 +46,67 @@ __global__ void __launch_bounds__(256) k_probe_gather(const uint32_t* __restrict
   sink[gid] = acc;
 }
 
+// Tensor-core issue-rate probe: one CTA per SM issues `rounds` x 4 MMAs
+// (M = 128, N, K = 16 each; BF16 operands resident in shared memory, FP32
+// accumulator in tensor memory) and waits for them: the sustained rate of the
+// instruction shape the convolution kernels use, which depends on N.
+template <int N>
+__global__ void __launch_bounds__(128, 1) k_probe_mma(int rounds, int* err) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  __shared__ uint32_t holder;
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int kBytes = (128 * 64 + N * 64) * 2;  // A: 128 x 64, B: N x 64 (BF16, zeros)
+  for (int i = tid; i < kBytes / 16; i += 128) reinterpret_cast<uint4*>(dyn)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) mcx::tc::tmem_alloc(&holder, N < 32 ? 32u : (uint32_t)N);
+  if (tid == 0) mcx::tc::mbar_init(&bar, 1);
+  mcx::tc::fence_async_smem();
+  mcx::tc::fence_before();
+  __syncthreads();
+  mcx::tc::fence_after();
+  const uint32_t tmem = holder;
+  if (tid == 0) {
+    const uint32_t a0 = mcx::tc::saddr(dyn), b0 = a0 + 128 * 64 * 2;
+    const uint32_t idesc = mcx::tc::idesc_bf16(128, N);
+    for (int r = 0; r < rounds; ++r)
+      for (int ks = 0; ks < 4; ++ks)
+        mcx::tc::mma_bf16(tmem, mcx::tc::sdesc(a0 + ks * 256, 128, 1024), mcx::tc::sdesc(b0 + ks * 256, 128, 1024),
+                          idesc, (r | ks) ? 1u : 0u);
+    mcx::tc::commit(&bar);
+  }
+  __syncwarp();
+  if (!mcx::tc::mbar_wait(&bar, 0) && tid == 0) atomicOr(err, 1);
+  mcx::tc::fence_before();
+  __syncthreads();
+  if (warp == 0) mcx::tc::tmem_free(tmem, N < 32 ? 32u : (uint32_t)N);
+}
+
+template <int N>
+cudaError_t launch_probe_mma(int grid, int rounds, int* err, cudaStream_t s) {
+  const int smem = (128 * 64 + N * 64) * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_probe_mma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_probe_mma<N><<<grid, 128, smem, s>>>(rounds, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+extern "C" int mc_probe_mma(int n, int grid, int rounds, int* err, void* stream) {
+  if (!err || grid < 1 || rounds < 1) return MC_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (n) {
+    case 16: e = launch_probe_mma<16>(grid, rounds, err, s); break;
+    case 32: e = launch_probe_mma<32>(grid, rounds, err, s); break;
+    case 64: e = launch_probe_mma<64>(grid, rounds, err, s); break;
+    case 128: e = launch_probe_mma<128>(grid, rounds, err, s); break;
+    case 256: e = launch_probe_mma<256>(grid, rounds, err, s); break;
+    default: return MC_ERR_INVALID_ARG;
+  }
+  return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
 
 extern "C" int mc_probe_gather(const void* buf, uint64_t n_words, int rounds, int grid, int block, uint32_t* sink,
                                void* stream) {

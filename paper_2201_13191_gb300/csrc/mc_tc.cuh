@@ -21,6 +21,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// Descriptor of a K-major operand in a swizzled canonical layout: rows of
+// `row_bytes` (32, 64 or 128: SWIZZLE_32B / 64B / 128B, the 16-byte chunks of
+// each row permuted by shared-memory address bits 7 and up), 8-row groups `sbo`
+// bytes apart.  The permutation follows the absolute address (measured: a view
+// starting at any row of a TMA-written tile reads correctly with the phase
+// field left at zero).
+__device__ __forceinline__ uint64_t sdesc_swz(uint32_t addr, uint32_t sbo, int row_bytes) {
+  const uint64_t layout = row_bytes == 128 ? 2ull : (row_bytes == 64 ? 4ull : 6ull);
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+         ((uint64_t)1 << 46) | (layout << 61);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
