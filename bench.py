@@ -399,9 +399,9 @@ def run_ours(args):
     el_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([el_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(t.item())
+        from paper_2201_13191_gb300.shard import max_time
+
+        el_ms = max_time(el_ms, device="cuda")
     value = world * N * n_ang * args.steps / (el_ms / 1e3)
 
     # end to end through the C ABI with host buffers: volume upload from pinned
@@ -426,9 +426,9 @@ def run_ours(args):
             torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            from paper_2201_13191_gb300.shard import max_time
+
+            e2e_s = max_time(e2e_s, device="cuda")
         e2e_value = world * N * n_ang * e2e_steps / e2e_s
 
     # roofline of the dominant kernel (transport): FP32 issue
@@ -719,8 +719,8 @@ def run_conv_bench(args):
                      "best_layer": {"layer": best["layer"], "tflops": best["fwd_tflops"],
                                     "frac": best["fwd_tflops"] / peak},
                      "mma_shape_peak_tflops": shape_peak,
-                     "shape_limited_peak": fl_f / shape_time,
-                     "frac_of_shape_limited_peak": (fl_f / ms_f / 1e9) / (fl_f / shape_time),
+                     "shape_limited_peak": fl_f / shape_time / 1e9,
+                     "frac_of_shape_limited_peak": (fl_f / ms_f) / (fl_f / shape_time),
                      "shape_note": "tcgen05.mma M=128 x N x K=16 issue rate measured live per N (mc_probe_mma); the "
                                    "layers' C_out tile sets N, so the FLOP-weighted attainable peak is lower than the "
                                    "dense GEMM figure"},

@@ -78,8 +78,9 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 
 // Gathers of the next MC_LOOKAHEAD midpoints are issued before any of them is
 // consumed: the step positions are fixed in advance, so the loads are
-// independent and several are in flight per warp.  A load is skipped when the
-// midpoint stays in the previous voxel.
+// independent and several are in flight per warp.  Every midpoint is loaded,
+// repeats included (they hit the line the previous load brought into L1), and
+// steps past the chord's end load a clamped, in-bounds word that is ignored.
 #ifndef MC_LOOKAHEAD
 #define MC_LOOKAHEAD 8
 #endif
@@ -92,17 +93,10 @@ __device__ __forceinline__ void gather_ahead(const VolumeView& V, const VoxRay& 
 #pragma unroll
   for (int u = 0; u < kLook; ++u) idx[u] = r.voxel<LAYOUT>(V, fmaf((float)(k0 + u) + 0.5f, h, ta));
 #pragma unroll
-  for (int u = 0; u < kLook; ++u) {
-    const int prev = u == 0 ? vprev : idx[u - 1];
-    if (k0 + u < n && idx[u] != prev) wd[u] = __ldg(V.vox + idx[u]);
-  }
-#pragma unroll
-  for (int u = 0; u < kLook; ++u) {
-    const int prev = u == 0 ? vprev : idx[u - 1];
-    if (idx[u] == prev) wd[u] = u == 0 ? wprev : wd[u - 1];
-  }
-  vprev = idx[kLook - 1];
-  wprev = wd[kLook - 1];
+  for (int u = 0; u < kLook; ++u) wd[u] = __ldg(V.vox + idx[u]);
+  (void)n;
+  (void)vprev;
+  (void)wprev;
 }
 
 // Optical depth of the fixed-step march x + t w, t in [0, t1] (Sec. II-C.2),
