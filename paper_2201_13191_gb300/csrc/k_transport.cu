@@ -117,15 +117,28 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   for (int k0 = 0; k0 < n; k0 += kLook) {
     uint32_t wd[kLook];
     gather_ahead<LAYOUT>(V, r, k0, n, h, ta, vprev, wprev, wd);
+    if (LAYOUT == VOX_LIN) {
+      // volume in L2 (the linear layout is chosen while it fits): branch-free,
+      // every step reads its material's attenuation from this thread's shared-
+      // memory column and steps past the end add nothing
 #pragma unroll
-    for (int u = 0; u < kLook; ++u) {
-      if (k0 + u < n) {
-        const int m = vox_mat(wd[u]);
-        if (m != cur) {
-          cur = m;
-          mu = smu[m * stride];
+      for (int u = 0; u < kLook; ++u) {
+        const float t = fmaf(smu[vox_mat(wd[u]) * stride], vox_rho(wd[u]), acc);
+        acc = k0 + u < n ? t : acc;
+      }
+    } else {
+      // volume in HBM (bricks): keep the shared-memory pipe free for the gathers,
+      // re-read the attenuation only when the material changes
+#pragma unroll
+      for (int u = 0; u < kLook; ++u) {
+        if (k0 + u < n) {
+          const int m = vox_mat(wd[u]);
+          if (m != cur) {
+            cur = m;
+            mu = smu[m * stride];
+          }
+          acc = fmaf(mu, vox_rho(wd[u]), acc);
         }
-        acc = fmaf(mu, vox_rho(wd[u]), acc);
       }
     }
   }
