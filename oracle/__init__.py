@@ -55,6 +55,8 @@ def lib():
         L.orc_set_geometry.argtypes = [P, d, d, i, i, d, d]
         L.orc_set_detector_response.argtypes = [P, P, i]
         L.orc_set_nee_mode.argtypes = [P, i]
+        L.orc_set_doppler.argtypes = [P, i]
+        L.orc_sample_doppler.argtypes = [P, i, d, d, u64, u64, P]
         L.orc_set_options.argtypes = [P, i, d, i, d]
         L.orc_primary.argtypes = [P, d, d, P, P]
         L.orc_scatter.argtypes = [P, d, u32, u64, u64, u64, d, u64, P, P, P, P, P]
@@ -117,6 +119,16 @@ class Oracle:
         E = np.ascontiguousarray(energies, dtype=np.float32)
         w = np.ascontiguousarray(weights, dtype=np.float64)
         _chk(self.L.orc_set_spectrum(self.h, _ptr(w), _ptr(E), len(E)), "set_spectrum")
+
+    def set_doppler(self, on):
+        """Doppler broadening of incoherent scatter (needs the bound tables)."""
+        _chk(self.L.orc_set_doppler(self.h, int(on)), "set_doppler")
+
+    def sample_doppler(self, mat, E, cos_t, n, seed):
+        """E'/E of n Doppler-broadened incoherent scatters through cos_t."""
+        out = np.zeros(n)
+        _chk(self.L.orc_sample_doppler(self.h, mat, E, cos_t, n, seed, _ptr(out)), "sample_doppler")
+        return out
 
     def set_nee_mode(self, mode):
         """0: score the sampled scatter type (the paper's); 1: expected value over both types."""

@@ -74,6 +74,7 @@ typedef struct {
   /* options */
   int n_split, max_order;
   int nee_mode; /* 0: score the sampled scatter type; 1: expected value over both types */
+  int doppler;  /* Doppler broadening of incoherent scatter (needs the bound tables) */
   double rr_threshold, eps_face;
 } orc_ctx;
 
@@ -302,6 +303,31 @@ int orc_set_geometry(orc_ctx *c, double sod, double sdd, int nu, int nv, double 
  * (mu_incoh/mu) x Compton term at E' + (mu_coh/mu) x Rayleigh term at E --
  * the expectation of mode 0's score over the type draw, so the same mean with
  * less variance. */
+/* Doppler broadening of incoherent scatter on (1) or off (0); it needs the
+ * bound-electron tables (their orbital model). */
+int orc_set_doppler(orc_ctx *c, int on) {
+  if (on != 0 && on != 1) return ORC_EINVAL;
+  if (on && (!c->have_tables || !c->bound)) return ORC_ESTATE;
+  c->doppler = on;
+  return ORC_OK;
+}
+
+static double sample_doppler(const orc_ctx *c, rng_t *g, int m, double E, double cos_t, int *fail);
+
+/* E'/E of one Doppler-broadened incoherent scatter of energy E through cos_t
+ * in material m (stream h = i, for the sampler tests). */
+int orc_sample_doppler(const orc_ctx *c, int m, double E, double cos_t, uint64_t n, uint64_t seed, double *out) {
+  if (!c->have_tables || !c->bound || m < 0 || m >= c->n_mat) return ORC_ESTATE;
+  for (uint64_t i = 0; i < n; ++i) {
+    rng_t g;
+    rng_init(&g, i, 0, seed);
+    int fail = 0;
+    out[i] = sample_doppler(c, &g, m, E, cos_t, &fail);
+    if (fail) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
 int orc_set_nee_mode(orc_ctx *c, int mode) {
   if (mode != 0 && mode != 1) return ORC_EINVAL;
   c->nee_mode = mode;
@@ -444,6 +470,72 @@ static double sample_compton(rng_t *g, double E, double mec2, double *ratio, int
   *fail = 1;
   *ratio = 1.0;
   return 1.0;
+}
+
+/* Doppler broadening of incoherent scattering (impulse approximation).  Each
+ * element's electrons share the hydrogen-like orbital behind the form factor
+ * F_i = Z_i (1 + b_i x^2)^-2, whose exponent is zeta_i = 2 pi a0 / sqrt(b_i)
+ * (atomic units) and whose Compton profile is
+ * J_i(p_z) = 8 / (3 pi zeta_i) (1 + (p_z / zeta_i)^2)^-3.  A scatter through
+ * cos(theta) = c picks element i with probability w_i S_i(x) / S_mol(x), draws
+ * p_z from J_i (Cauchy proposal t = tan(pi (u - 1/2)), accepted with
+ * probability (1 + t^2)^-2) and solves the impulse-approximation relation
+ * P sqrt(1 + tau^2 - 2 tau c) = tau (1 + kappa (1 - c)) - 1 for tau = E'/E
+ * (P = p_z / (m_e c), kappa = E / m_e c^2); a draw without a root in
+ * 0 < tau <= 1 is redrawn (the profile is truncated to physical energies). */
+static const double ALPHA_FS = 1.0 / 137.035999084; /* CODATA 2018 */
+static const double A0_ANGSTROM = 0.529177210903;   /* Bohr radius, CODATA 2018 */
+
+static double doppler_tau(double kappa, double c, double P) {
+  const double a = 1.0 + kappa * (1.0 - c);
+  const double P2 = P * P;
+  const double den = a * a - P2;
+  if (!(den > 0)) return 0;
+  const double B = a - P2 * c;
+  const double D = B * B - den * (1.0 - P2);
+  if (!(D >= 0)) return 0;
+  const double t = (B + (P >= 0 ? 1.0 : -1.0) * sqrt(D)) / den;
+  if (!(t > 0 && t <= 1.0)) return 0;
+  if (P != 0 && (a * t - 1.0) * P < 0) return 0; /* root of the squared equation only */
+  return t;
+}
+
+static double sample_doppler(const orc_ctx *c, rng_t *g, int m, double E, double cos_t, int *fail) {
+  const double K = (E / c->hc) * (E / c->hc);
+  const double u = 0.5 * K * (1.0 - cos_t);
+  const double kappa = E / c->mec2;
+  const double smax = smol(c, m, u);
+  for (int it = 0; it < 256; ++it) {
+    const double ue = rng_u(g) * smax, uc = rng_u(g), ua = rng_u(g);
+    int el = c->n_comp[m] - 1;
+    double cum = 0;
+    for (int i = 0; i < c->n_comp[m]; ++i) {
+      const double Z = c->comp[m][i][0], w = c->comp[m][i][1], b = c->comp[m][i][2];
+      const double q = 1.0 + b * u, q2 = q * q;
+      cum += w * Z * (1.0 - 1.0 / (q2 * q2));
+      if (ue < cum) {
+        el = i;
+        break;
+      }
+    }
+    const double t = tan(PI * (uc - 0.5));
+    const double w1 = 1.0 + t * t;
+    if (ua * w1 * w1 > 1.0) continue; /* Cauchy -> (1 + t^2)^-3 */
+    const double zeta = 2.0 * PI * A0_ANGSTROM / sqrt(c->comp[m][el][2]);
+    const double tau = doppler_tau(kappa, cos_t, t * zeta * ALPHA_FS);
+    if (tau > 0) return tau;
+  }
+  *fail = 1;
+  return 1.0 / (1.0 + kappa * (1.0 - cos_t));
+}
+
+/* Side stream of pseudo-particle s of an interaction whose pseudo-particle
+ * blocks start at k0: counter (2^31 | (k0 + s) << 6 | j, angle, h_lo, h_hi),
+ * j = 0, 1, ... (disjoint from every history's own blocks). */
+static void rng_side(rng_t *d, const rng_t *g, uint32_t k0s) {
+  *d = *g;
+  d->ctr[0] = 0x80000000u | (k0s << 6);
+  d->idx = 4;
 }
 
 /* Incoherent scattering with the scattering function: Kahn's method for the
@@ -886,6 +978,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       if (type != 0) st[type == 1 ? ST_COMPTON : ST_RAYLEIGH] += 1;
       /* point-detector scoring, split into n_split pseudo-particles, eq. (Th) */
       rng_align(&g);
+      const uint32_t k0 = g.ctr[0];
       for (int s = 0; s < c->n_split; ++s) {
         uint32_t r = rng_next(&g);
         double va = rng_u(&g), vb = rng_u(&g), vr = rng_u(&g);
@@ -901,9 +994,14 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         const double geo = A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
         double sc;
         st[ST_NEE_RAYS] += 1;
+        rng_t side;
+        rng_side(&side, &g, k0 + (uint32_t)s);
+        int dfail = 0;
         if (c->nee_mode == 0) {
           double Ep;
           double p = orc_nee_pdf(c, type, mint, E, lam, &Ep);
+          if (type == 1 && c->doppler) Ep = E * sample_doppler(c, &side, mint, E, lam, &dfail);
+          st[ST_SAMPLER_FAIL] += dfail;
           double x0 = W * det_eta(c, Ep) * p * geo;
           if (c->rr_threshold > 0 && x0 < c->rr_threshold) {
             if (vr >= x0 / c->rr_threshold) {
@@ -922,6 +1020,8 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
           const double mu = pe + in + co;
           double pc = orc_nee_pdf(c, 1, mint, E, lam, &Ep);
           double pr = orc_nee_pdf(c, 2, mint, E, lam, NULL);
+          if (c->doppler) Ep = E * sample_doppler(c, &side, mint, E, lam, &dfail);
+          st[ST_SAMPLER_FAIL] += dfail;
           double xc = W * (in / mu) * det_eta(c, Ep) * pc * geo;
           double xr = W * (co / mu) * det_eta(c, E) * pr * geo;
           const double x0 = xc + xr;
@@ -953,7 +1053,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       if (type == 1) {
         double rr;
         ct = sample_incoherent(c, &g, mint, E, &rr, &fail);
-        Enew = E / rr;
+        Enew = c->doppler ? E * sample_doppler(c, &g, mint, E, ct, &fail) : E / rr;
       } else {
         ct = sample_rayleigh(c, &g, mint, E, &fail);
       }
