@@ -78,6 +78,8 @@ typedef struct mc_options {
                             interaction, absorptions included, scores (mu_incoh/mu) x Compton term at E'
                             + (mu_coh/mu) x Rayleigh term at E, both attenuations from one shared march;
                             same mean, less variance */
+  int doppler;           /* 1: Doppler broadening of incoherent scatter (impulse approximation with the
+                            orbital model of the bound tables; needs tables of version 2), 0 = off (default) */
 } mc_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -90,6 +90,7 @@ class Options(C.Structure):
         ("voxel_layout", C.c_int),
         ("use_graph", C.c_int),
         ("nee_mode", C.c_int),
+        ("doppler", C.c_int),
     ]
 
 

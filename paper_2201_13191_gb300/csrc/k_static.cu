@@ -95,6 +95,8 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   mc_options opt;
   int sm_count = 0;
   static_views(ctx, &tv, &vv, &gv, &opt, &sm_count);
+  if (opt.doppler && !tv.bound)
+    return static_fail(ctx, MC_ERR_STATE, "Doppler broadening needs the bound-electron tables (version 2)");
   {
     const double diag = std::sqrt((double)vv.nx * vv.dx * vv.nx * vv.dx + (double)vv.ny * vv.dy * vv.ny * vv.dy +
                                   (double)vv.nz * vv.dz * vv.nz * vv.dz);
@@ -159,6 +161,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   tp.seed = seed;
   tp.n_split = opt.n_split;
   tp.nee_mode = opt.nee_mode;
+  tp.doppler = opt.doppler;
   tp.rr_threshold = opt.rr_threshold;
   tp.max_order = opt.max_scatter_order;
   tp.n_batches = 1;

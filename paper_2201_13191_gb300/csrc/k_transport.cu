@@ -248,6 +248,70 @@ __device__ __forceinline__ float rayleigh(Rng& g, const SmemTables& T, int m, fl
   return 1.f;
 }
 
+// Doppler broadening (impulse approximation).  Element i's electrons share the
+// hydrogen-like orbital behind the form factor (exponent zeta_i = 2 pi a0 /
+// sqrt(b_i), atomic units), Compton profile J_i ~ (1 + (p_z / zeta_i)^2)^-3.
+// A scatter through cos(theta) = c picks element i with probability
+// w_i S_i(x) / S_mol(x), draws p_z from J_i (Cauchy proposal, acceptance
+// (1 + t^2)^-2) and solves P sqrt(1 + tau^2 - 2 tau c) = tau (1 + kappa (1 - c)) - 1
+// for tau = E'/E (P = p_z / m_e c); a draw without a root in 0 < tau <= 1 is
+// redrawn.  Three draws per try, from the given stream.
+__device__ __forceinline__ float doppler_tau(float kappa, float c, float P) {
+  const float a = fmaf(kappa, 1.f - c, 1.f);
+  const float P2 = P * P;
+  const float den = a * a - P2;
+  if (!(den > 0.f)) return 0.f;
+  // (a - P^2 c)^2 - (a^2 - P^2)(1 - P^2), rearranged to avoid cancellation at small P
+  const float D = P2 * (a * a - 2.f * a * c + 1.f) + P2 * P2 * (c * c - 1.f);
+  if (!(D >= 0.f)) return 0.f;
+  const float t = (a - P2 * c + copysignf(sqrtf(D), P)) / den;
+  if (!(t > 0.f && t <= 1.f)) return 0.f;
+  if (P != 0.f && (a * t - 1.f) * P < 0.f) return 0.f;
+  return t;
+}
+
+__device__ __forceinline__ float sample_doppler(Rng& g, const SmemTables& T, int m, float E, float c, bool& fail) {
+  constexpr float kZetaC = 2.f * kPi * 0.529177210903f;  // 2 pi a0 (Angstrom)
+  constexpr float kAlpha = 1.f / 137.035999084f;
+  const float K = (E * T.inv_hc) * (E * T.inv_hc);
+  const float u = 0.5f * K * (1.f - c);
+  const float kappa = E / T.mec2;
+  const float smax = T.smol(m, u);
+  const int nc = T.ncomp[m];
+  for (int it = 0; it < 256; ++it) {
+    const float ue = g.u() * smax, uc = g.u(), ua = g.u();
+    int el = nc - 1;
+    float cum = 0.f;
+    for (int i = 0; i < nc; ++i) {
+      const float bu = T.comp[m * kMaxComp + i].y * u;
+      const float q = 1.f + bu, q2 = q * q;
+      cum += T.compz[m * kMaxComp + i] * (bu * (2.f + bu) * (q2 + 1.f)) / (q2 * q2);
+      if (ue < cum) {
+        el = i;
+        break;
+      }
+    }
+    const float t = tanf(kPi * (uc - 0.5f));
+    const float w1 = fmaf(t, t, 1.f);
+    if (ua * w1 * w1 > 1.f) continue;
+    const float zeta = kZetaC * rsqrtf(T.comp[m * kMaxComp + el].y);
+    const float tau = doppler_tau(kappa, c, t * zeta * kAlpha);
+    if (tau > 0.f) return tau;
+  }
+  fail = true;
+  return 1.f / fmaf(kappa, 1.f - c, 1.f);
+}
+
+// Side stream of pseudo-particle k (its counter block k = k0 + s): blocks
+// (2^31 | k << 6 | j, angle, h_lo, h_hi), disjoint from every history's own blocks.
+__device__ __forceinline__ Rng side_stream(uint2 key, uint32_t k, uint32_t a, uint32_t hlo, uint32_t hhi) {
+  Rng d;
+  d.key = key;
+  d.ctr = make_uint4(0x80000000u | (k << 6), a, hlo, hhi);
+  d.idx = 4;
+  return d;
+}
+
 __device__ __forceinline__ float3 rotate(float3 w, float ct, float phi) {
   const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
   float sp, cp;
@@ -312,7 +376,7 @@ __device__ __forceinline__ void tally_add<true>(const TransportParams& P, float*
   tally_combine(P, s_img, off, v);
 }
 
-template <int LAYOUT, bool COMBINE, bool EV>
+template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
 __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
                                                 int r, int s, float* my_mu, int stride, float nee_scale,
                                                 uint32_t npix, size_t img, Counters& C, float* s_img,
@@ -367,9 +431,16 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
       F2 += cp[i].x / (q2 * q2);
     }
     const float pr = (1.f + lam * lam) * F2 * (1.f / T.at(TAB_ICOH, mint, i0, f0));
-    T.locate(Ep, i1, f1);
+    float Ep_s = Ep;
+    if (DOP) {
+      bool df = false;
+      Rng d = side_stream(key, R.k0[r] + (uint32_t)s, a, hlo, hhi);
+      Ep_s = E * sample_doppler(d, T, mint, E, lam, df);
+      if (df) ++C.fail;
+    }
+    T.locate(Ep_s, i1, f1);
     const float gw = R.W[r] * cosg * nee_scale / dd2;
-    float xc = gw * (in * imu) * T.response(i1, f1, Ep) * pc;
+    float xc = gw * (in * imu) * T.response(i1, f1, Ep_s) * pc;
     float xr = gw * (co * imu) * T.response(i0, f0, E) * pr;
     ++C.nee_rays;
     const float x0 = xc + xr;
@@ -390,6 +461,12 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
     Ep = E * ratio;
     p = ratio * ratio * (ratio + 1.f / ratio - 1.f + lam * lam) * R.norm[r];
     if (T.bound) p *= T.smol(mint, 0.5f * (E * T.inv_hc) * (E * T.inv_hc) * (1.f - lam));
+    if (DOP) {
+      bool df = false;
+      Rng d = side_stream(key, R.k0[r] + (uint32_t)s, a, hlo, hhi);
+      Ep = E * sample_doppler(d, T, mint, E, lam, df);
+      if (df) ++C.fail;
+    }
   } else {
     Ep = E;
     const float K = (E * T.inv_hc) * (E * T.inv_hc);
@@ -429,7 +506,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 #endif
 constexpr int kBuckets = 16;
 
-template <int LAYOUT, bool COMBINE, bool EV>
+template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
 __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -643,7 +720,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
                 if (it == 99999) fail = true;
               }
             }
-            Enew = E / rk;
+            Enew = DOP ? E * sample_doppler(g, T, mint, E, ct, fail) : E / rk;
           } else {
             ct = rayleigh(g, T, mint, E, fail);
           }
@@ -692,14 +769,14 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         const int j = base + lane;
         if (j < n_jobs) {
           const int q = j / n_split;
-          pseudo_particle<LAYOUT, COMBINE, EV>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+          pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
         }
       }
     }
 #else
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
-      pseudo_particle<LAYOUT, COMBINE, EV>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+      pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
     }
 #endif
     const bool more = alive || next < total;
@@ -756,19 +833,19 @@ int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_p
 }
 
 namespace {
-template <int LAYOUT, bool COMBINE, bool EV>
+template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
 cudaError_t launch_one(const TransportParams& p, int grid, int block, int smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<LAYOUT, COMBINE, EV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_transport<LAYOUT, COMBINE, EV, DOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_transport<LAYOUT, COMBINE, EV><<<grid, block, smem, s>>>(p);
+  k_transport<LAYOUT, COMBINE, EV, DOP><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false, false>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false, false, false>, block, smem);
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
@@ -776,18 +853,30 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, cuda
   const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, simg);
   const bool combine = p.tally_mode != TALLY_GLOBAL;
   const bool ev = p.nee_mode == 1;
-  if (p.vol.layout == VOX_BRICK) {
-    if (ev)
-      return combine ? launch_one<VOX_BRICK, true, true>(p, grid, block, smem, s)
-                     : launch_one<VOX_BRICK, false, true>(p, grid, block, smem, s);
-    return combine ? launch_one<VOX_BRICK, true, false>(p, grid, block, smem, s)
-                   : launch_one<VOX_BRICK, false, false>(p, grid, block, smem, s);
+  const int variant = (p.vol.layout == VOX_BRICK ? 8 : 0) | (combine ? 4 : 0) | (ev ? 2 : 0) | (p.doppler ? 1 : 0);
+  switch (variant) {
+#define MC_LAUNCH(V, L, C, E, D) \
+  case V:                        \
+    return launch_one<L, C, E, D>(p, grid, block, smem, s);
+    MC_LAUNCH(0, VOX_LIN, false, false, false)
+    MC_LAUNCH(1, VOX_LIN, false, false, true)
+    MC_LAUNCH(2, VOX_LIN, false, true, false)
+    MC_LAUNCH(3, VOX_LIN, false, true, true)
+    MC_LAUNCH(4, VOX_LIN, true, false, false)
+    MC_LAUNCH(5, VOX_LIN, true, false, true)
+    MC_LAUNCH(6, VOX_LIN, true, true, false)
+    MC_LAUNCH(7, VOX_LIN, true, true, true)
+    MC_LAUNCH(8, VOX_BRICK, false, false, false)
+    MC_LAUNCH(9, VOX_BRICK, false, false, true)
+    MC_LAUNCH(10, VOX_BRICK, false, true, false)
+    MC_LAUNCH(11, VOX_BRICK, false, true, true)
+    MC_LAUNCH(12, VOX_BRICK, true, false, false)
+    MC_LAUNCH(13, VOX_BRICK, true, false, true)
+    MC_LAUNCH(14, VOX_BRICK, true, true, false)
+    MC_LAUNCH(15, VOX_BRICK, true, true, true)
+#undef MC_LAUNCH
   }
-  if (ev)
-    return combine ? launch_one<VOX_LIN, true, true>(p, grid, block, smem, s)
-                   : launch_one<VOX_LIN, false, true>(p, grid, block, smem, s);
-  return combine ? launch_one<VOX_LIN, true, false>(p, grid, block, smem, s)
-                 : launch_one<VOX_LIN, false, false>(p, grid, block, smem, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s) {

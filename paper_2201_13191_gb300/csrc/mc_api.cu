@@ -122,6 +122,7 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->voxel_layout < 0 || o->voxel_layout > 2) return why = "voxel_layout must be 0, 1 or 2", -1;
   if (o->use_graph < 0 || o->use_graph > 1) return why = "use_graph must be 0 or 1", -1;
   if (o->nee_mode < 0 || o->nee_mode > 1) return why = "nee_mode must be 0 or 1", -1;
+  if (o->doppler < 0 || o->doppler > 1) return why = "doppler must be 0 or 1", -1;
   return 0;
 }
 
@@ -321,6 +322,8 @@ int check_ready(mc_ctx* ctx) {
   if (!ctx->have_volume) return fail(ctx, MC_ERR_STATE, "volume not loaded");
   if (!ctx->have_spectrum) return fail(ctx, MC_ERR_STATE, "spectrum not set");
   if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
+  if (ctx->opt.doppler && !ctx->bound)
+    return fail(ctx, MC_ERR_STATE, "Doppler broadening needs the bound-electron tables (version 2)");
   const double rmax = 0.5 * std::sqrt((double)ctx->nx * ctx->dx * ctx->nx * ctx->dx +
                                       (double)ctx->ny * ctx->dy * ctx->ny * ctx->dy);
   if (!(rmax < ctx->sod) || !(rmax < (double)ctx->sdd - ctx->sod))
@@ -423,6 +426,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     tp.seed_dev = reinterpret_cast<const unsigned long long*>(ctx->d_spec);
     tp.n_split = ctx->opt.n_split;
     tp.nee_mode = ctx->opt.nee_mode;
+    tp.doppler = ctx->opt.doppler;
     tp.rr_threshold = ctx->opt.rr_threshold;
     tp.max_order = ctx->opt.max_scatter_order;
     tp.n_batches = nb_img;
@@ -589,6 +593,7 @@ void mc_default_options(mc_options* o) {
   o->voxel_layout = 0;
   o->use_graph = 0;
   o->nee_mode = 0;
+  o->doppler = 0;
 }
 
 int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {
@@ -966,6 +971,8 @@ int mc_fdk(mc_ctx* ctx, const float* p, int n_proj, const float* angles, int NU,
            float dx, float dy, float dz, float* vol, void* stream) {
   if (!ctx) return MC_ERR_INVALID_ARG;
   if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
+  if (ctx->opt.doppler && !ctx->bound)
+    return fail(ctx, MC_ERR_STATE, "Doppler broadening needs the bound-electron tables (version 2)");
   if (!p || !vol || !angles || n_proj < 1 || NU < 2 || NV < 2 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) ||
       !(dy > 0) || !(dz > 0) || NU > 50000)
     return fail(ctx, MC_ERR_INVALID_ARG, "bad reconstruction arguments");

@@ -88,6 +88,7 @@ struct TransportParams {
   unsigned long long seed;
   int n_split;
   int nee_mode;  // 0: sampled type's pdf; 1: expected value over the type (both terms, one march)
+  int doppler;   // Doppler broadening of incoherent scatter (bound tables)
   float rr_threshold;
   int max_order;
   int n_batches;
