@@ -56,6 +56,8 @@ def lib():
         L.orc_set_detector_response.argtypes = [P, P, i]
         L.orc_set_nee_mode.argtypes = [P, i]
         L.orc_set_doppler.argtypes = [P, i]
+        L.orc_load_mesh.argtypes = [P, P, i, P, P, i, P, P, P, i]
+        L.orc_mesh_primary.argtypes = [P, d, P]
         L.orc_sample_doppler.argtypes = [P, i, d, d, u64, u64, P]
         L.orc_set_options.argtypes = [P, i, d, i, d]
         L.orc_primary.argtypes = [P, d, d, P, P]
@@ -119,6 +121,22 @@ class Oracle:
         E = np.ascontiguousarray(energies, dtype=np.float32)
         w = np.ascontiguousarray(weights, dtype=np.float64)
         _chk(self.L.orc_set_spectrum(self.h, _ptr(w), _ptr(E), len(E)), "set_spectrum")
+
+    def load_mesh(self, mesh):
+        """Triangle-mesh geometry (mc_inputs.meshes dict); replaces the volume for mesh_primary."""
+        v = np.ascontiguousarray(mesh["vertices"], dtype=np.float32)
+        t = np.ascontiguousarray(mesh["triangles"], dtype=np.int32)
+        tb = np.ascontiguousarray(mesh["tri_body"], dtype=np.int32)
+        bm = np.ascontiguousarray(mesh["body_material"], dtype=np.int32)
+        br = np.ascontiguousarray(mesh["body_density"], dtype=np.float32)
+        bp = np.ascontiguousarray(mesh["body_parent"], dtype=np.int32)
+        _chk(self.L.orc_load_mesh(self.h, _ptr(v), len(v), _ptr(t), _ptr(tb), len(t), _ptr(bm), _ptr(br), _ptr(bp),
+                                  len(bm)), "load_mesh")
+
+    def mesh_primary(self, angle):
+        Ip = np.zeros((self.nv, self.nu))
+        _chk(self.L.orc_mesh_primary(self.h, float(np.float32(angle)), _ptr(Ip)), "mesh_primary")
+        return Ip
 
     def set_doppler(self, on):
         """Doppler broadening of incoherent scatter (needs the bound tables)."""

@@ -45,6 +45,7 @@
 #define ORC_EIO -8
 #define ORC_MAXMAT 16
 #define ORC_MAXCOMP 8
+#define ORC_MAXBODY 64
 
 static const double PI = 3.14159265358979323846;
 
@@ -68,6 +69,12 @@ typedef struct {
   double *S, *Ebin;
   /* detector response eta(E) at the table nodes (NULL: eta(E) = E) */
   double *eta;
+  /* triangle-mesh geometry (CAD bodies); replaces the volume while loaded */
+  int have_mesh, n_tri, n_body;
+  double *tri;   /* [n_tri][9] vertex coordinates */
+  int *tri_body; /* [n_tri] */
+  int body_mat[ORC_MAXBODY], body_parent[ORC_MAXBODY];
+  double body_rho[ORC_MAXBODY];
   /* geometry */
   int have_geometry, nu, nv;
   double sod, sdd, pu, pv;
@@ -152,6 +159,7 @@ void orc_destroy(orc_ctx *c) {
   if (!c) return;
   free(c->mu_pe); free(c->mu_in); free(c->mu_co); free(c->icoh); free(c->iincoh);
   free(c->mat); free(c->rho); free(c->S); free(c->Ebin); free(c->eta);
+  free(c->tri); free(c->tri_body);
   free(c);
 }
 
@@ -777,6 +785,151 @@ static double primary_sum(const orc_ctx *c, const double *rhoL, double *tau_mean
  * where ceil(L/step) itself is within rounding of an integer, either
  * neighbouring step count is a valid evaluation (largest |ln| ratio of the
  * images they give). */
+/* ------------------------------------------------------------------ */
+/* Triangle-mesh geometry (the paper's CAD model of closed triangulated
+ * surfaces).  Bodies are closed, outward-oriented surfaces with a material
+ * and density, optionally inside a parent body whose material they replace;
+ * outside every body is vacuum. */
+int orc_load_mesh(orc_ctx *c, const float *v, int nv, const int *tris, const int *tri_body, int nt,
+                  const int *body_mat, const float *body_rho, const int *body_parent, int nb) {
+  if (!c->have_tables) return ORC_ESTATE;
+  if (!v || !tris || !tri_body || nv < 3 || nt < 1 || nb < 1 || nb > ORC_MAXBODY) return ORC_EINVAL;
+  for (int b = 0; b < nb; ++b)
+    if (body_mat[b] < 0 || body_mat[b] >= c->n_mat || !(body_rho[b] >= 0) || body_parent[b] >= b ||
+        body_parent[b] < -1)
+      return ORC_EINVAL;
+  double *t = malloc((size_t)nt * 9 * sizeof(double));
+  int *tb = malloc((size_t)nt * sizeof(int));
+  if (!t || !tb) {
+    free(t); free(tb);
+    return ORC_EINVAL;
+  }
+  for (int k = 0; k < nt; ++k) {
+    if (tri_body[k] < 0 || tri_body[k] >= nb) {
+      free(t); free(tb);
+      return ORC_EINVAL;
+    }
+    tb[k] = tri_body[k];
+    for (int q = 0; q < 3; ++q) {
+      int i = tris[3 * k + q];
+      if (i < 0 || i >= nv) {
+        free(t); free(tb);
+        return ORC_EINVAL;
+      }
+      for (int a = 0; a < 3; ++a) t[9 * k + 3 * q + a] = (double)v[3 * i + a];
+    }
+  }
+  free(c->tri); free(c->tri_body);
+  c->tri = t;
+  c->tri_body = tb;
+  c->n_tri = nt;
+  c->n_body = nb;
+  for (int b = 0; b < nb; ++b) {
+    c->body_mat[b] = body_mat[b];
+    c->body_rho[b] = (double)body_rho[b];
+    c->body_parent[b] = body_parent[b];
+  }
+  c->have_mesh = 1;
+  return ORC_OK;
+}
+
+/* Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013): the
+ * triangle is sheared into the ray's frame (kz the dominant axis of dir) and
+ * the three edge functions U, V, W of the origin are evaluated; an edge
+ * function exactly zero counts as inside for only one of the two triangles
+ * that share the edge (half-open rule on the edge's projected direction,
+ * normalised by the triangle's facing), so a ray through an edge or a vertex
+ * crosses the surface exactly once.  Returns 1 and the ray parameter *t on a
+ * hit. */
+static int edge_incl(double ex, double ey) { return ey > 0 || (ey == 0 && ex < 0); }
+typedef struct {
+  int kx, ky, kz;
+  double Sx, Sy, Sz;
+} shear_t;
+static void shear_of(const double dir[3], shear_t *h) {
+  int kz = 0;
+  if (fabs(dir[1]) > fabs(dir[kz])) kz = 1;
+  if (fabs(dir[2]) > fabs(dir[kz])) kz = 2;
+  int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+  if (dir[kz] < 0) { int tmp = kx; kx = ky; ky = tmp; }
+  h->kx = kx; h->ky = ky; h->kz = kz;
+  h->Sx = dir[kx] / dir[kz];
+  h->Sy = dir[ky] / dir[kz];
+  h->Sz = 1.0 / dir[kz];
+}
+static int ray_tri(const double org[3], const shear_t *h, const double *tv, double *t) {
+  double A[3], B[3], C[3];
+  for (int i = 0; i < 3; ++i) {
+    A[i] = tv[i] - org[i];
+    B[i] = tv[3 + i] - org[i];
+    C[i] = tv[6 + i] - org[i];
+  }
+  const double Ax = A[h->kx] - h->Sx * A[h->kz], Ay = A[h->ky] - h->Sy * A[h->kz];
+  const double Bx = B[h->kx] - h->Sx * B[h->kz], By = B[h->ky] - h->Sy * B[h->kz];
+  const double Cx = C[h->kx] - h->Sx * C[h->kz], Cy = C[h->ky] - h->Sy * C[h->kz];
+  const double U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+  const double det = U + V + W;
+  if (det == 0) return 0;
+  const double sg = det > 0 ? 1.0 : -1.0;
+  if (!(sg * U > 0 || (U == 0 && edge_incl(sg * (Cx - Bx), sg * (Cy - By))))) return 0;
+  if (!(sg * V > 0 || (V == 0 && edge_incl(sg * (Ax - Cx), sg * (Ay - Cy))))) return 0;
+  if (!(sg * W > 0 || (W == 0 && edge_incl(sg * (Bx - Ax), sg * (By - Ay))))) return 0;
+  const double T = h->Sz * (U * A[h->kz] + V * B[h->kz] + W * C[h->kz]);
+  *t = T / det;
+  return 1;
+}
+
+/* Per-material column masses rho*L (g/cm^3 x mm) along x + t w, t in (0, t1):
+ * every crossing of body b's surface adds sign x t to its inside length
+ * (+ on leaving, - on entering; a closed surface crossed from outside sums to
+ * the length inside it), and the body's material replaces its parent's
+ * there.  The sums are taken about the point of the ray closest to the
+ * origin, which keeps the parameters small. */
+static void mesh_rhoL(const orc_ctx *c, const double x[3], const double w[3], double t1, double *rhoL) {
+  double t0 = -(x[0] * w[0] + x[1] * w[1] + x[2] * w[2]);
+  double org[3] = {x[0] + t0 * w[0], x[1] + t0 * w[1], x[2] + t0 * w[2]};
+  shear_t h;
+  shear_of(w, &h);
+  double Lb[ORC_MAXBODY] = {0};
+  for (int k = 0; k < c->n_tri; ++k) {
+    double t;
+    const double *tv = c->tri + 9 * k;
+    if (!ray_tri(org, &h, tv, &t)) continue;
+    if (!(t + t0 > 0 && t + t0 < t1)) continue;
+    double e1[3] = {tv[3] - tv[0], tv[4] - tv[1], tv[5] - tv[2]};
+    double e2[3] = {tv[6] - tv[0], tv[7] - tv[1], tv[8] - tv[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double dn = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+    Lb[c->tri_body[k]] += dn > 0 ? t : -t;
+  }
+  for (int b = 0; b < c->n_body; ++b) {
+    if (Lb[b] == 0) continue;
+    rhoL[c->body_mat[b]] += c->body_rho[b] * Lb[b];
+    const int pb = c->body_parent[b];
+    if (pb >= 0) rhoL[c->body_mat[pb]] -= c->body_rho[pb] * Lb[b];
+  }
+}
+
+/* Primary image of the mesh geometry, eq. (Ip) with exact path lengths. */
+int orc_mesh_primary(const orc_ctx *c, double beta, double *Ip) {
+  if (!(c->have_tables && c->have_mesh && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
+  pose_t P;
+  pose(c, beta, &P);
+  for (int j = 0; j < c->nv; ++j)
+    for (int i = 0; i < c->nu; ++i) {
+      double X[3];
+      det_point(c, &P, i + 0.5, j + 0.5, X);
+      double D[3] = {X[0] - P.s[0], X[1] - P.s[1], X[2] - P.s[2]};
+      double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      double w[3] = {D[0] / d, D[1] / d, D[2] / d};
+      double rhoL[ORC_MAXMAT] = {0};
+      mesh_rhoL(c, P.s, w, d, rhoL);
+      double sum = primary_sum(c, rhoL, NULL);
+      Ip[(size_t)j * c->nu + i] = sum * c->pu * c->pv * (c->sdd / d) / (4.0 * PI * d * d);
+    }
+  return ORC_OK;
+}
+
 int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *bound) {
   if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
   if (!(step > 0)) return ORC_EINVAL;
