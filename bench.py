@@ -64,6 +64,8 @@ def parse():
                    help="tensor-core throughput of the denoiser's convolutions and its inference latency")
     p.add_argument("--correct-eval", action="store_true", help="iterative scatter correction on a large flat panel")
     p.add_argument("--vr-eval", action="store_true", help="expected-value vs sampled-type point-detector scoring")
+    p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
+    p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
     p.add_argument("--cor-detector", type=int, default=2048)
     p.add_argument("--cor-pixel", type=float, default=0.1)
@@ -917,6 +919,46 @@ def run_vr_eval(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mesh_bench(args):
+    """Primary images of the triangle-mesh (CAD) cylinder-rod phantom by ray casting
+    (eq. Ip with exact path lengths): rays per second through the hierarchy."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+    from mc_inputs import default_table_path, kramers_spectrum, read_tables
+    from mc_inputs.meshes import cylinder_rod_mesh
+
+    mcx.build()
+    tp = default_table_path("full", tempfile.mkdtemp(prefix="mcmesh"))
+    T = read_tables(tp)
+    mesh = cylinder_rod_mesh(args.mesh_segments)
+    ctx = mcx.Context(0)
+    ctx.load_tables(tp)
+    ctx.set_spectrum(*kramers_spectrum(T))
+    ctx.set_geometry(300.0, 600.0, 512, 512, 0.25, 0.25)
+    ctx.load_mesh(mesh)
+    n_ang = args.angles if args.angles > 1 else 36
+    angles = (2.0 * np.pi * np.arange(n_ang) / n_ang).astype(np.float32)
+    out = {"primary": ctx.empty_images(n_ang)}
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ctx.project(angles, 1, 0.25, 1, scatter=False, out=out, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.project(angles, 1, 0.25, 1, scatter=False, out=out, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rays = 512 * 512 * n_ang
+    line = {"metric": "mesh primary rays/s (CAD surface model, BVH ray casting)", "value": rays / (ms / 1e3),
+            "unit": "rays/s", "higher_is_better": True, "dtype": "f32",
+            "config": {"workload": f"cylinder-rod surfaces, {len(mesh['triangles'])} triangles, 512^2 x 0.25 mm, "
+                                   f"{n_ang} angles, 111-bin spectrum", "steps": args.steps},
+            "ms_per_step": ms, "ms_per_projection": ms / n_ang}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.denoise_eval:
@@ -927,6 +969,8 @@ def main():
         run_correct_eval(args)
     elif args.vr_eval:
         run_vr_eval(args)
+    elif args.mesh_bench:
+        run_mesh_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -48,6 +48,7 @@ extern "C" {
 
 #define MC_MAX_MATERIALS 8
 #define MC_MAX_BINS 512
+#define MC_MAX_BODIES 64
 
 typedef struct mc_ctx mc_ctx;
 
@@ -275,16 +276,24 @@ int mc_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, int n, int h, 
  * 2. Launch shape: short transport runs of probe_photons histories per angle
  *    at the chosen step, over block size {128, 192, 256}, blocks per SM
  *    {1 .. occupancy} and tally mode {global, warp}; the fastest is kept.
- * The chosen block_size, blocks_per_sm and tally_mode are written into the
- * context's options; *out receives them with the step and the measured
- * histories/s.  Allocates temporary device buffers.  Errors as mc_project. */
+ * 3. Russian roulette (Sec. II-C.1): thresholds of 0.3, 1, 3 and 10 times
+ *    the mean attenuated pseudo-particle score of a run without roulette are
+ *    compared by figure of merit 1 / (noise^2 x time), the noise being the
+ *    8-batch estimate of the scatter image's relative L2 error; the best
+ *    (or none) is kept.
+ * The chosen block_size, blocks_per_sm, tally_mode and rr_threshold are
+ * written into the context's options; *out receives them with the step, the
+ * measured histories/s and the figure-of-merit gain of the roulette.
+ * Allocates temporary device buffers.  Errors as mc_project. */
 typedef struct mc_tuning {
   float step_mm;
   int block_size;
   int blocks_per_sm;
   int tally_mode;
   double histories_per_s;
-  double step_error; /* relative L2 of the chosen step's primary vs step_min */
+  double step_error;   /* relative L2 of the chosen step's primary vs step_min */
+  float rr_threshold;  /* chosen Russian-roulette threshold (0: off) */
+  double rr_fom_gain;  /* figure of merit with it / without roulette */
 } mc_tuning;
 int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t probe_photons, float step_min,
                 float step_max, float step_tol, mc_tuning *out, void *stream);
@@ -318,6 +327,24 @@ int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t pro
 #define MC_STATIC_MAX_ANGLES 4096
 int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm,
                               uint64_t seed, float *scatter_out, void *stream);
+
+/* Triangle-mesh geometry (the paper's CAD surface model, Sec. II-A: closed
+ * triangulated surfaces).  Host arrays: vertices FP32 [n_vertices][3] (mm, the
+ * volume frame: rotation axis z), triangles int32 [n_triangles][3] (counter-
+ * clockwise seen from outside), tri_body int32 [n_triangles], and per body
+ * material (table index), density (g/cm^3, >= 0) and parent (-1: in vacuum,
+ * else an earlier body inside which this one replaces the parent's
+ * material); up to MC_MAX_BODIES bodies.  Each body's surface must be closed.
+ * The library copies the data, builds a bounding-volume hierarchy and switches
+ * the context to this geometry until mc_load_volume is called again.  With a
+ * mesh, mc_project computes primary images (eq. Ip) by exact ray casting:
+ * watertight ray/triangle tests, a body's path length as the signed sum of its
+ * crossings; scatter on meshes is not available (MC_ERR_STATE).
+ * Errors: STATE (no tables), INVALID_ARG (indices, bodies, non-finite
+ * vertices), CUDA/OOM. */
+int mc_load_mesh(mc_ctx *ctx, const float *vertices, int n_vertices, const int *triangles, const int *tri_body,
+                 int n_triangles, const int *body_material, const float *body_density, const int *body_parent,
+                 int n_bodies);
 
 /* Detector response (Sec. II-D.2: the model maps each detected photon energy
  * through the panel's energy-response curve).  eta[n]: the expected signal

@@ -35,7 +35,7 @@ EXPORTED = [
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
     "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
-    "mc_probe_gather", "mc_set_detector_response", "mc_probe_mma",
+    "mc_probe_gather", "mc_set_detector_response", "mc_probe_mma", "mc_load_mesh",
 ]
 
 
@@ -53,6 +53,8 @@ class Tuning(C.Structure):
         ("tally_mode", C.c_int),
         ("histories_per_s", C.c_double),
         ("step_error", C.c_double),
+        ("rr_threshold", C.c_float),
+        ("rr_fom_gain", C.c_double),
     ]
 
 
@@ -143,6 +145,7 @@ def library():
         L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
         L.mc_set_detector_response.argtypes = [P, vp, i]
         L.mc_probe_mma.argtypes = [i, i, i, vp, vp]
+        L.mc_load_mesh.argtypes = [P, vp, i, vp, vp, i, vp, vp, vp, i]
         _lib = L
     return _lib
 
@@ -286,6 +289,17 @@ class Context:
         self.nu, self.nv = nu, nv
         self._check(self.L.mc_set_geometry(self.h, sod, sdd, nu, nv, pu, pv))
 
+    def load_mesh(self, mesh):
+        """Triangle-mesh geometry (an mc_inputs.meshes dict of host arrays); primary images only."""
+        v = np.ascontiguousarray(mesh["vertices"], dtype=np.float32)
+        t = np.ascontiguousarray(mesh["triangles"], dtype=np.int32)
+        tb = np.ascontiguousarray(mesh["tri_body"], dtype=np.int32)
+        bm = np.ascontiguousarray(mesh["body_material"], dtype=np.int32)
+        br = np.ascontiguousarray(mesh["body_density"], dtype=np.float32)
+        bp = np.ascontiguousarray(mesh["body_parent"], dtype=np.int32)
+        self._check(self.L.mc_load_mesh(self.h, _np_ptr(v), len(v), _np_ptr(t), _np_ptr(tb), len(t), _np_ptr(bm),
+                                        _np_ptr(br), _np_ptr(bp), len(bm)))
+
     def set_detector_response(self, eta):
         """eta at the table's energy nodes (keV per photon, host), or None for eta(E) = E."""
         if eta is None:
@@ -358,13 +372,14 @@ class Context:
                 saved = json.load(f).get(cache_key)
             if saved:
                 self.set_options(block_size=saved["block_size"], blocks_per_sm=saved["blocks_per_sm"],
-                                 tally_mode=saved["tally_mode"])
+                                 tally_mode=saved["tally_mode"], rr_threshold=saved.get("rr_threshold", 0.0))
                 return saved
         a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
         t = Tuning()
         self._check(self.L.mc_autotune(self.h, _np_ptr(a), len(a), int(probe_photons), float(step_min),
                                        float(step_max), float(step_tol), C.byref(t), _stream_handle(stream)))
         self.opt.block_size, self.opt.blocks_per_sm, self.opt.tally_mode = t.block_size, t.blocks_per_sm, t.tally_mode
+        self.opt.rr_threshold = t.rr_threshold
         res = {k: getattr(t, k) for k, _ in Tuning._fields_}
         if cache and cache_key:
             data = {}

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["mc_api.cu", "k_transport.cu", "k_primary.cu", "k_post.cu", "k_static.cu", "k_conv.cu", "k_nn.cu",
-           "denoiser.cu", "k_recon.cu", "k_probe.cu"]
+           "denoiser.cu", "k_recon.cu", "k_probe.cu", "k_mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -39,6 +39,13 @@ struct mc_ctx {
   float2* d_blob = nullptr;
   int blob_bytes = 0, blob_stage = 0;
   bool blob_dirty = true;
+  // triangle-mesh geometry (replaces the volume while mesh_mode)
+  bool have_mesh = false, mesh_mode = false;
+  float4 *d_mesh_nodes = nullptr, *d_mesh_tris = nullptr;
+  int4* d_mesh_bodies = nullptr;
+  float* d_mesh_rho = nullptr;
+  int mesh_nodes = 0, mesh_tris = 0, mesh_bodies = 0;
+  double mesh_rmax = 0;  // largest distance of a vertex from the rotation axis
   // volume
   bool have_volume = false;
   uint32_t* d_vox = nullptr;  // packed voxel words (material | FP16 density)
@@ -319,13 +326,15 @@ SpectrumView spectrum_view(const mc_ctx* ctx) {
 int check_ready(mc_ctx* ctx) {
   if (!ctx) return MC_ERR_INVALID_ARG;
   if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "tables not loaded");
-  if (!ctx->have_volume) return fail(ctx, MC_ERR_STATE, "volume not loaded");
+  if (ctx->mesh_mode ? !ctx->have_mesh : !ctx->have_volume)
+    return fail(ctx, MC_ERR_STATE, ctx->mesh_mode ? "mesh not loaded" : "volume not loaded");
   if (!ctx->have_spectrum) return fail(ctx, MC_ERR_STATE, "spectrum not set");
   if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
   if (ctx->opt.doppler && !ctx->bound)
     return fail(ctx, MC_ERR_STATE, "Doppler broadening needs the bound-electron tables (version 2)");
-  const double rmax = 0.5 * std::sqrt((double)ctx->nx * ctx->dx * ctx->nx * ctx->dx +
-                                      (double)ctx->ny * ctx->dy * ctx->ny * ctx->dy);
+  const double rmax = ctx->mesh_mode ? ctx->mesh_rmax
+                                     : 0.5 * std::sqrt((double)ctx->nx * ctx->dx * ctx->nx * ctx->dx +
+                                                       (double)ctx->ny * ctx->dy * ctx->ny * ctx->dy);
   if (!(rmax < ctx->sod) || !(rmax < (double)ctx->sdd - ctx->sod))
     return fail(ctx, MC_ERR_INVALID_ARG, "the volume must lie strictly between source and detector");
   return MC_OK;
@@ -338,10 +347,24 @@ int check_ready(mc_ctx* ctx) {
 // is captured once into a CUDA graph and replayed while its launch shape
 // (sizes, pointers, options) stays the same; the seed is read on the device, so
 // one graph serves every seed.
+MeshView mesh_view(const mc_ctx* c) {
+  MeshView m;
+  m.nodes = c->d_mesh_nodes;
+  m.tris = c->d_mesh_tris;
+  m.bodies = c->d_mesh_bodies;
+  m.body_rho = c->d_mesh_rho;
+  m.n_nodes = c->mesh_nodes;
+  m.n_tris = c->mesh_tris;
+  m.n_bodies = c->mesh_bodies;
+  return m;
+}
+
 int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uint64_t h_begin, uint64_t h_count,
                  float step, uint64_t seed, float* primary_out, float* scatter_out, float* var_out, void* stream) {
   int rc = check_ready(ctx);
   if (rc) return rc;
+  if (ctx->mesh_mode && scatter_out)
+    return fail(ctx, MC_ERR_STATE, "scatter on the triangle-mesh geometry is not available: primary images only");
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   (void)cudaGetLastError();  // a failed call elsewhere must not be blamed on this one
@@ -468,7 +491,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_stats, 0, S_NSTAT * 8, q);
     if (e == cudaSuccess && primary_out) {
       e = record(ctx->ev[2], q, capture);
-      if (e == cudaSuccess) e = launch_primary(pp, q);
+      if (e == cudaSuccess) e = ctx->mesh_mode ? launch_primary_mesh(pp, mesh_view(ctx), q) : launch_primary(pp, q);
       if (e == cudaSuccess) e = record(ctx->ev[3], q, capture);
     }
     if (e == cudaSuccess && scatter_out) {
@@ -481,7 +504,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_st, ctx->d_stats, S_NSTAT * 8, cudaMemcpyDeviceToHost, q);
     return e;
   };
-  if (ctx->opt.use_graph) {
+  if (ctx->opt.use_graph && !ctx->mesh_mode) {
     // graph key: every parameter and size the captured sequence depends on
     std::vector<unsigned char> key(sizeof(pp) + sizeof(tp) + 64);
     std::memcpy(key.data(), &pp, sizeof(pp));
@@ -629,6 +652,10 @@ void mc_destroy(mc_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->d_blob);
   cudaFree(ctx->d_vox);
+  cudaFree(ctx->d_mesh_nodes);
+  cudaFree(ctx->d_mesh_tris);
+  cudaFree(ctx->d_mesh_bodies);
+  cudaFree(ctx->d_mesh_rho);
   cudaFree(ctx->d_spec);
   cudaFree(ctx->d_tally);
   cudaFree(ctx->d_stats);
@@ -793,6 +820,69 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz;
   ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   ctx->have_volume = true;
+  ctx->mesh_mode = false;
+  return MC_OK;
+}
+
+int mc_load_mesh(mc_ctx* ctx, const float* vertices, int n_vertices, const int* triangles, const int* tri_body,
+                 int n_triangles, const int* body_material, const float* body_density, const int* body_parent,
+                 int n_bodies) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "load tables before the mesh");
+  if (!vertices || !triangles || !tri_body || !body_material || !body_density || !body_parent || n_vertices < 3 ||
+      n_triangles < 1 || n_bodies < 1 || n_bodies > MC_MAX_BODIES)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad mesh sizes");
+  for (int b = 0; b < n_bodies; ++b)
+    if (body_material[b] < 0 || body_material[b] >= ctx->n_mat || !(body_density[b] >= 0.f) ||
+        !std::isfinite(body_density[b]) || body_parent[b] < -1 || body_parent[b] >= b)
+      return fail(ctx, MC_ERR_INVALID_ARG, "bad body (material, density >= 0, parent -1 or an earlier body)");
+  double rmax = 0;
+  for (int i = 0; i < n_vertices; ++i) {
+    const float* p = vertices + 3 * i;
+    if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]))
+      return fail(ctx, MC_ERR_INVALID_ARG, "non-finite vertex");
+    rmax = std::max(rmax, std::sqrt((double)p[0] * p[0] + (double)p[1] * p[1]));
+  }
+  for (int k = 0; k < n_triangles; ++k) {
+    if (tri_body[k] < 0 || tri_body[k] >= n_bodies) return fail(ctx, MC_ERR_INVALID_ARG, "triangle body out of range");
+    for (int q = 0; q < 3; ++q)
+      if (triangles[3 * k + q] < 0 || triangles[3 * k + q] >= n_vertices)
+        return fail(ctx, MC_ERR_INVALID_ARG, "triangle vertex out of range");
+  }
+  std::vector<float4> nodes, tris;
+  build_mesh_bvh(vertices, triangles, tri_body, n_triangles, nodes, tris);
+  std::vector<int4> bodies(n_bodies);
+  std::vector<float> rho(n_bodies);
+  for (int b = 0; b < n_bodies; ++b) {
+    const int pb = body_parent[b];
+    float dens = body_density[b];
+    int dbits;
+    std::memcpy(&dbits, &dens, 4);
+    bodies[b] = make_int4(body_material[b], pb, pb >= 0 ? body_material[pb] : 0, dbits);
+    rho[b] = body_density[b];
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaFree(ctx->d_mesh_nodes);
+  cudaFree(ctx->d_mesh_tris);
+  cudaFree(ctx->d_mesh_bodies);
+  cudaFree(ctx->d_mesh_rho);
+  ctx->d_mesh_nodes = ctx->d_mesh_tris = nullptr;
+  ctx->d_mesh_bodies = nullptr;
+  ctx->d_mesh_rho = nullptr;
+  ctx->have_mesh = ctx->mesh_mode = false;
+  CK(cudaMalloc((void**)&ctx->d_mesh_nodes, nodes.size() * sizeof(float4)), "mesh allocation");
+  CK(cudaMalloc((void**)&ctx->d_mesh_tris, tris.size() * sizeof(float4)), "mesh allocation");
+  CK(cudaMalloc((void**)&ctx->d_mesh_bodies, bodies.size() * sizeof(int4)), "mesh allocation");
+  CK(cudaMalloc((void**)&ctx->d_mesh_rho, rho.size() * sizeof(float)), "mesh allocation");
+  CK(cudaMemcpy(ctx->d_mesh_nodes, nodes.data(), nodes.size() * sizeof(float4), cudaMemcpyHostToDevice), "mesh upload");
+  CK(cudaMemcpy(ctx->d_mesh_tris, tris.data(), tris.size() * sizeof(float4), cudaMemcpyHostToDevice), "mesh upload");
+  CK(cudaMemcpy(ctx->d_mesh_bodies, bodies.data(), bodies.size() * sizeof(int4), cudaMemcpyHostToDevice), "mesh upload");
+  CK(cudaMemcpy(ctx->d_mesh_rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice), "mesh upload");
+  ctx->mesh_nodes = (int)(nodes.size() / 2);
+  ctx->mesh_tris = n_triangles;
+  ctx->mesh_bodies = n_bodies;
+  ctx->mesh_rmax = rmax;
+  ctx->have_mesh = ctx->mesh_mode = true;
   return MC_OK;
 }
 
@@ -955,6 +1045,71 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   ctx->opt.block_size = best.block_size;
   ctx->opt.blocks_per_sm = best.blocks_per_sm;
   ctx->opt.tally_mode = best.tally_mode;
+  // 3. Russian roulette threshold (Sec. II-C.1) by figure of merit 1 / (noise^2 x time): the noise is the
+  //    batch estimate of the scatter image's relative L2 error; thresholds are multiples of the mean
+  //    attenuated pseudo-particle score of a run without roulette
+  float best_rr = 0.f;
+  double fom0 = 0, best_fom = 0;
+  {
+    float* d_var = nullptr;
+    e = cudaMalloc((void**)&d_var, n * 4);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "autotune allocation"));
+    std::vector<float> var(n);
+    const mc_options shape = ctx->opt;
+    auto fom_of = [&](float rr, double* mean_score) -> int {
+      ctx->opt = shape;
+      ctx->opt.rr_threshold = rr;
+      ctx->opt.n_batches = 8;
+      ctx->opt.use_graph = 0;
+      int r = project_impl(ctx, angles, n_angles, probe, 0, probe, best_step, 11, nullptr, d_img, d_var, stream);
+      if (r && r != MC_ERR_LIMIT) return r;
+      if (cudaMemcpy(img.data(), d_img, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(var.data(), d_var, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "autotune readback");
+      double s2 = 0, v = 0, sum = 0;
+      for (size_t i = 0; i < n; ++i) {
+        s2 += (double)img[i] * img[i];
+        v += var[i];
+        sum += img[i];
+      }
+      const double ms = ctx->stats[10];
+      if (mean_score) *mean_score = ctx->stats[3] > 0 ? sum / ctx->stats[3] : 0.0;
+      best_fom = (s2 > 0 && v > 0 && ms > 0) ? s2 / (v * ms) : 0.0;  // 1 / (rel noise^2 x ms)
+      return MC_OK;
+    };
+    double xbar = 0;
+    rc = fom_of(0.f, &xbar);
+    if (rc) {
+      cudaFree(d_var);
+      ctx->opt = saved;
+      return finish(rc);
+    }
+    fom0 = best_fom;
+    double top = fom0;
+    const float mult[4] = {0.3f, 1.f, 3.f, 10.f};
+    for (int c = 0; c < 4 && xbar > 0; ++c) {
+      const float thr = (float)(mult[c] * xbar);
+      rc = fom_of(thr, nullptr);
+      if (rc) {
+        cudaFree(d_var);
+        ctx->opt = saved;
+        return finish(rc);
+      }
+      if (best_fom > top) {
+        top = best_fom;
+        best_rr = thr;
+      }
+    }
+    best_fom = top;
+    cudaFree(d_var);
+  }
+  ctx->opt = saved;
+  ctx->opt.block_size = best.block_size;
+  ctx->opt.blocks_per_sm = best.blocks_per_sm;
+  ctx->opt.tally_mode = best.tally_mode;
+  ctx->opt.rr_threshold = best_rr;
+  out->rr_threshold = best_rr;
+  out->rr_fom_gain = fom0 > 0 ? best_fom / fom0 : 1.0;
   out->step_mm = best_step;
   out->block_size = best.block_size;
   out->blocks_per_sm = best.blocks_per_sm;
@@ -971,8 +1126,6 @@ int mc_fdk(mc_ctx* ctx, const float* p, int n_proj, const float* angles, int NU,
            float dx, float dy, float dz, float* vol, void* stream) {
   if (!ctx) return MC_ERR_INVALID_ARG;
   if (!ctx->have_geometry) return fail(ctx, MC_ERR_STATE, "geometry not set");
-  if (ctx->opt.doppler && !ctx->bound)
-    return fail(ctx, MC_ERR_STATE, "Doppler broadening needs the bound-electron tables (version 2)");
   if (!p || !vol || !angles || n_proj < 1 || NU < 2 || NV < 2 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) ||
       !(dy > 0) || !(dz > 0) || NU > 50000)
     return fail(ctx, MC_ERR_INVALID_ARG, "bad reconstruction arguments");

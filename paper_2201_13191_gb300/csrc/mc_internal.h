@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mc.h"
 
 namespace mcx {
@@ -126,6 +128,21 @@ int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_p
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
+
+// Triangle-mesh geometry (k_mesh.cu): BVH nodes as float4 pairs (lo.xyz + first,
+// hi.xyz + count; count 0 = inner node with children first, first + 1),
+// triangles as three float4 (xyz; the first's w carries the body id), bodies as
+// int4 (material, parent or -1, parent material, density bits).
+struct MeshView {
+  const float4* nodes;
+  const float4* tris;
+  const int4* bodies;
+  const float* body_rho;
+  int n_nodes, n_tris, n_bodies;
+};
+void build_mesh_bvh(const float* v, const int* tris, const int* tri_body, int nt, std::vector<float4>& nodes,
+                    std::vector<float4>& out_tris);
+cudaError_t launch_primary_mesh(const PrimaryParams& p, const MeshView& m, cudaStream_t s);
 // Checks a device-resident volume (ids < n_mat, finite non-negative binary16
 // densities); *bad_host = 1 if any voxel fails.  Synchronises s.
 cudaError_t validate_volume_device(const uint8_t* mat, const uint16_t* rho, size_t n, int n_mat, cudaStream_t s,

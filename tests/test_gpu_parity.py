@@ -272,7 +272,11 @@ def test_autotune_picks_a_valid_configuration(gpu, table_path, tables, tmp_path)
     res = c.autotune([0.0, 1.0], 200_000, 0.1, 0.8, 5e-3, cache=str(tmp_path / "tune.json"), cache_key="cyl64")
     assert 0.1 <= res["step_mm"] <= 0.8 + 1e-6 and res["step_error"] <= 5e-3
     assert res["block_size"] in (128, 192, 256) and res["blocks_per_sm"] >= 1 and res["histories_per_s"] > 0
-    # the tuned launch shape computes the same image
+    # roulette: none, or a threshold whose figure of merit beat none
+    assert res["rr_threshold"] >= 0.0 and res["rr_fom_gain"] >= 1.0
+    assert (res["rr_threshold"] == 0.0) == (res["rr_fom_gain"] == 1.0)
+    # the tuned launch shape computes the same image (roulette off: it changes the estimator, not its mean)
+    c.set_options(rr_threshold=0.0)
     got = c.project([0.5], 100_000, 0.25, 9, primary=False)["scatter"].cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-12)
     # a second context reuses the cached result
