@@ -19,7 +19,10 @@
  *     scatter-toward-detector pdfs eqs. (pmueforIncoherent) and
  *     (pmueforcoherent), split into N_split pseudo-particles aimed at
  *     randomly selected pixels (Sec. II-A and II-C.1), optional Russian
- *     roulette, summed per eq. (Is).
+ *     roulette, summed per eq. (Is);
+ *   - the same histories through closed triangulated bodies (the CAD surface
+ *     model of Sec. II-A) with exact path lengths: free flights over the
+ *     sorted surface crossings, point-detector attenuation by exact chords.
  *
  * Readings of the paper that it implements (all listed in the design notes):
  * lengths in mm, energies in keV, eta(E) = E unless a detector response
@@ -75,6 +78,8 @@ typedef struct {
   int *tri_body; /* [n_tri] */
   int body_mat[ORC_MAXBODY], body_parent[ORC_MAXBODY];
   double body_rho[ORC_MAXBODY];
+  int mesh_active; /* photon histories run in the mesh (set by orc_load_mesh, cleared by orc_load_volume) */
+  double mesh_rxy; /* largest distance of a vertex from the rotation axis */
   /* geometry */
   int have_geometry, nu, nv;
   double sod, sdd, pu, pv;
@@ -253,6 +258,7 @@ int orc_load_volume(orc_ctx *c, const uint8_t *mat, const uint16_t *rho16, int n
   c->mat = m; c->rho = r;
   c->nx = nx; c->ny = ny; c->nz = nz; c->dx = dx; c->dy = dy; c->dz = dz;
   c->have_volume = 1;
+  c->mesh_active = 0;
   return ORC_OK;
 }
 
@@ -829,7 +835,14 @@ int orc_load_mesh(orc_ctx *c, const float *v, int nv, const int *tris, const int
     c->body_rho[b] = (double)body_rho[b];
     c->body_parent[b] = body_parent[b];
   }
+  double r2 = 0;
+  for (int i = 0; i < nv; ++i) {
+    const double q = (double)v[3 * i] * v[3 * i] + (double)v[3 * i + 1] * v[3 * i + 1];
+    if (q > r2) r2 = q;
+  }
+  c->mesh_rxy = sqrt(r2);
   c->have_mesh = 1;
+  c->mesh_active = 1;
   return ORC_OK;
 }
 
@@ -881,11 +894,13 @@ static int ray_tri(const double org[3], const shear_t *h, const double *tv, doub
 
 /* Per-material column masses rho*L (g/cm^3 x mm) along x + t w, t in (0, t1):
  * every crossing of body b's surface adds sign x t to its inside length
- * (+ on leaving, - on entering; a closed surface crossed from outside sums to
- * the length inside it), and the body's material replaces its parent's
- * there.  The sums are taken about the point of the ray closest to the
- * origin, which keeps the parameters small. */
-static void mesh_rhoL(const orc_ctx *c, const double x[3], const double w[3], double t1, double *rhoL) {
+ * (+ on leaving, - on entering, t measured from x: crossings of a closed
+ * surface alternate, so the sum is the length inside it, also when x itself
+ * is inside), and the body's material replaces its parent's there.  The ray
+ * is tested from the point closest to the origin, which keeps the
+ * parameters small. */
+static long mesh_rhoL(const orc_ctx *c, const double x[3], const double w[3], double t1, double *rhoL) {
+  long ncross = 0;
   double t0 = -(x[0] * w[0] + x[1] * w[1] + x[2] * w[2]);
   double org[3] = {x[0] + t0 * w[0], x[1] + t0 * w[1], x[2] + t0 * w[2]};
   shear_t h;
@@ -900,7 +915,8 @@ static void mesh_rhoL(const orc_ctx *c, const double x[3], const double w[3], do
     double e2[3] = {tv[6] - tv[0], tv[7] - tv[1], tv[8] - tv[2]};
     double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     double dn = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
-    Lb[c->tri_body[k]] += dn > 0 ? t : -t;
+    Lb[c->tri_body[k]] += dn > 0 ? t + t0 : -(t + t0);
+    ++ncross;
   }
   for (int b = 0; b < c->n_body; ++b) {
     if (Lb[b] == 0) continue;
@@ -908,6 +924,83 @@ static void mesh_rhoL(const orc_ctx *c, const double x[3], const double w[3], do
     const int pb = c->body_parent[b];
     if (pb >= 0) rhoL[c->body_mat[pb]] -= c->body_rho[pb] * Lb[b];
   }
+  return ncross;
+}
+
+/* One surface crossing of a half-line: its parameter and triangle. */
+typedef struct {
+  double t;
+  int tri;
+} crossing_t;
+static int cmp_crossing(const void *pa, const void *pb) {
+  const crossing_t *a = pa, *b = pb;
+  if (a->t != b->t) return a->t < b->t ? -1 : 1;
+  return a->tri < b->tri ? -1 : (a->tri > b->tri);
+}
+
+/* Free flight through the mesh with exact path lengths (the CAD model's ray
+ * tracing, Sec. II-A).  Every crossing of the half-line x + t w, t > 0, is
+ * collected (buf holds n_tri entries) and sorted by t.  Body b contains x when
+ * the half-line crosses its closed surface an odd number of times, so the
+ * start medium follows from the crossings themselves; each crossing then
+ * toggles its body, and the medium is the deepest body containing the point
+ * (a parent precedes its children: the highest index present).  Inside body
+ * b the optical depth grows by rho_b mu/rho(m_b, E) per unit length.  Returns
+ * 1 with the interaction distance *tint and material *mint when the depth
+ * reaches tau_star, 0 after the last crossing (escape: outside every closed
+ * surface); *nseg += the segments walked. */
+static int mesh_flight(const orc_ctx *c, crossing_t *buf, const double x[3], const double w[3], double E,
+                       double tau_star, double *tint, int *mint, long *nseg) {
+  double t0 = -(x[0] * w[0] + x[1] * w[1] + x[2] * w[2]);
+  double org[3] = {x[0] + t0 * w[0], x[1] + t0 * w[1], x[2] + t0 * w[2]};
+  shear_t h;
+  shear_of(w, &h);
+  int n = 0;
+  uint64_t inside = 0;
+  for (int k = 0; k < c->n_tri; ++k) {
+    double t;
+    if (!ray_tri(org, &h, c->tri + 9 * k, &t)) continue;
+    t += t0;
+    if (!(t > 0)) continue;
+    buf[n].t = t;
+    buf[n].tri = k;
+    ++n;
+    inside ^= 1ull << c->tri_body[k];
+  }
+  qsort(buf, n, sizeof(crossing_t), cmp_crossing);
+  double tau = 0, tprev = 0;
+  for (int i = 0; i <= n; ++i) {
+    *nseg += 1;
+    if (i == n) break;
+    if (inside) {
+      int b = 63;
+      while (!(inside >> b & 1)) --b;
+      const double mu = c->body_rho[b] * mu_rho_tot(c, c->body_mat[b], E) * 0.1;
+      const double len = buf[i].t - tprev;
+      if (mu > 0 && tau + mu * len >= tau_star) {
+        *tint = tprev + (tau_star - tau) / mu;
+        *mint = c->body_mat[b];
+        return 1;
+      }
+      tau += mu * len;
+    }
+    tprev = buf[i].t;
+    inside ^= 1ull << c->tri_body[buf[i].tri];
+  }
+  return 0;
+}
+
+/* Optical depth at energy E from x to x + t1 w: the fixed-step march through
+ * the volume, or the exact column masses through the mesh. */
+static double path_tau(const orc_ctx *c, const double x[3], const double w[3], double t1, double step, double E,
+                       long *nsteps) {
+  if (!c->mesh_active) return march_tau(c, x, w, 0.0, t1, step, E, nsteps);
+  double rhoL[ORC_MAXMAT] = {0};
+  *nsteps += mesh_rhoL(c, x, w, t1, rhoL);
+  double tau = 0;
+  for (int m = 0; m < c->n_mat; ++m)
+    if (rhoL[m] != 0) tau += mu_rho_tot(c, m, E) * 0.1 * rhoL[m];
+  return tau;
 }
 
 /* Primary image of the mesh geometry, eq. (Ip) with exact path lengths. */
@@ -1033,15 +1126,17 @@ enum {
 int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N, uint64_t h_begin, uint64_t h_end,
                 double step, uint64_t seed, double *Is, double *Is_order, double *analog, double *analog0,
                 double *stats) {
-  if (!(c->have_tables && c->have_volume && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
+  const int mesh = c->mesh_active;
+  if (!(c->have_tables && (mesh || c->have_volume) && c->have_spectrum && c->have_geometry)) return ORC_ESTATE;
   if (!(step > 0) || h_end > N || h_begin > h_end) return ORC_EINVAL;
-  /* the volume must lie between source and detector */
-  double rmax = 0.5 * sqrt(pow(c->nx * c->dx, 2) + pow(c->ny * c->dy, 2));
+  /* the object must lie between source and detector */
+  double rmax = mesh ? c->mesh_rxy : 0.5 * sqrt(pow(c->nx * c->dx, 2) + pow(c->ny * c->dy, 2));
   if (!(rmax < c->sod) || !(rmax < c->sdd - c->sod)) return ORC_EINVAL;
+  crossing_t *xbuf = mesh ? malloc((size_t)c->n_tri * sizeof(crossing_t)) : NULL;
   uint64_t *M = malloc(c->n_bins * sizeof(uint64_t));
   uint64_t *pre = malloc((c->n_bins + 1) * sizeof(uint64_t));
   if (orc_stratify(c->n_bins, c->S, N, M) != ORC_OK) {
-    free(M); free(pre);
+    free(M); free(pre); free(xbuf);
     return ORC_EINVAL;
   }
   pre[0] = 0;
@@ -1078,7 +1173,11 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       int hit = 0;
       double tint = 0;
       int mint = 0;
-      if (clip_box(c, x, w, 0.0, INFINITY, &ta, &tb)) {
+      if (mesh) {
+        long nseg = 0;
+        hit = mesh_flight(c, xbuf, x, w, E, tau_star, &tint, &mint, &nseg);
+        st[ST_FLIGHT_STEPS] += nseg;
+      } else if (clip_box(c, x, w, 0.0, INFINITY, &ta, &tb)) {
         double L = tb - ta;
         long n = (long)ceil(L / step);
         if (n < 1) n = 1;
@@ -1164,7 +1263,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
             x0 = c->rr_threshold;
           }
           long ns = 0;
-          double tp = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
+          double tp = path_tau(c, x, dir, dd, step, Ep, &ns);
           st[ST_NEE_STEPS] += ns;
           sc = x0 * exp(-tp);
         } else {
@@ -1187,9 +1286,9 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
             xr *= c->rr_threshold / x0;
           }
           long ns = 0, ns2 = 0;
-          double tc = march_tau(c, x, dir, 0.0, dd, step, Ep, &ns);
-          double tr = march_tau(c, x, dir, 0.0, dd, step, E, &ns2);
-          st[ST_NEE_STEPS] += ns; /* one march's steps: both walk the same midpoints */
+          double tc = path_tau(c, x, dir, dd, step, Ep, &ns);
+          double tr = path_tau(c, x, dir, dd, step, E, &ns2);
+          st[ST_NEE_STEPS] += ns; /* one march's steps: both walk the same midpoints (or crossings) */
           sc = xc * exp(-tc) + xr * exp(-tr);
         }
         Is[pix] += sc;
@@ -1235,7 +1334,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
   (void)nsteps;
   if (stats)
     for (int k = 0; k < ST_N; ++k) stats[k] += st[k];
-  free(M); free(pre);
+  free(M); free(pre); free(xbuf);
   return ORC_OK;
 }
 

@@ -412,8 +412,10 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     ctx->angles_cap = n_angles;
   }
   if (scatter_out) CK(ensure(ctx->d_tally, ctx->tally_cap, img * nb_img), "tally allocation");
-  // the previous call synchronised its stream, so the pinned buffer is free
-  rc = fill_spectrum(ctx, N, seed, ctx->h_pin);
+  // the previous call synchronised its stream, so the pinned buffer is free; a
+  // primary-only call runs no histories, so any photon count serves (the
+  // stratification is then taken at 2^62 photons, which every bin reaches)
+  rc = fill_spectrum(ctx, scatter_out ? N : (1ull << 62), seed, ctx->h_pin);
   if (rc) return rc;
   std::memcpy(ctx->h_pin + ang_off, angles, (size_t)n_angles * 4);
   const SpectrumView sv = spectrum_view(ctx);
