@@ -951,11 +951,29 @@ def run_mesh_bench(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     rays = 512 * 512 * n_ang
+    # Monte Carlo scatter through the same surfaces: one projection per step
+    N = int(args.photons) if args.photons else 10_000_000
+    sc = {"scatter": ctx.empty_images(1)}
+    for _ in range(max(3, args.warmup)):
+        ctx.project(angles[:1], N, 0.25, 1, primary=False, out=sc, stream=st)
+    e0.record(st)
+    for k in range(args.steps):
+        ctx.project(angles[:1], N, 0.25, 2 + k, primary=False, out=sc, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_sc = e0.elapsed_time(e1) / args.steps
+    stt = ctx.last_stats()
+    ray_casts = stt["nee_rays"] + stt["compton"] + stt["rayleigh"] + stt["photo"] + stt["escape"]
     line = {"metric": "mesh primary rays/s (CAD surface model, BVH ray casting)", "value": rays / (ms / 1e3),
             "unit": "rays/s", "higher_is_better": True, "dtype": "f32",
             "config": {"workload": f"cylinder-rod surfaces, {len(mesh['triangles'])} triangles, 512^2 x 0.25 mm, "
                                    f"{n_ang} angles, 111-bin spectrum", "steps": args.steps},
-            "ms_per_step": ms, "ms_per_projection": ms / n_ang}
+            "ms_per_step": ms, "ms_per_projection": ms / n_ang,
+            "scatter": {"photons_per_projection": N, "ms_per_projection": ms_sc,
+                        "histories_per_s": N / (ms_sc / 1e3),
+                        "flight_and_detector_rays_per_s": ray_casts / (ms_sc / 1e3),
+                        "surface_crossings_per_history": (stt["flight_steps"] + stt["nee_steps"]) / N,
+                        "n_split": 10}}
     print(json.dumps(line), flush=True)
 
 

@@ -119,3 +119,20 @@ def cylinder_rod_mesh(n_seg=96):
     cyl = cylinder_mesh(25.0, 60.0, n_seg)
     rod = cylinder_mesh(5.0, 60.0, max(16, n_seg // 3), center=(10.0, 0.0, 0.0))
     return assemble([(cyl[0], cyl[1], MAT_WATER, 1.0, -1), (rod[0], rod[1], MAT_AL, 2.7, 0)])
+
+
+# Nested boxes whose faces lie on the planes of a 2 mm voxel grid centred on the origin: a water box with an
+# aluminium box inside it that shares the water box's top face (coincident surfaces of two bodies).
+NESTED_OUTER = ((-30.0, -24.0, -20.0), (30.0, 24.0, 20.0))
+NESTED_INNER = ((-2.0, -10.0, -8.0), (14.0, 2.0, 20.0))
+NESTED_RHO_AL = 2.69921875  # 2.7 g/cm^3 rounded to binary16 (exact in binary32)
+
+
+def nested_boxes_mesh():
+    def box(b):
+        (a0, a1, a2), (b0, b1, b2) = b
+        return box_mesh(((b0 - a0) / 2, (b1 - a1) / 2, (b2 - a2) / 2), center=((a0 + b0) / 2, (a1 + b1) / 2, (a2 + b2) / 2))
+
+    vo, to = box(NESTED_OUTER)
+    vi, ti = box(NESTED_INNER)
+    return assemble([(vo, to, MAT_WATER, 1.0, -1), (vi, ti, MAT_AL, NESTED_RHO_AL, 0)])

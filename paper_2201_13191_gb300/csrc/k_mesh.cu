@@ -1,20 +1,15 @@
-// Triangle-mesh (CAD) geometry: the paper's original surface model (Sec. II-A,
-// "CAD surface model using triangular elements"; Sec. III, "closed triangulated
-// surfaces").  Bodies are closed, outward-oriented triangle surfaces with a
-// material, a density and optionally a parent body whose material they replace;
-// outside every body is vacuum.
+// Triangle-mesh (CAD) geometry, host side and primary images: the paper's
+// original surface model (Sec. II-A, "CAD surface model using triangular
+// elements"; Sec. III, "closed triangulated surfaces").  The device ray
+// casting (hierarchy descent, watertight triangle test, signed chord sums,
+// exact free flights) is in mc_mesh.cuh, shared with the transport kernel.
 //
 // Host: a bounding-volume hierarchy over the triangles (median split of the
-// centroids along the longest axis, leaves of up to kLeaf triangles), children
-// stored next to each other.  Device: one thread per pixel casts the source ray
-// through the hierarchy (explicit stack) and tests leaf triangles with the
-// watertight shear-and-edge-function test; an edge function exactly zero counts
-// as inside for only one of the two triangles sharing that edge (half-open rule
-// on the edge's projected direction, normalised by the facing), so every
-// surface crossing counts once.  A body's inside length is the signed sum of its
-// crossing parameters (+ leaving, - entering), taken about the ray point
-// closest to the origin; the primary image then follows eq. (Ip) with exact
-// per-material column masses.
+// centroids along the longest axis, leaves of up to kLeaf triangles, so the
+// depth stays below log2(triangles) + 2 and a descent's stack below
+// mesh::kStack), children stored next to each other.  Device: one thread per
+// pixel casts the source ray; the primary image then follows eq. (Ip) with
+// exact per-material column masses.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,117 +17,13 @@
 #include <cstring>
 #include <vector>
 
-#include "mc_device.cuh"
+#include "mc_mesh.cuh"
 
 namespace mcx {
 namespace {
 
 constexpr int kLeaf = 4;
-constexpr int kStack = 64;
 constexpr float kPi = 3.14159265358979f;
-
-struct Shear {
-  int kx, ky, kz;
-  float Sx, Sy, Sz;
-};
-
-__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
-__device__ __forceinline__ Shear shear_of(float3 d) {
-  Shear h;
-  int kz = 0;
-  if (fabsf(d.y) > fabsf(comp(d, kz))) kz = 1;
-  if (fabsf(d.z) > fabsf(comp(d, kz))) kz = 2;
-  int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
-  if (comp(d, kz) < 0.f) {
-    const int t = kx;
-    kx = ky;
-    ky = t;
-  }
-  h.kx = kx;
-  h.ky = ky;
-  h.kz = kz;
-  h.Sx = comp(d, kx) / comp(d, kz);
-  h.Sy = comp(d, ky) / comp(d, kz);
-  h.Sz = 1.f / comp(d, kz);
-  return h;
-}
-
-__device__ __forceinline__ bool edge_incl(float ex, float ey) { return ey > 0.f || (ey == 0.f && ex < 0.f); }
-
-// Watertight test; true and *t (ray parameter from org) on a hit.
-__device__ __forceinline__ bool ray_tri(float3 org, const Shear& h, float3 v0, float3 v1, float3 v2, float& t) {
-  const float3 A = sub3(v0, org), B = sub3(v1, org), C = sub3(v2, org);
-  const float Az = comp(A, h.kz), Bz = comp(B, h.kz), Cz = comp(C, h.kz);
-  const float Ax = comp(A, h.kx) - h.Sx * Az, Ay = comp(A, h.ky) - h.Sy * Az;
-  const float Bx = comp(B, h.kx) - h.Sx * Bz, By = comp(B, h.ky) - h.Sy * Bz;
-  const float Cx = comp(C, h.kx) - h.Sx * Cz, Cy = comp(C, h.ky) - h.Sy * Cz;
-  const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
-  const float det = U + V + W;
-  if (det == 0.f) return false;
-  const float sg = det > 0.f ? 1.f : -1.f;
-  if (!(sg * U > 0.f || (U == 0.f && edge_incl(sg * (Cx - Bx), sg * (Cy - By))))) return false;
-  if (!(sg * V > 0.f || (V == 0.f && edge_incl(sg * (Ax - Cx), sg * (Ay - Cy))))) return false;
-  if (!(sg * W > 0.f || (W == 0.f && edge_incl(sg * (Bx - Ax), sg * (By - Ay))))) return false;
-  t = h.Sz * (U * Az + V * Bz + W * Cz) / det;
-  return true;
-}
-
-// Slab test of the ray against a box over (t_lo, t_hi).
-__device__ __forceinline__ bool hit_box(float3 org, float3 inv, float4 lo, float4 hi, float t_lo, float t_hi) {
-  float ta = (lo.x - org.x) * inv.x, tb = (hi.x - org.x) * inv.x;
-  float t0 = fminf(ta, tb), t1 = fmaxf(ta, tb);
-  ta = (lo.y - org.y) * inv.y;
-  tb = (hi.y - org.y) * inv.y;
-  t0 = fmaxf(t0, fminf(ta, tb));
-  t1 = fminf(t1, fmaxf(ta, tb));
-  ta = (lo.z - org.z) * inv.z;
-  tb = (hi.z - org.z) * inv.z;
-  t0 = fmaxf(t0, fminf(ta, tb));
-  t1 = fminf(t1, fmaxf(ta, tb));
-  // padded by a relative epsilon so that a hit exactly on a face of the box is not lost
-  const float pad = 1e-5f * fmaxf(fabsf(t0), fabsf(t1)) + 1e-6f;
-  return t0 - pad <= fminf(t1, t_hi) + pad && t1 + pad >= t_lo;
-}
-
-// Per-material column masses rho L (g/cm^3 x mm) along x + t w, t in (0, t1).
-__device__ __forceinline__ void mesh_rhoL(const MeshView& M, float3 x, float3 w, float t1, float* rl) {
-  const float t0 = -dot3(x, w);
-  const float3 org = make_float3(fmaf(t0, w.x, x.x), fmaf(t0, w.y, x.y), fmaf(t0, w.z, x.z));
-  const float lo_t = -t0, hi_t = t1 - t0;
-  const Shear h = shear_of(w);
-  const float3 inv = make_float3(1.f / w.x, 1.f / w.y, 1.f / w.z);
-  int stack[kStack];
-  int sp = 0;
-  stack[sp++] = 0;
-  while (sp > 0) {
-    const int ni = stack[--sp];
-    const float4 lo = __ldg(M.nodes + 2 * ni), hi = __ldg(M.nodes + 2 * ni + 1);
-    if (!hit_box(org, inv, lo, hi, lo_t, hi_t)) continue;
-    const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
-    if (count == 0) {
-      if (sp + 2 <= kStack) {
-        stack[sp++] = first;
-        stack[sp++] = first + 1;
-      }
-      continue;
-    }
-    for (int k = first; k < first + count; ++k) {
-      const float4 a = __ldg(M.tris + 3 * k), b = __ldg(M.tris + 3 * k + 1), c = __ldg(M.tris + 3 * k + 2);
-      const float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
-      float t;
-      if (!ray_tri(org, h, v0, v1, v2, t)) continue;
-      if (!(t > lo_t && t < hi_t)) continue;
-      const float3 e1 = sub3(v1, v0), e2 = sub3(v2, v0);
-      const float3 n = make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
-      const float st = dot3(n, w) > 0.f ? t : -t;
-      const int body = __float_as_int(a.w);
-      const int4 bd = __ldg(M.bodies + body);  // material, parent, parent material, density bits
-      rl[bd.x] += __int_as_float(bd.w) * st;
-      if (bd.y >= 0) rl[bd.z] -= __ldg(M.body_rho + bd.y) * st;
-    }
-  }
-}
 
 __global__ void __launch_bounds__(256) k_primary_mesh(const PrimaryParams P, const MeshView M) {
   extern __shared__ float s_mub[];  // [n_bins][n_mat]: 0.1 * mu/rho at each bin energy
@@ -161,7 +52,7 @@ __global__ void __launch_bounds__(256) k_primary_mesh(const PrimaryParams P, con
   float rl[kMaxMat];
 #pragma unroll
   for (int m = 0; m < kMaxMat; ++m) rl[m] = 0.f;
-  mesh_rhoL(M, ps.s, w, d, rl);
+  mesh::mesh_rhoL(M, ps.s, w, d, rl, true);
   float sum = 0.f;
   for (int n = 0; n < nb; ++n) {
     const float S = __ldg(P.spec.sn + n);

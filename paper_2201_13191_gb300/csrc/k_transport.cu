@@ -1,5 +1,6 @@
 // Persistent photon-transport kernel: source sampling over the binned spectrum,
-// fixed-step free flight through the uint8/FP16 voxel volume, interaction
+// fixed-step free flight through the uint8/FP16 voxel volume (or exact flights
+// through triangle-mesh bodies, the CAD model of Sec. II-A), interaction
 // sampling (photoelectric, Compton by Kahn's method, Rayleigh by form-factor
 // inversion plus Thomson rejection) and point-detector scoring split into
 // n_split pseudo-particles aimed at random pixels (arXiv 2201.13191 Sec. II-A,
@@ -14,6 +15,7 @@
 #include <stdint.h>
 
 #include "mc_device.cuh"
+#include "mc_mesh.cuh"
 
 namespace mcx {
 
@@ -184,6 +186,32 @@ __device__ __forceinline__ float2 march_tau2(const VolumeView& V, float3 x, floa
   }
   nsteps += (unsigned long long)n;
   return make_float2(acc_a * h, acc_b * h);
+}
+
+// Optical depths through the mesh bodies from x to x + t1 w (exact chords):
+// one descent gives the column masses, then one sum per energy.
+__device__ __forceinline__ float mesh_tau(const MeshView& M, int nm, float3 x, float3 w, float t1, const float* smu,
+                                          int stride, unsigned long long& nsteps) {
+  float rl[kMaxMat];
+#pragma unroll
+  for (int m = 0; m < kMaxMat; ++m) rl[m] = 0.f;
+  nsteps += (unsigned long long)mesh::mesh_rhoL(M, x, w, t1, rl, false);
+  float tau = 0.f;
+  for (int m = 0; m < nm; ++m) tau = fmaf(smu[m * stride], rl[m], tau);
+  return tau;
+}
+__device__ __forceinline__ float2 mesh_tau2(const MeshView& M, float3 x, float3 w, float t1, const SmemTables& T,
+                                            int ia, float fa, int ib, float fb, unsigned long long& nsteps) {
+  float rl[kMaxMat];
+#pragma unroll
+  for (int m = 0; m < kMaxMat; ++m) rl[m] = 0.f;
+  nsteps += (unsigned long long)mesh::mesh_rhoL(M, x, w, t1, rl, false);
+  float a = 0.f, b = 0.f;
+  for (int m = 0; m < T.n_mat; ++m) {
+    a = fmaf(0.1f * T.at(TAB_TOT, m, ia, fa), rl[m], a);
+    b = fmaf(0.1f * T.at(TAB_TOT, m, ib, fb), rl[m], b);
+  }
+  return make_float2(a, b);
 }
 
 // Kahn's rejection method for the Klein-Nishina distribution; returns
@@ -450,7 +478,9 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
       xc *= sc;
       xr *= sc;
     }
-    const float2 tp = march_tau2<LAYOUT>(V, x, dir, dd2 * idd, P.step, T, i1, f1, i0, f0, C.nee_steps);
+    float2 tp;
+    if constexpr (LAYOUT == GEO_MESH) tp = mesh_tau2(P.mesh, x, dir, dd2 * idd, T, i1, f1, i0, f0, C.nee_steps);
+    else tp = march_tau2<LAYOUT>(V, x, dir, dd2 * idd, P.step, T, i1, f1, i0, f0, C.nee_steps);
     tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix,
                        xc * __expf(-tp.x) + xr * __expf(-tp.y));
     return;
@@ -491,7 +521,9 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
     x0 = P.rr_threshold;
   }
   fill_mu(T, ei, ef, my_mu, stride);
-  const float tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
+  float tp;
+  if constexpr (LAYOUT == GEO_MESH) tp = mesh_tau(P.mesh, T.n_mat, x, dir, dd2 * idd, my_mu, stride, C.nee_steps);
+  else tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
   tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix, x0 * __expf(-tp));
 }
 
@@ -624,7 +656,12 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
       bool hit = false;
       float tint = 0.f;
       int mint = 0;
-      if (clip_box(V, x, w, 0.f, __int_as_float(0x7f800000), ta, tb)) {
+      if constexpr (LAYOUT == GEO_MESH) {
+        fill_mu(T, E, my_mu, B);
+        hit = mesh::mesh_flight(P.mesh, x, w, tau_star, my_mu, B, tint, mint, C.flight_steps);
+        (void)ta;
+        (void)tb;
+      } else if (clip_box(V, x, w, 0.f, __int_as_float(0x7f800000), ta, tb)) {
         fill_mu(T, E, my_mu, B);
         const float L = tb - ta;
         const int n = step_count(L, P.step);
@@ -842,10 +879,11 @@ cudaError_t launch_one(const TransportParams& p, int grid, int block, int smem, 
 }
 }  // namespace
 
-cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_transport<VOX_LIN, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh) {
+  auto* k = mesh ? k_transport<GEO_MESH, false, false, false> : k_transport<VOX_LIN, false, false, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport<VOX_LIN, false, false, false>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
@@ -853,7 +891,10 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, cuda
   const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, simg);
   const bool combine = p.tally_mode != TALLY_GLOBAL;
   const bool ev = p.nee_mode == 1;
-  const int variant = (p.vol.layout == VOX_BRICK ? 8 : 0) | (combine ? 4 : 0) | (ev ? 2 : 0) | (p.doppler ? 1 : 0);
+  // the mesh geometry takes the global tally (the modes give the same image)
+  const int variant = p.geometry == GEO_MESH
+                          ? 16 | (ev ? 2 : 0) | (p.doppler ? 1 : 0)
+                          : (p.vol.layout == VOX_BRICK ? 8 : 0) | (combine ? 4 : 0) | (ev ? 2 : 0) | (p.doppler ? 1 : 0);
   switch (variant) {
 #define MC_LAUNCH(V, L, C, E, D) \
   case V:                        \
@@ -874,6 +915,10 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, cuda
     MC_LAUNCH(13, VOX_BRICK, true, false, true)
     MC_LAUNCH(14, VOX_BRICK, true, true, false)
     MC_LAUNCH(15, VOX_BRICK, true, true, true)
+    MC_LAUNCH(16, GEO_MESH, false, false, false)
+    MC_LAUNCH(17, GEO_MESH, false, false, true)
+    MC_LAUNCH(18, GEO_MESH, false, true, false)
+    MC_LAUNCH(19, GEO_MESH, false, true, true)
 #undef MC_LAUNCH
   }
   return cudaErrorInvalidValue;

@@ -46,6 +46,7 @@ struct mc_ctx {
   float* d_mesh_rho = nullptr;
   int mesh_nodes = 0, mesh_tris = 0, mesh_bodies = 0;
   double mesh_rmax = 0;  // largest distance of a vertex from the rotation axis
+  float mesh_half[3] = {0.f, 0.f, 0.f};  // half extents of a box about the origin holding every vertex
   // volume
   bool have_volume = false;
   uint32_t* d_vox = nullptr;  // packed voxel words (material | FP16 density)
@@ -263,13 +264,15 @@ GeomView geom_view(const mc_ctx* c) {
 //   seed u64 | prefix u64[n+1] | energy f32[n] | wbin f32[n] | sn f32[n]
 size_t spectrum_block_bytes(int n) { return 8 + (size_t)(n + 1) * 8 + (size_t)n * 16; }
 
-int fill_spectrum(mc_ctx* ctx, uint64_t N, uint64_t seed, unsigned char* host) {
+int fill_spectrum(mc_ctx* ctx, uint64_t N, uint64_t seed, unsigned char* host, bool histories = true) {
   const int n = (int)ctx->S.size();
   std::vector<uint64_t> M(n, 0);
   std::vector<int> elig(n, 0);
   std::vector<double> fr(n, 0.0);
   uint64_t sum = 0;
-  for (int i = 0; i < n; ++i) {
+  // a primary-only call runs no histories: no photon counts, every count zero
+  if (!histories) N = 0;
+  for (int i = 0; i < n && histories; ++i) {
     const double x = (double)N * ctx->S[i];
     const double fl = std::floor(x);
     if (ctx->S[i] <= 0) M[i] = 0;
@@ -363,8 +366,6 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
                  float step, uint64_t seed, float* primary_out, float* scatter_out, float* var_out, void* stream) {
   int rc = check_ready(ctx);
   if (rc) return rc;
-  if (ctx->mesh_mode && scatter_out)
-    return fail(ctx, MC_ERR_STATE, "scatter on the triangle-mesh geometry is not available: primary images only");
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   (void)cudaGetLastError();  // a failed call elsewhere must not be blamed on this one
@@ -412,10 +413,8 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     ctx->angles_cap = n_angles;
   }
   if (scatter_out) CK(ensure(ctx->d_tally, ctx->tally_cap, img * nb_img), "tally allocation");
-  // the previous call synchronised its stream, so the pinned buffer is free; a
-  // primary-only call runs no histories, so any photon count serves (the
-  // stratification is then taken at 2^62 photons, which every bin reaches)
-  rc = fill_spectrum(ctx, scatter_out ? N : (1ull << 62), seed, ctx->h_pin);
+  // the previous call synchronised its stream, so the pinned buffer is free
+  rc = fill_spectrum(ctx, N, seed, ctx->h_pin, scatter_out != nullptr);
   if (rc) return rc;
   std::memcpy(ctx->h_pin + ang_off, angles, (size_t)n_angles * 4);
   const SpectrumView sv = spectrum_view(ctx);
@@ -438,7 +437,17 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
   }
   if (scatter_out) {
     tp.tab = table_view(ctx);
-    tp.vol = volume_view(ctx);
+    if (ctx->mesh_mode) {
+      // the box only orders the point-detector jobs by their chord toward the panel
+      tp.vol.hx = ctx->mesh_half[0];
+      tp.vol.hy = ctx->mesh_half[1];
+      tp.vol.hz = ctx->mesh_half[2];
+      tp.geometry = GEO_MESH;
+      tp.mesh = mesh_view(ctx);
+    } else {
+      tp.vol = volume_view(ctx);
+      tp.geometry = tp.vol.layout;
+    }
     tp.geo = geom_view(ctx);
     tp.spec = sv;
     tp.angles = ctx->d_angles;
@@ -472,7 +481,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, tp.tally_mode == TALLY_SHARED ? (int)tally_pixels : 0);
     int per_sm = ctx->opt.blocks_per_sm;
     if (per_sm == 0) {
-      CK(transport_occupancy(block, smem, &per_sm), "occupancy query");
+      CK(transport_occupancy(block, smem, &per_sm, ctx->mesh_mode), "occupancy query");
       per_sm = std::max(1, per_sm);
     }
     const unsigned long long work = (unsigned long long)n_angles * h_count;
@@ -839,11 +848,13 @@ int mc_load_mesh(mc_ctx* ctx, const float* vertices, int n_vertices, const int* 
         !std::isfinite(body_density[b]) || body_parent[b] < -1 || body_parent[b] >= b)
       return fail(ctx, MC_ERR_INVALID_ARG, "bad body (material, density >= 0, parent -1 or an earlier body)");
   double rmax = 0;
+  float half[3] = {0.f, 0.f, 0.f};
   for (int i = 0; i < n_vertices; ++i) {
     const float* p = vertices + 3 * i;
     if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]))
       return fail(ctx, MC_ERR_INVALID_ARG, "non-finite vertex");
     rmax = std::max(rmax, std::sqrt((double)p[0] * p[0] + (double)p[1] * p[1]));
+    for (int a = 0; a < 3; ++a) half[a] = std::max(half[a], std::fabs(p[a]));
   }
   for (int k = 0; k < n_triangles; ++k) {
     if (tri_body[k] < 0 || tri_body[k] >= n_bodies) return fail(ctx, MC_ERR_INVALID_ARG, "triangle body out of range");
@@ -884,6 +895,7 @@ int mc_load_mesh(mc_ctx* ctx, const float* vertices, int n_vertices, const int* 
   ctx->mesh_tris = n_triangles;
   ctx->mesh_bodies = n_bodies;
   ctx->mesh_rmax = rmax;
+  for (int a = 0; a < 3; ++a) ctx->mesh_half[a] = half[a];
   ctx->have_mesh = ctx->mesh_mode = true;
   return MC_OK;
 }
@@ -959,6 +971,7 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   if (!ctx) return MC_ERR_INVALID_ARG;
   int rc = check_ready(ctx);
   if (rc) return rc;
+  if (ctx->mesh_mode) return fail(ctx, MC_ERR_STATE, "the autotuner tunes the voxel march: load a volume");
   if (!out || !angles || n_angles < 1 || probe < 1 || !(step_min > 0.f) || !(step_max >= step_min) || !(step_tol > 0.f))
     return fail(ctx, MC_ERR_INVALID_ARG, "bad autotune arguments");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -1540,6 +1553,7 @@ namespace mcx {
 int static_check(mc_ctx* ctx, int* device, int* nu, int* nv) {
   const int rc = check_ready(ctx);
   if (rc) return rc;
+  if (ctx->mesh_mode) return fail(ctx, MC_ERR_STATE, "the static-scratch entry point serves the voxel volume only");
   *device = ctx->device;
   *nu = ctx->nu;
   *nv = ctx->nv;

@@ -45,6 +45,9 @@ struct TableView {
 // bricks), Morton order inside a brick, so each 32-byte sector holds a 2x2x2
 // cube and each 128-byte line a 4x4x2 slab whatever the ray direction.
 enum VoxLayout { VOX_LIN = 0, VOX_BRICK = 1 };
+// Transport geometry selector beside the two voxel layouts: closed triangle-
+// mesh bodies (MeshView below) with exact flights instead of the march.
+constexpr int GEO_MESH = 2;
 
 // The packed volume carries a one-voxel border that repeats the edge voxels
 // (padded dims px = nx + 2, ...), so a midpoint that rounding puts a hair
@@ -78,6 +81,17 @@ struct SpectrumView {
   int n_bins;
 };
 
+// Triangle-mesh geometry (k_mesh.cu): BVH nodes as float4 pairs (lo.xyz + first,
+// hi.xyz + count; count 0 = inner node with children first, first + 1),
+// triangles as three float4 (xyz; the first's w carries the body id), bodies as
+// int4 (material, parent or -1, parent material, density bits).
+struct MeshView {
+  const float4* nodes;
+  const float4* tris;
+  const int4* bodies;
+  const float* body_rho;
+  int n_nodes, n_tris, n_bodies;
+};
 struct TransportParams {
   TableView tab;
   VolumeView vol;
@@ -100,6 +114,10 @@ struct TransportParams {
   // when set, the Philox key is read from device memory at kernel start (a
   // captured graph then serves every seed); otherwise `seed` is used
   const unsigned long long* seed_dev = nullptr;
+  // triangle-mesh geometry (geometry == GEO_MESH); `vol` then carries only the
+  // half extents of a box around the bodies (hx, hy, hz)
+  int geometry = 0;  // VOX_LIN / VOX_BRICK from vol.layout, or GEO_MESH
+  MeshView mesh = {};
 };
 
 // How pseudo-particle scores reach the FP64 image (eq. Is):
@@ -125,21 +143,10 @@ struct PrimaryParams {
 // launch wrappers (return cudaError_t of the launch)
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
 int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels = 0);
-cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm);
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh = false);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
 
-// Triangle-mesh geometry (k_mesh.cu): BVH nodes as float4 pairs (lo.xyz + first,
-// hi.xyz + count; count 0 = inner node with children first, first + 1),
-// triangles as three float4 (xyz; the first's w carries the body id), bodies as
-// int4 (material, parent or -1, parent material, density bits).
-struct MeshView {
-  const float4* nodes;
-  const float4* tris;
-  const int4* bodies;
-  const float* body_rho;
-  int n_nodes, n_tris, n_bodies;
-};
 void build_mesh_bvh(const float* v, const int* tris, const int* tri_body, int nt, std::vector<float4>& nodes,
                     std::vector<float4>& out_tris);
 cudaError_t launch_primary_mesh(const PrimaryParams& p, const MeshView& m, cudaStream_t s);

@@ -18,25 +18,16 @@ import numpy as np
 import pytest
 
 from mc_inputs import mono_spectrum
-from mc_inputs.meshes import assemble, box_mesh
+from mc_inputs.meshes import NESTED_INNER, NESTED_OUTER, NESTED_RHO_AL, assemble, box_mesh, nested_boxes_mesh
 from mc_inputs.phantoms import fp16_bits
 from mc_inputs.tables import MAT_AL, MAT_WATER
 
+assert NESTED_RHO_AL == float(np.float16(2.7))
+
 E_KEV = 60.0
-RHO_AL = float(np.float16(2.7))  # exactly representable in binary16 and binary32
-
-OUTER = ((-30.0, -24.0, -20.0), (30.0, 24.0, 20.0))  # water
-INNER = ((-2.0, -10.0, -8.0), (14.0, 2.0, 20.0))     # aluminium, top face on the outer top face
-
-
-def _nested_mesh():
-    (lo, hi), (li, hi2) = OUTER, INNER
-    half_o = tuple((b - a) / 2 for a, b in zip(lo, hi))
-    half_i = tuple((b - a) / 2 for a, b in zip(li, hi2))
-    ctr_i = tuple((a + b) / 2 for a, b in zip(li, hi2))
-    vo, to = box_mesh(half_o)
-    vi, ti = box_mesh(half_i, center=ctr_i)
-    return assemble([(vo, to, MAT_WATER, 1.0, -1), (vi, ti, MAT_AL, RHO_AL, 0)])
+RHO_AL = NESTED_RHO_AL
+OUTER, INNER = NESTED_OUTER, NESTED_INNER  # water; aluminium, top face on the outer top face
+_nested_mesh = nested_boxes_mesh
 
 
 def _nested_volume(d=2.0):
