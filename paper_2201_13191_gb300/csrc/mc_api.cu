@@ -863,7 +863,8 @@ int mc_load_mesh(mc_ctx* ctx, const float* vertices, int n_vertices, const int* 
         return fail(ctx, MC_ERR_INVALID_ARG, "triangle vertex out of range");
   }
   std::vector<float4> nodes, tris;
-  build_mesh_bvh(vertices, triangles, tri_body, n_triangles, nodes, tris);
+  const int depth = build_mesh_bvh(vertices, triangles, tri_body, n_triangles, nodes, tris);
+  if (depth >= 63) return fail(ctx, MC_ERR_INTERNAL, "bounding-volume hierarchy deeper than the device stack");
   std::vector<int4> bodies(n_bodies);
   std::vector<float> rho(n_bodies);
   for (int b = 0; b < n_bodies; ++b) {

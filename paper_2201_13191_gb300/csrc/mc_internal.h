@@ -147,8 +147,9 @@ cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool me
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
 
-void build_mesh_bvh(const float* v, const int* tris, const int* tri_body, int nt, std::vector<float4>& nodes,
-                    std::vector<float4>& out_tris);
+// Returns the depth of the deepest leaf (the device descent needs depth < 64).
+int build_mesh_bvh(const float* v, const int* tris, const int* tri_body, int nt, std::vector<float4>& nodes,
+                   std::vector<float4>& out_tris);
 cudaError_t launch_primary_mesh(const PrimaryParams& p, const MeshView& m, cudaStream_t s);
 // Checks a device-resident volume (ids < n_mat, finite non-negative binary16
 // densities); *bad_host = 1 if any voxel fails.  Synchronises s.

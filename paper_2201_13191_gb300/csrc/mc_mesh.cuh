@@ -24,7 +24,7 @@
 namespace mcx {
 namespace mesh {
 
-constexpr int kStack = 64;  // median-split hierarchy: depth <= log2(triangles) + 1
+constexpr int kStack = 64;  // the host builder keeps the depth (stack entries - 1) below 63
 constexpr int kWin = 8;     // crossings held per window of the free flight
 
 struct Shear {
@@ -92,33 +92,46 @@ __device__ __forceinline__ bool hit_box(float3 org, float3 inv, float4 lo, float
 }
 
 // Calls f(k, t, v0, v1, v2) for every leaf triangle k the ray org + t w crosses
-// with t_lo < t < t_hi.
+// with t_lo < t < t_hi.  An inner node tests both children's boxes and
+// descends into a hit child directly, stacking the other only when both are
+// hit, so the (local-memory) stack sees one entry per two-way branch.
 template <class F>
 __device__ __forceinline__ void visit(const MeshView& M, float3 org, float3 w, float t_lo, float t_hi, F&& f) {
   const Shear h = shear_of(w);
   const float3 inv = make_float3(1.f / w.x, 1.f / w.y, 1.f / w.z);
   int stack[kStack];
   int sp = 0;
-  stack[sp++] = 0;
-  while (sp > 0) {
-    const int ni = stack[--sp];
+  int ni = 0;
+  {
+    const float4 lo = __ldg(M.nodes), hi = __ldg(M.nodes + 1);
+    if (!hit_box(org, inv, lo, hi, t_lo, t_hi)) return;
+  }
+  for (;;) {
     const float4 lo = __ldg(M.nodes + 2 * ni), hi = __ldg(M.nodes + 2 * ni + 1);
-    if (!hit_box(org, inv, lo, hi, t_lo, t_hi)) continue;
     const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
     if (count == 0) {
-      // the host builder bounds the depth by kStack - 1, so both children fit
-      stack[sp++] = first;
-      stack[sp++] = first + 1;
-      continue;
+      const float4 al = __ldg(M.nodes + 2 * first), ah = __ldg(M.nodes + 2 * first + 1);
+      const float4 bl = __ldg(M.nodes + 2 * first + 2), bh = __ldg(M.nodes + 2 * first + 3);
+      const bool ha = hit_box(org, inv, al, ah, t_lo, t_hi), hb = hit_box(org, inv, bl, bh, t_lo, t_hi);
+      if (ha || hb) {
+        // the host builder bounds the depth by kStack - 1, so the stack cannot overflow
+        if (ha && hb) stack[sp++] = first + 1;
+        ni = ha ? first : first + 1;
+        continue;
+      }
+    } else {
+      for (int k = first; k < first + count; ++k) {
+        const float4 a = __ldg(M.tris + 3 * k), b = __ldg(M.tris + 3 * k + 1), c = __ldg(M.tris + 3 * k + 2);
+        const float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z),
+                     v2 = make_float3(c.x, c.y, c.z);
+        float t;
+        if (!ray_tri(org, h, v0, v1, v2, t)) continue;
+        if (!(t > t_lo && t < t_hi)) continue;
+        f(k, t, v0, v1, v2);
+      }
     }
-    for (int k = first; k < first + count; ++k) {
-      const float4 a = __ldg(M.tris + 3 * k), b = __ldg(M.tris + 3 * k + 1), c = __ldg(M.tris + 3 * k + 2);
-      const float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
-      float t;
-      if (!ray_tri(org, h, v0, v1, v2, t)) continue;
-      if (!(t > t_lo && t < t_hi)) continue;
-      f(k, t, v0, v1, v2);
-    }
+    if (sp == 0) break;
+    ni = stack[--sp];
   }
 }
 
