@@ -94,7 +94,10 @@ __device__ __forceinline__ bool hit_box(float3 org, float3 inv, float4 lo, float
 // Calls f(k, t, v0, v1, v2) for every leaf triangle k the ray org + t w crosses
 // with t_lo < t < t_hi.  An inner node tests both children's boxes and
 // descends into a hit child directly, stacking the other only when both are
-// hit, so the (local-memory) stack sees one entry per two-way branch.
+// hit, so the (local-memory) stack sees one entry per two-way branch.  The
+// descent to the next leaf and the leaf's triangle tests are separate loops
+// ("while-while"), so the lanes of a warp that reach leaves at different
+// depths test their triangles together.
 template <class F>
 __device__ __forceinline__ void visit(const MeshView& M, float3 org, float3 w, float t_lo, float t_hi, F&& f) {
   const Shear h = shear_of(w);
@@ -107,9 +110,14 @@ __device__ __forceinline__ void visit(const MeshView& M, float3 org, float3 w, f
     if (!hit_box(org, inv, lo, hi, t_lo, t_hi)) return;
   }
   for (;;) {
-    const float4 lo = __ldg(M.nodes + 2 * ni), hi = __ldg(M.nodes + 2 * ni + 1);
-    const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
-    if (count == 0) {
+    // descend until ni is a leaf (or nothing is left)
+    int first, count;
+    bool done = false;
+    for (;;) {
+      const float4 lo = __ldg(M.nodes + 2 * ni), hi = __ldg(M.nodes + 2 * ni + 1);
+      first = __float_as_int(lo.w);
+      count = __float_as_int(hi.w);
+      if (count != 0) break;
       const float4 al = __ldg(M.nodes + 2 * first), ah = __ldg(M.nodes + 2 * first + 1);
       const float4 bl = __ldg(M.nodes + 2 * first + 2), bh = __ldg(M.nodes + 2 * first + 3);
       const bool ha = hit_box(org, inv, al, ah, t_lo, t_hi), hb = hit_box(org, inv, bl, bh, t_lo, t_hi);
@@ -117,18 +125,21 @@ __device__ __forceinline__ void visit(const MeshView& M, float3 org, float3 w, f
         // the host builder bounds the depth by kStack - 1, so the stack cannot overflow
         if (ha && hb) stack[sp++] = first + 1;
         ni = ha ? first : first + 1;
-        continue;
+      } else if (sp > 0) {
+        ni = stack[--sp];
+      } else {
+        done = true;
+        break;
       }
-    } else {
-      for (int k = first; k < first + count; ++k) {
-        const float4 a = __ldg(M.tris + 3 * k), b = __ldg(M.tris + 3 * k + 1), c = __ldg(M.tris + 3 * k + 2);
-        const float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z),
-                     v2 = make_float3(c.x, c.y, c.z);
-        float t;
-        if (!ray_tri(org, h, v0, v1, v2, t)) continue;
-        if (!(t > t_lo && t < t_hi)) continue;
-        f(k, t, v0, v1, v2);
-      }
+    }
+    if (done) break;
+    for (int k = first; k < first + count; ++k) {
+      const float4 a = __ldg(M.tris + 3 * k), b = __ldg(M.tris + 3 * k + 1), c = __ldg(M.tris + 3 * k + 2);
+      const float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
+      float t;
+      if (!ray_tri(org, h, v0, v1, v2, t)) continue;
+      if (!(t > t_lo && t < t_hi)) continue;
+      f(k, t, v0, v1, v2);
     }
     if (sp == 0) break;
     ni = stack[--sp];
