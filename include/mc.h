@@ -337,11 +337,15 @@ int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles
  * material); up to MC_MAX_BODIES bodies.  Each body's surface must be closed.
  * The library copies the data, builds a bounding-volume hierarchy and switches
  * the context to this geometry until mc_load_volume is called again.  With a
- * mesh, mc_project computes primary images (eq. Ip) by exact ray casting:
- * watertight ray/triangle tests, a body's path length as the signed sum of its
- * crossings; scatter on meshes is not available (MC_ERR_STATE).
+ * mesh, mc_project and mc_project_histories compute primary images (eq. Ip) by
+ * exact ray casting (watertight ray/triangle tests, a body's path length as the
+ * signed sum of its crossings) and scatter images (eq. Is) from photon
+ * histories with exact free flights through the bodies and exact point-
+ * detector attenuation; step_mm is validated but unused, and the warp-combined
+ * and shared tally modes act as the global one.  mc_autotune and
+ * mc_project_scatter_static serve the voxel volume only (MC_ERR_STATE).
  * Errors: STATE (no tables), INVALID_ARG (indices, bodies, non-finite
- * vertices), CUDA/OOM. */
+ * vertices), INTERNAL (hierarchy deeper than the device stack), CUDA/OOM. */
 int mc_load_mesh(mc_ctx *ctx, const float *vertices, int n_vertices, const int *triangles, const int *tri_body,
                  int n_triangles, const int *body_material, const float *body_density, const int *body_parent,
                  int n_bodies);
