@@ -88,6 +88,7 @@ typedef struct {
   int nee_mode; /* 0: score the sampled scatter type; 1: expected value over both types */
   int doppler;  /* Doppler broadening of incoherent scatter (needs the bound tables) */
   double rr_threshold, eps_face;
+  int tile_u, tile_v; /* > 0: tile-stratified point-detector pixels (see orc_set_tiles) */
 } orc_ctx;
 
 /* ------------------------------------------------------------------ */
@@ -345,6 +346,24 @@ int orc_sample_doppler(const orc_ctx *c, int m, double E, double cos_t, uint64_t
 int orc_set_nee_mode(orc_ctx *c, int mode) {
   if (mode != 0 && mode != 1) return ORC_EINVAL;
   c->nee_mode = mode;
+  return ORC_OK;
+}
+
+/* Tile-stratified point-detector scoring: the panel is cut into tiles of
+ * tile_u x tile_v pixels (ragged at the far edges), T tiles in all; history h
+ * aims all its pseudo-particles at tile t = (h + o) mod T, at pixels drawn
+ * uniformly within it (probability 1/P_t instead of 1/P), and its scores
+ * carry the factor T.  The offset o is uniform on [0, T), one per run and
+ * angle, from the Philox block (2^32 - 1, angle, 2^32 - 1, 2^32 - 1) (above
+ * every history's blocks), so each energy bin's consecutive histories start
+ * at a uniformly random tile: a tile receives M_n / T of bin n's histories in
+ * expectation, whatever M_n, and every pixel receives in expectation what the
+ * unstratified estimator gives it.  tile_u = tile_v = 0 turns it off; one tile
+ * covering the panel reduces exactly to the unstratified estimator. */
+int orc_set_tiles(orc_ctx *c, int tile_u, int tile_v) {
+  if (tile_u < 0 || tile_v < 0 || (tile_u == 0) != (tile_v == 0)) return ORC_EINVAL;
+  c->tile_u = tile_u;
+  c->tile_v = tile_v;
   return ORC_OK;
 }
 
@@ -1141,6 +1160,18 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
   }
   pre[0] = 0;
   for (int n = 0; n < c->n_bins; ++n) pre[n + 1] = pre[n] + M[n];
+  const int tiled = c->tile_u > 0;
+  const int ntu = tiled ? (c->nu + c->tile_u - 1) / c->tile_u : 1;
+  const int ntv = tiled ? (c->nv + c->tile_v - 1) / c->tile_v : 1;
+  const uint64_t T = (uint64_t)ntu * ntv;
+  uint64_t tile_off = 0;
+  if (tiled) {
+    const uint32_t ctr[4] = {0xFFFFFFFFu, angle_index, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox(ctr, key, out);
+    tile_off = ((uint64_t)out[0] * T) >> 32;
+  }
   pose_t P;
   pose(c, beta, &P);
   const size_t npix = (size_t)c->nu * c->nv;
@@ -1162,6 +1193,18 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
     double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
     double w[3] = {D[0] / d, D[1] / d, D[2] / d};
     double W = c->S[bin] / (double)M[bin] * A_det * (c->sdd / d) / (4.0 * PI * d * d);
+    /* the pixels this history's pseudo-particles aim at: the whole panel, or its tile */
+    int u0 = 0, v0 = 0, wt = c->nu, ht = c->nv;
+    double tile_w = 1.0;
+    if (tiled) {
+      const uint64_t t = (h % T + tile_off) % T;
+      u0 = (int)(t % ntu) * c->tile_u;
+      v0 = (int)(t / ntu) * c->tile_v;
+      wt = c->nu - u0 < c->tile_u ? c->nu - u0 : c->tile_u;
+      ht = c->nv - v0 < c->tile_v ? c->nv - v0 : c->tile_v;
+      tile_w = (double)T;
+    }
+    const uint64_t Pt = (uint64_t)wt * ht;
     double x[3] = {P.s[0], P.s[1], P.s[2]};
     double e_src = E * W, e_dep = 0, e_esc = 0;
     int order = 0;
@@ -1234,8 +1277,9 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       for (int s = 0; s < c->n_split; ++s) {
         uint32_t r = rng_next(&g);
         double va = rng_u(&g), vb = rng_u(&g), vr = rng_u(&g);
-        uint64_t pix = ((uint64_t)r * (uint64_t)npix) >> 32;
-        int pi = (int)(pix % c->nu), pj = (int)(pix / c->nu);
+        uint64_t pt = ((uint64_t)r * Pt) >> 32;
+        int pi = u0 + (int)(pt % wt), pj = v0 + (int)(pt / wt);
+        uint64_t pix = (uint64_t)pj * c->nu + pi;
         double Pp[3];
         det_point(c, &P, pi + va, pj + vb, Pp);
         double DD[3] = {Pp[0] - x[0], Pp[1] - x[1], Pp[2] - x[2]};
@@ -1243,7 +1287,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         double dir[3] = {DD[0] / dd, DD[1] / dd, DD[2] / dd};
         double lam = w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2];
         double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
-        const double geo = A_px * cosg * ((double)npix / c->n_split) / (2.0 * PI * dd * dd);
+        const double geo = tile_w * A_px * cosg * ((double)Pt / c->n_split) / (2.0 * PI * dd * dd);
         double sc;
         st[ST_NEE_RAYS] += 1;
         rng_t side;
