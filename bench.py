@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
+    p.add_argument("--tally", choices=["auto", "global", "shared", "warp", "tiled"], default="auto",
+                   help="how point-detector scores reach the image (tiled: tile-stratified, --tile pixels)")
+    p.add_argument("--tile", type=int, nargs=2, default=[64, 64], metavar=("U", "V"))
     p.add_argument("--cor-detector", type=int, default=2048)
     p.add_argument("--cor-pixel", type=float, default=0.1)
     p.add_argument("--cor-proj", type=int, default=1024)
@@ -340,7 +343,9 @@ def run_ours(args):
     n_ang = max(1, args.angles)
     angles = (2.0 * np.pi * np.arange(n_ang) / n_ang).astype(np.float32)
     seed = wl["seed"] + 1000 * rank
-    ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph), nee_mode=args.nee_mode)
+    tally = {"auto": 0, "global": 1, "shared": 2, "warp": 3, "tiled": 4}[args.tally]
+    ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph), nee_mode=args.nee_mode,
+                      tally_mode=tally, tile_u=args.tile[0], tile_v=args.tile[1])
     ctx.load_tables(tp)
     ctx.setup(wl)
     if args.detector == "panel":
@@ -467,7 +472,8 @@ def run_ours(args):
                        "step_mm": wl["step_mm"], "n_split": 10, "spectrum": f"{len(wl['weights'])} bins",
                        "l2_flush": True, "parallelism": "replicas" if world > 1 else "single",
                        "autotune": tuned, "voxel_layout": args.voxel_layout, "detector": args.detector,
-                       "nee_mode": args.nee_mode},
+                       "nee_mode": args.nee_mode,
+                       "tally": args.tally + (f" {args.tile[0]}x{args.tile[1]}" if args.tally == "tiled" else "")},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

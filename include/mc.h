@@ -58,6 +58,13 @@ typedef struct mc_ctx mc_ctx;
 #define MC_TALLY_SHARED 2 /* per-block FP32 shared-memory image (warp-combined adds), flushed into
                              FP64 at block end; needs n_batches x n_angles x nu x nv <= 12288 */
 #define MC_TALLY_WARP 3   /* lanes of a warp hitting the same pixel combine (match + shuffle) first */
+#define MC_TALLY_TILED 4  /* tile-stratified point-detector pixels: the panel is cut into tiles of
+                             tile_u x tile_v pixels (T tiles); history h aims every pseudo-particle at
+                             tile (h + o) mod T only, o uniform on [0, T) per run and angle (Philox
+                             block (2^32-1, angle, 2^32-1, 2^32-1)), at a pixel uniform in the tile, with
+                             weight T (unbiased); each block works through chunks of one (angle, tile)
+                             and tallies the tile in shared memory, flushed into FP64 per chunk; needs
+                             n_batches x tile_u x tile_v <= 12288 */
 
 typedef struct mc_options {
   int n_split;           /* pseudo-particles per scatter interaction (Sec. II-C.1), default 10 */
@@ -81,6 +88,7 @@ typedef struct mc_options {
                             same mean, less variance */
   int doppler;           /* 1: Doppler broadening of incoherent scatter (impulse approximation with the
                             orbital model of the bound tables; needs tables of version 2), 0 = off (default) */
+  int tile_u, tile_v;    /* tile size in pixels of MC_TALLY_TILED, default 64 x 64 */
 } mc_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -93,6 +93,8 @@ class Options(C.Structure):
         ("use_graph", C.c_int),
         ("nee_mode", C.c_int),
         ("doppler", C.c_int),
+        ("tile_u", C.c_int),
+        ("tile_v", C.c_int),
     ]
 
 

@@ -189,6 +189,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   if (e != cudaSuccess) return static_cuda_fail(ctx, e, "static transport");
   static_set_stats(ctx, st, 0.f);
   if (st[S_INTERNAL]) return static_fail(ctx, MC_ERR_TIMEOUT, "a block gave up waiting for its table copy");
+  if (st[S_BAD_SMEM]) return static_fail(ctx, MC_ERR_INTERNAL, "transport launched with less shared memory than its layout");
   if (st[S_LIMIT] || st[S_SAMPLER_FAIL])
     return static_fail(ctx, MC_ERR_LIMIT, "histories hit the scatter-order or sampler cap (outputs valid)");
   return MC_OK;

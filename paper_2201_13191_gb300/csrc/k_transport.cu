@@ -358,6 +358,12 @@ __device__ __forceinline__ float3 rotate(float3 w, float ct, float phi) {
   return make_float3(o.x * in, o.y * in, o.z * in);
 }
 
+__device__ __forceinline__ int transport_shared_pixels_dev(const TransportParams& p) {
+  if (p.tally_mode == TALLY_SHARED) return (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv);
+  if (p.tally_mode == TALLY_TILED) return p.n_batches * p.tile_u * p.tile_v;
+  return 0;
+}
+
 __device__ __forceinline__ uint32_t G_npix(const TransportParams& P) {
   return (uint32_t)P.geo.nu * (uint32_t)P.geo.nv;
 }
@@ -395,7 +401,7 @@ __device__ __noinline__ void tally_combine(const TransportParams& P, float* s_im
   float sum = 0.f;
   for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
   if (lane != leader) return;
-  if (P.tally_mode == TALLY_SHARED) atomicAdd(s_img + off, sum);
+  if (P.tally_mode == TALLY_SHARED || P.tally_mode == TALLY_TILED) atomicAdd(s_img + off, sum);
   else atomicAdd(P.tally + off, (double)sum);
 }
 
@@ -404,18 +410,42 @@ __device__ __forceinline__ void tally_add<true>(const TransportParams& P, float*
   tally_combine(P, s_img, off, v);
 }
 
+// Pixels a block's pseudo-particles aim at under the tile-stratified tally: the
+// current chunk's tile (origin, width, height) and the score factor T P_t / P
+// (weight T, pixel drawn among the tile's P_t instead of the panel's P).
+struct TileSel {
+  int u0, v0, wt, ht;
+  float scale;
+};
+
 template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
 __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const SmemTables& T, const Records& R,
                                                 int r, int s, float* my_mu, int stride, float nee_scale,
                                                 uint32_t npix, size_t img, Counters& C, float* s_img,
-                                                uint2 key) {
+                                                uint2 key, const TileSel& ts) {
   const VolumeView& V = P.vol;
   const GeomView& G = P.geo;
   const uint32_t hlo = R.hlo[r], hhi = R.hhi[r], a = R.ang[r];
   const uint4 blk = philox4x32_10(make_uint4(R.k0[r] + (uint32_t)s, a, hlo, hhi), key);
   const float va = Rng::u01(blk.y), vb = Rng::u01(blk.z), vr = Rng::u01(blk.w);
-  const uint32_t pix = __umulhi(blk.x, npix);
-  const uint32_t pi = pix % (uint32_t)G.nu, pj = pix / (uint32_t)G.nu;
+  const unsigned long long hh = ((unsigned long long)hhi << 32) | hlo;
+  const int bt = P.n_batches > 1 ? (int)(hh % (unsigned long long)P.n_batches) : 0;
+  uint32_t pi, pj;
+  size_t off;
+  float tscale = 1.f;
+  if (COMBINE && P.tally_mode == TALLY_TILED) {
+    const uint32_t Pt = (uint32_t)(ts.wt * ts.ht);
+    const uint32_t pt = __umulhi(blk.x, Pt);
+    pi = (uint32_t)ts.u0 + pt % (uint32_t)ts.wt;
+    pj = (uint32_t)ts.v0 + pt / (uint32_t)ts.wt;
+    off = (size_t)bt * Pt + pt;
+    tscale = ts.scale;
+  } else {
+    const uint32_t pix = __umulhi(blk.x, npix);
+    pi = pix % (uint32_t)G.nu;
+    pj = pix / (uint32_t)G.nu;
+    off = ((size_t)bt * P.n_angles + a) * img + pix;
+  }
   const float cb = R.cb[r], sb = R.sb[r];
   Pose ps;
   const float rr0 = G.sod - G.sdd;
@@ -434,8 +464,6 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   const int tm = R.tm[r];
   const int type = tm >> 8, mint = tm & 255;
   const float E = R.E[r];
-  const unsigned long long hh = ((unsigned long long)hhi << 32) | hlo;
-  const int bt = P.n_batches > 1 ? (int)(hh % (unsigned long long)P.n_batches) : 0;
   if (EV) {
     // expected value over the interaction type: (mu_incoh/mu) Compton term at
     // E' + (mu_coh/mu) Rayleigh term at E, attenuations from one shared march
@@ -467,7 +495,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
       if (df) ++C.fail;
     }
     T.locate(Ep_s, i1, f1);
-    const float gw = R.W[r] * cosg * nee_scale / dd2;
+    const float gw = R.W[r] * cosg * (nee_scale * tscale) / dd2;
     float xc = gw * (in * imu) * T.response(i1, f1, Ep_s) * pc;
     float xr = gw * (co * imu) * T.response(i0, f0, E) * pr;
     ++C.nee_rays;
@@ -481,8 +509,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
     float2 tp;
     if constexpr (LAYOUT == GEO_MESH) tp = mesh_tau2(P.mesh, x, dir, dd2 * idd, T, i1, f1, i0, f0, C.nee_steps);
     else tp = march_tau2<LAYOUT>(V, x, dir, dd2 * idd, P.step, T, i1, f1, i0, f0, C.nee_steps);
-    tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix,
-                       xc * __expf(-tp.x) + xr * __expf(-tp.y));
+    tally_add<COMBINE>(P, s_img, off, xc * __expf(-tp.x) + xr * __expf(-tp.y));
     return;
   }
   float Ep, p;
@@ -514,7 +541,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   int ei;
   float ef;
   T.locate(Ep, ei, ef);
-  float x0 = R.W[r] * T.response(ei, ef, Ep) * p * cosg * nee_scale / dd2;
+  float x0 = R.W[r] * T.response(ei, ef, Ep) * p * cosg * (nee_scale * tscale) / dd2;
   ++C.nee_rays;
   if (P.rr_threshold > 0.f && x0 < P.rr_threshold) {
     if (vr >= x0 / P.rr_threshold) return;
@@ -524,7 +551,7 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   float tp;
   if constexpr (LAYOUT == GEO_MESH) tp = mesh_tau(P.mesh, T.n_mat, x, dir, dd2 * idd, my_mu, stride, C.nee_steps);
   else tp = march_tau<LAYOUT>(V, x, dir, dd2 * idd, P.step, my_mu, stride, C.nee_steps);
-  tally_add<COMBINE>(P, s_img, ((size_t)bt * P.n_angles + a) * img + pix, x0 * __expf(-tp));
+  tally_add<COMBINE>(P, s_img, off, x0 * __expf(-tp));
 }
 
 #ifndef MC_MIN_BLOCKS
@@ -538,12 +565,60 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 #endif
 constexpr int kBuckets = 16;
 
+// Tile-stratified tally: the block's current chunk of histories, all of one
+// angle and one tile (histories h with (h + o_a) mod T = t, o_a the angle's
+// tile offset, uniform on [0, T) from the Philox block (2^32 - 1, a, 2^32 - 1,
+// 2^32 - 1)).  Local index j runs over [j, j_end); history = first + T j.
+struct TileChunk {
+  unsigned long long j, j_end, first;
+  int a, u0, v0, wt, ht, done;
+};
+
+// Thread 0 takes chunks from the global counter until a non-empty one (or none is left).
+__device__ void tile_fetch(const TransportParams& P, uint2 key, TileChunk& c) {
+  const unsigned long long T = (unsigned long long)P.n_tiles, K = P.tile_k;
+  const unsigned long long hb = P.h_begin, he = P.h_begin + P.h_count;
+  if (T == 0 || K == 0 || P.tile_chunk == 0) {
+    c.done = 1;
+    return;
+  }
+  for (;;) {
+    const unsigned long long id = atomicAdd(P.stats + S_WORK, 1ull);
+    if (id >= P.n_chunks) {
+      c.done = 1;
+      return;
+    }
+    const int a = (int)(id / (T * K));
+    const unsigned long long t = (id / K) % T, k = id % K;
+    const uint4 ob = philox4x32_10(make_uint4(0xFFFFFFFFu, (uint32_t)a, 0xFFFFFFFFu, 0xFFFFFFFFu), key);
+    const unsigned long long o = ((unsigned long long)ob.x * T) >> 32;
+    const unsigned long long res = (t + T - o) % T;  // h = res (mod T)
+    const unsigned long long first = hb + (res + T - hb % T) % T;
+    const unsigned long long cnt = first < he ? (he - first - 1) / T + 1 : 0ull;
+    const unsigned long long jb = k * P.tile_chunk;
+    const unsigned long long je = min(jb + P.tile_chunk, cnt);
+    if (jb >= je) continue;
+    c.j = jb;
+    c.j_end = je;
+    c.first = first;
+    c.a = a;
+    c.u0 = (int)(t % (unsigned long long)P.n_tu) * P.tile_u;
+    c.v0 = (int)(t / (unsigned long long)P.n_tu) * P.tile_v;
+    c.wt = min(P.tile_u, P.geo.nu - c.u0);
+    c.ht = min(P.tile_v, P.geo.nv - c.v0);
+    c.done = 0;
+    return;
+  }
+}
+
 template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
 __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_nrec, s_job;
   __shared__ int s_bucket[kBuckets + 1];
+  __shared__ TileChunk s_tc;
+  const bool tiled = COMBINE && P.tally_mode == TALLY_TILED;
   const int nm = P.tab.n_mat, ns = P.tab.n_stage;
   const int nb = P.spec.n_bins;
   const int B = blockDim.x;
@@ -565,9 +640,19 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   R.k0 = reinterpret_cast<uint32_t*>(rec + 15 * B);
   R.len = rec + 16 * B;
   int* s_ord = reinterpret_cast<int*>(rec + 17 * B);  // record order for the pseudo-particle phase
-  float* s_img = rec + 18 * B;                         // shared tally image (TALLY_SHARED)
-  const int n_simg =
-      (COMBINE && P.tally_mode == TALLY_SHARED) ? (int)((size_t)P.n_batches * P.n_angles * G_npix(P)) : 0;
+  float* s_img = rec + 18 * B;                         // shared tally image (TALLY_SHARED) or tile (TALLY_TILED)
+  // the shared image's size; the host sizes the dynamic shared memory with the same rule
+  const int n_simg = COMBINE ? transport_shared_pixels_dev(P) : 0;
+  {
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const size_t need = (size_t)P.tab.blob_bytes + (size_t)(nb + 1) * 8 + (size_t)nb * 8 + (size_t)kMaxMat * B * 4 +
+                        (size_t)18 * B * 4 + (size_t)n_simg * 4;
+    if (need > dyn) {  // uniform over the block: no thread has reached a barrier yet
+      if (threadIdx.x == 0) atomicAdd(P.stats + S_BAD_SMEM, 1ull);
+      return;
+    }
+  }
   for (int i = threadIdx.x; i < n_simg; i += B) s_img[i] = 0.f;
 
   const bool staged = stage_bulk(s_blob, P.tab.blob, P.tab.blob_bytes, &bar);
@@ -576,7 +661,10 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
     s_E[i] = P.spec.energy[i];
     s_wb[i] = P.spec.wbin[i];
   }
-  if (threadIdx.x == 0) s_nrec = 0;
+  if (threadIdx.x == 0) {
+    s_nrec = 0;
+    s_tc.done = 0;
+  }
   __syncthreads();
   if (!staged) {
     if (threadIdx.x == 0) atomicAdd(P.stats + S_INTERNAL, 1ull);
@@ -622,13 +710,31 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   const unsigned long long seed = P.seed_dev ? __ldg(P.seed_dev) : P.seed;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   g.init(0, 0, seed);
+  if (tiled) {
+    if (threadIdx.x == 0) tile_fetch(P, key, s_tc);
+    __syncthreads();
+  }
 
   for (;;) {
+    if (tiled && s_tc.done) break;
     // ---- flight phase: one free flight per live photon
-    if (!alive && next < total) {
+    bool fresh = false;
+    if (tiled) {
+      if (!alive) {
+        const unsigned long long j = atomicAdd(&s_tc.j, 1ull);
+        if (j < s_tc.j_end) {
+          a = s_tc.a;
+          h = s_tc.first + (unsigned long long)P.n_tiles * j;
+          fresh = true;
+        }
+      }
+    } else if (!alive && next < total) {
       a = (int)(next / P.h_count);
       h = P.h_begin + (next - (unsigned long long)a * P.h_count);
       next += stride;
+      fresh = true;
+    }
+    if (fresh) {
       int lo = 0, hi = nb - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -779,6 +885,14 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
     // ---- pseudo-particle phase: the block marches every queued ray together
     const int nrec = s_nrec;
     const int n_jobs = nrec * n_split;
+    TileSel ts = {0, 0, 0, 0, 1.f};
+    if (tiled) {
+      ts.u0 = s_tc.u0;
+      ts.v0 = s_tc.v0;
+      ts.wt = s_tc.wt;
+      ts.ht = s_tc.ht;
+      ts.scale = (float)P.n_tiles * (float)(s_tc.wt * s_tc.ht) / (float)npix;
+    }
 #if MC_SORT
     {
       // counting sort of the records into length buckets, longest first
@@ -806,22 +920,38 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         const int j = base + lane;
         if (j < n_jobs) {
           const int q = j / n_split;
-          pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+          pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, s_ord[q], j - q * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key, ts);
         }
       }
     }
 #else
     for (int j = threadIdx.x; j < n_jobs; j += B) {
       const int r = j / n_split;
-      pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key);
+      pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, r, j - r * n_split, my_mu, B, nee_scale, npix, img, C, s_img, key, ts);
     }
 #endif
-    const bool more = alive || next < total;
+    const bool more = alive || (tiled ? s_tc.j < s_tc.j_end : next < total);
     __syncthreads();
     if (threadIdx.x == 0) s_nrec = 0;
-    if (!__syncthreads_or(more)) break;
+    if (!__syncthreads_or(more)) {
+      if (!tiled) break;
+      // the chunk is finished: its tile goes into the FP64 image, then the next chunk
+      const int Pt = s_tc.wt * s_tc.ht;
+      for (int i = threadIdx.x; i < P.n_batches * Pt; i += B) {
+        const float v = s_img[i];
+        if (v != 0.f) {
+          const int bt = i / Pt, pt = i - bt * Pt;
+          const size_t pix = (size_t)(s_tc.v0 + pt / s_tc.wt) * G.nu + (size_t)(s_tc.u0 + pt % s_tc.wt);
+          atomicAdd(P.tally + ((size_t)bt * P.n_angles + s_tc.a) * img + pix, (double)v);
+          s_img[i] = 0.f;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) tile_fetch(P, key, s_tc);
+      __syncthreads();
+    }
   }
-  if (COMBINE && n_simg) {
+  if (COMBINE && P.tally_mode == TALLY_SHARED && n_simg) {
     __syncthreads();
     for (int i = threadIdx.x; i < n_simg; i += B)
       if (s_img[i] != 0.f) atomicAdd(P.tally + i, (double)s_img[i]);
@@ -865,6 +995,12 @@ __global__ void k_finalize(const double* __restrict__ tally, int B, size_t n, fl
 
 }  // namespace
 
+int transport_shared_pixels(const TransportParams& p) {
+  if (p.tally_mode == TALLY_SHARED) return (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv);
+  if (p.tally_mode == TALLY_TILED) return p.n_batches * p.tile_u * p.tile_v;
+  return 0;
+}
+
 int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels) {
   return t.blob_bytes + (n_bins + 1) * 8 + n_bins * 8 + kMaxMat * block * 4 + 18 * block * 4 + shared_pixels * 4;
 }
@@ -887,8 +1023,7 @@ cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool me
 }
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s) {
-  const int simg = p.tally_mode == TALLY_SHARED ? (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv) : 0;
-  const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, simg);
+  const int smem = transport_smem_bytes(p.tab, p.spec.n_bins, block, transport_shared_pixels(p));
   const bool combine = p.tally_mode != TALLY_GLOBAL;
   const bool ev = p.nee_mode == 1;
   // the mesh geometry takes the global tally (the modes give the same image)

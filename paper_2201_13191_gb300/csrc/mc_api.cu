@@ -122,7 +122,9 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
     return why = "block_size must be 0 or a multiple of 32 in [32, 256]", -1;
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return why = "blocks_per_sm must be in [0, 64]", -1;
-  if (o->tally_mode < 0 || o->tally_mode > 3) return why = "tally_mode must be 0, 1, 2 or 3", -1;
+  if (o->tally_mode < 0 || o->tally_mode > 4) return why = "tally_mode must be 0 .. 4", -1;
+  if (o->tile_u < 1 || o->tile_v < 1 || o->tile_u > 4096 || o->tile_v > 4096)
+    return why = "tile_u and tile_v must be in 1 .. 4096", -1;
   if (o->sg_order < 0 || o->sg_window < o->sg_order + 2 || o->sg_window % 2 == 0 || o->sg_window > 31)
     return why = "sg_window must be odd, >= sg_order + 2 and <= 31", -1;
   if (!(o->cubic_a < 0.f && o->cubic_a > -3.f)) return why = "cubic_a must be in (-3, 0)", -1;
@@ -471,6 +473,15 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
       if (tally_pixels > (size_t)kSharedTallyMaxPixels)
         return fail(ctx, MC_ERR_INVALID_ARG, "tally_mode SHARED needs n_batches x n_angles x nu x nv <= 12288");
       tp.tally_mode = TALLY_SHARED;
+    } else if (ctx->opt.tally_mode == MC_TALLY_TILED && !ctx->mesh_mode) {
+      const int tu = std::min(ctx->opt.tile_u, ctx->nu), tv = std::min(ctx->opt.tile_v, ctx->nv);
+      if ((size_t)nb_img * tu * tv > (size_t)kSharedTallyMaxPixels)
+        return fail(ctx, MC_ERR_INVALID_ARG, "tally_mode TILED needs n_batches x tile_u x tile_v <= 12288");
+      tp.tally_mode = TALLY_TILED;
+      tp.tile_u = tu;
+      tp.tile_v = tv;
+      tp.n_tu = (ctx->nu + tu - 1) / tu;
+      tp.n_tiles = tp.n_tu * ((ctx->nv + tv - 1) / tv);
     } else if (ctx->opt.tally_mode == MC_TALLY_WARP) {
       tp.tally_mode = TALLY_WARP;
     } else {
@@ -478,7 +489,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
       tp.tally_mode = TALLY_GLOBAL;
     }
     block = ctx->opt.block_size ? ctx->opt.block_size : 256;
-    const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, tp.tally_mode == TALLY_SHARED ? (int)tally_pixels : 0);
+    const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, transport_shared_pixels(tp));
     int per_sm = ctx->opt.blocks_per_sm;
     if (per_sm == 0) {
       CK(transport_occupancy(block, smem, &per_sm, ctx->mesh_mode), "occupancy query");
@@ -488,6 +499,17 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     const unsigned long long need = (work + block - 1) / block;
     grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(need, (unsigned long long)ctx->sm_count * per_sm));
     if (work == 0) grid = 0;
+    if (tp.tally_mode == TALLY_TILED && grid > 0) {
+      // chunks of one (angle, tile): about 8 per block for balance, at least 4 histories per thread so
+      // that the wait for a chunk's last photon stays short, at most a tile's share of the run
+      const unsigned long long per_tile = (h_count + tp.n_tiles - 1) / tp.n_tiles;
+      unsigned long long c = work / ((unsigned long long)grid * 8);
+      c = std::max<unsigned long long>(c, 4ull * block);
+      c = std::max<unsigned long long>(1, std::min(c, per_tile));
+      tp.tile_chunk = c;
+      tp.tile_k = (per_tile + c - 1) / c;
+      tp.n_chunks = (unsigned long long)n_angles * tp.n_tiles * std::max<unsigned long long>(1, tp.tile_k);
+    }
   }
 
   // ---- the enqueue sequence
@@ -556,6 +578,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
   ctx->stats[10] = ms_t;
   ctx->stats[11] = ms_p;
   if (st[S_INTERNAL]) return fail(ctx, MC_ERR_TIMEOUT, "a block gave up waiting for its table copy");
+  if (st[S_BAD_SMEM]) return fail(ctx, MC_ERR_INTERNAL, "transport launched with less shared memory than its layout");
   if (st[S_LIMIT] || st[S_SAMPLER_FAIL])
     return fail(ctx, MC_ERR_LIMIT, "histories hit the scatter-order or sampler cap (outputs valid)");
   return MC_OK;
@@ -628,6 +651,8 @@ void mc_default_options(mc_options* o) {
   o->use_graph = 0;
   o->nee_mode = 0;
   o->doppler = 0;
+  o->tile_u = 64;
+  o->tile_v = 64;
 }
 
 int mc_create(mc_ctx** out, int cuda_device, const mc_options* opt) {

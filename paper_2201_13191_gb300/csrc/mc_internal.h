@@ -19,7 +19,10 @@ enum TabKind { TAB_TOT = 0, TAB_PE = 1, TAB_IN = 2, TAB_CO = 3, TAB_ICOH = 4, TA
 // Statistic slots (uint64 counters on the device, doubles at the ABI).
 enum Stat {
   S_HIST = 0, S_FLIGHT_STEPS, S_NEE_STEPS, S_NEE_RAYS, S_PHOTO, S_COMPTON, S_RAYLEIGH, S_ESCAPE,
-  S_LIMIT, S_SAMPLER_FAIL, S_INTERNAL, S_NSTAT
+  S_LIMIT, S_SAMPLER_FAIL, S_INTERNAL,
+  S_WORK,  // chunk counter of the tile-stratified tally (blocks take work from it)
+  S_BAD_SMEM,  // blocks that found less dynamic shared memory than their layout needs (and did nothing)
+  S_NSTAT
 };
 
 // Staged table blob (device global, copied per block into shared memory):
@@ -118,6 +121,11 @@ struct TransportParams {
   // half extents of a box around the bodies (hx, hy, hz)
   int geometry = 0;  // VOX_LIN / VOX_BRICK from vol.layout, or GEO_MESH
   MeshView mesh = {};
+  // TALLY_TILED: tiles of tile_u x tile_v pixels, n_tu across, n_tiles in all;
+  // work in chunks of up to tile_chunk histories of one (angle, tile), tile_k
+  // chunks per (angle, tile), n_chunks in all, handed out by stats[S_WORK]
+  int tile_u = 0, tile_v = 0, n_tu = 0, n_tiles = 0;
+  unsigned long long tile_chunk = 0, tile_k = 0, n_chunks = 0;
 };
 
 // How pseudo-particle scores reach the FP64 image (eq. Is):
@@ -126,7 +134,12 @@ struct TransportParams {
 //                 their scores (match + shuffle), one atomic per pixel group;
 //   TALLY_SHARED  a per-block FP32 image in shared memory (warp-combined adds),
 //                 flushed into the FP64 image once at the end of the block.
-enum TallyMode { TALLY_GLOBAL = 0, TALLY_WARP = 1, TALLY_SHARED = 2 };
+//   TALLY_TILED   tile-stratified point-detector pixels: history h aims at tile
+//                 (h + o) mod T only (o uniform per run and angle, weight T); a
+//                 block works through chunks of one (angle, tile) and tallies the
+//                 tile in shared memory (warp-combined adds), flushing it into the
+//                 FP64 image after each chunk.
+enum TallyMode { TALLY_GLOBAL = 0, TALLY_WARP = 1, TALLY_SHARED = 2, TALLY_TILED = 3 };
 constexpr int kSharedTallyMaxPixels = 12288;  // 48 KB of FP32 per block
 
 struct PrimaryParams {
@@ -143,6 +156,8 @@ struct PrimaryParams {
 // launch wrappers (return cudaError_t of the launch)
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, cudaStream_t s);
 int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels = 0);
+// FP32 pixels of the shared tally image the kernel keeps for these parameters
+int transport_shared_pixels(const TransportParams& p);
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh = false);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
