@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--correct-eval", action="store_true", help="iterative scatter correction on a large flat panel")
     p.add_argument("--vr-eval", action="store_true", help="expected-value vs sampled-type point-detector scoring")
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
+    p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
     p.add_argument("--tally", choices=["auto", "global", "shared", "warp", "tiled"], default="auto",
@@ -925,6 +926,59 @@ def run_vr_eval(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tally_eval(args):
+    """Tally modes on the bench workload: transport time, relative L2 noise of the
+    scatter image and figure of merit 1 / (noise^2 x time) of the global tally and
+    of tile-stratified tallies of several tile sizes.  The noise is taken two ways:
+    from the batch variance (10 batches) and from the spread of the images of
+    independent seeds; also the distance of each mean image from the global one in
+    units of the combined noise (the tile-stratified estimator is unbiased)."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    tp, wl = make_inputs(tempfile.mkdtemp(prefix="mctally"), args.photons or 1e8, args.workload)
+    N = wl["n_photons"]
+    modes = [("global", 1, 64)] + [(f"tiled {t}x{t}", 4, t) for t in (8, 16, 24, 32)]
+    res, imgs = {}, {}
+    for name, mode, t in modes:
+        ctx = mcx.Context(0, n_batches=10, tally_mode=mode, tile_u=t, tile_v=t)
+        ctx.load_tables(tp)
+        ctx.setup(wl)
+        ms, noise, runs = [], [], []
+        for k in range(args.warmup + args.steps):
+            out = ctx.project([0.0], N, wl["step_mm"], 100 + k, primary=False, variance=True)
+            st = ctx.last_stats()
+            if k >= args.warmup:
+                img = out["scatter"][0].double()
+                var = out["variance"][0].double()
+                ms.append(st["transport_ms"])
+                noise.append(float(torch.sqrt(var.sum()) / torch.linalg.norm(img)))
+                runs.append(img)
+        t_s = float(np.mean(ms)) / 1e3
+        n2 = float(np.mean(np.square(noise)))
+        R = torch.stack(runs)
+        mean = R.mean(0)
+        run_var = R.var(0, unbiased=True)  # per run
+        n2_runs = float(run_var.sum() / (mean * mean).sum())
+        imgs[name] = (mean, run_var / len(runs))
+        res[name] = {"transport_s": t_s, "histories_per_s": N / t_s, "rel_l2_noise_batches": float(np.sqrt(n2)),
+                     "rel_l2_noise_runs": float(np.sqrt(n2_runs)), "figure_of_merit": 1.0 / (n2_runs * t_s)}
+    g_img, g_var = imgs["global"]
+    for name in res:
+        if name == "global":
+            continue
+        m, v = imgs[name]
+        res[name]["mean_diff_over_noise"] = float(torch.linalg.norm(m - g_img) / torch.sqrt((v + g_var).sum()))
+        res[name]["fom_gain"] = res[name]["figure_of_merit"] / res["global"]["figure_of_merit"]
+    line = {"metric": "figure of merit 1/(relative L2 noise^2 x transport time) by tally mode", "unit": "1/s",
+            "higher_is_better": True,
+            "config": {"workload": args.workload, "photons": N, "batches": 10, "steps": args.steps},
+            "modes": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_mesh_bench(args):
     """Primary images of the triangle-mesh (CAD) cylinder-rod phantom by ray casting
     (eq. Ip with exact path lengths): rays per second through the hierarchy."""
@@ -995,6 +1049,8 @@ def main():
         run_vr_eval(args)
     elif args.mesh_bench:
         run_mesh_bench(args)
+    elif args.tally_eval:
+        run_tally_eval(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

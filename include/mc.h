@@ -70,7 +70,8 @@ typedef struct mc_options {
   int n_split;           /* pseudo-particles per scatter interaction (Sec. II-C.1), default 10 */
   float rr_threshold;    /* Russian roulette on the pseudo-particle weight x0 (Sec. II-C.1); 0 = off */
   int max_scatter_order; /* a history ends after this many scatters (energy deposited), default 64 */
-  int n_batches;         /* >1: histories h mod n_batches form batches for scatter_var_out */
+  int n_batches;         /* >1: histories h mod n_batches form batches for scatter_var_out (with
+                            MC_TALLY_TILED: floor(h / T) mod n_batches, T the number of tiles) */
   int block_size;        /* transport threads per block; 0 = default (256) */
   int blocks_per_sm;     /* persistent grid = SMs x blocks_per_sm; 0 = default (occupancy) */
   int tally_mode;        /* MC_TALLY_* */

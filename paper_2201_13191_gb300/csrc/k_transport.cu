@@ -429,7 +429,10 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   const uint4 blk = philox4x32_10(make_uint4(R.k0[r] + (uint32_t)s, a, hlo, hhi), key);
   const float va = Rng::u01(blk.y), vb = Rng::u01(blk.z), vr = Rng::u01(blk.w);
   const unsigned long long hh = ((unsigned long long)hhi << 32) | hlo;
-  const int bt = P.n_batches > 1 ? (int)(hh % (unsigned long long)P.n_batches) : 0;
+  // batch of the variance estimate: h mod n_batches; under the tile-stratified tally
+  // floor(h / T) mod n_batches, so that every batch holds its share of every tile
+  const unsigned long long hb = (COMBINE && P.tally_mode == TALLY_TILED) ? hh / (unsigned long long)P.n_tiles : hh;
+  const int bt = P.n_batches > 1 ? (int)(hb % (unsigned long long)P.n_batches) : 0;
   uint32_t pi, pj;
   size_t off;
   float tscale = 1.f;
