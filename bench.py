@@ -668,7 +668,7 @@ def run_conv_bench(args):
         dw = torch.zeros((co, 9, ci), device="cuda")
         npx = B * h * w
         ktiles = (9 * ci + 127) // 128
-        splits = max(1, min(npx // 512, 2 * 152 // ktiles + 1))
+        splits = max(1, min(npx // 256, 4 * 152 // ktiles + 1))
 
         def fwd():
             if L.mc_nn_conv3x3(ptr(x), ptr(wt), ptr(bias), ptr(y), B, h, w, ci, co, 1, 0, ptr(err), sh):

@@ -173,7 +173,7 @@ cudaError_t back(Denoiser* d, int i, int n, const __nv_bfloat16* x, const __nv_b
   wp.cout = l.cout;
   wp.err = d->err;
   const int ktiles = (9 * l.cin + 127) / 128;
-  int splits = (int)std::max<size_t>(1, std::min<size_t>(np / 512, (size_t)(2 * 152 / ktiles + 1)));
+  int splits = (int)std::max<size_t>(1, std::min<size_t>(np / 256, (size_t)(4 * 152 / ktiles + 1)));
   TRY(launch_conv3x3_wgrad(wp, splits, s));
   if (gx) {
     const int c1 = split > 0 ? split : l.cin;

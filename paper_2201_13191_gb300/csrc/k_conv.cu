@@ -27,13 +27,23 @@ constexpr int kStageK = 64;    // reduction elements per stage
 constexpr int kKG = kStageK / 8;
 constexpr int kThreads = 128;  // four warps: one per 32 tensor-memory lanes
 
+// Weight-gradient operand tiles: the K-major no-swizzle canonical layout (core
+// matrices of 8 rows x 16 bytes) with padded strides, core matrices kLbo bytes
+// apart along K and 8-row groups kSbo apart, so that eight lanes storing the
+// same row of eight different core matrices hit eight different 16-byte bank
+// slots (the unpadded 128 / 1024-byte strides put them all on one).
+constexpr int kLbo = 128 + 16;
+constexpr int kSbo = kKG * kLbo + 16;
 template <int N>
 struct ConvSmem {
-  static constexpr int a_bytes = kM * kStageK * 2;  // 16 KB
-  static constexpr int b_bytes = N * kStageK * 2;   // <= 32 KB
+  static constexpr int a_bytes = (kM / 8) * kSbo;
+  static constexpr int b_bytes = (N / 8) * kSbo;
   static constexpr int stage_bytes = a_bytes + b_bytes;
   static constexpr int bytes = 2 * stage_bytes + 1024;  // + alignment slack
 };
+__device__ __forceinline__ uint32_t wg_off(int row, int k) {
+  return (uint32_t)((row >> 3) * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
+}
 
 // ---------------------------------------------------------------------------
 // Forward (and input-gradient) convolution.
@@ -237,12 +247,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
 }
 
 // Weight gradient.  CTA (blockIdx.x = k tile, blockIdx.y = pixel split).
+// Transpose of an 8 x 8 block of 16-bit values held as 8 rows of 16 bytes:
+// out[i] word m = (v[2m] element i, v[2m+1] element i).
+__device__ __forceinline__ void transpose8x8(const uint4 (&v)[8], uint4 (&o)[8]) {
+#pragma unroll
+  for (int pr = 0; pr < 4; ++pr) {
+    uint32_t lo[4], hi[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t a = pr == 0 ? v[2 * m].x : pr == 1 ? v[2 * m].y : pr == 2 ? v[2 * m].z : v[2 * m].w;
+      const uint32_t b = pr == 0 ? v[2 * m + 1].x : pr == 1 ? v[2 * m + 1].y : pr == 2 ? v[2 * m + 1].z : v[2 * m + 1].w;
+      lo[m] = __byte_perm(a, b, 0x5410);  // element 2 pr of both rows
+      hi[m] = __byte_perm(a, b, 0x7632);  // element 2 pr + 1 of both rows
+    }
+    o[2 * pr] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    o[2 * pr + 1] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  }
+}
+
+// Weight gradient dW[co][k] = sum_q dY[q][co] X(q shifted by tap(k))[c(k)],
+// k = tap * C_in + c.  GEMM rows = 128 values of k (blockIdx.x), columns =
+// C_out (N), reduction over the pixels [pbeg, pend) of this CTA (blockIdx.y of
+// `splits`), 64 pixels per stage.  Both operands are K-major (pixels along K)
+// while the tensors are channel-minor, so each thread turns one 8 x 8 block
+// (8 pixels x 8 channels, eight 16-byte loads) into one core matrix (8 rows of
+// 8 pixels) by a register transpose and one 16-byte store per row.  A stage's
+// loads go out before the previous stage's MMAs are waited on (two buffers,
+// one mbarrier each); thread 0 issues the MMAs.  The partial tile is added
+// into dW (FP32 atomics).
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p) {
   extern __shared__ unsigned char dyn_raw[];
   unsigned char* dyn = reinterpret_cast<unsigned char*>(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_holder;
   __shared__ __align__(8) uint64_t mbar[2];
+  constexpr int kBUnits = (N / 8) * (kStageK / 8);          // 8 x 8 blocks of the dY operand per stage
+  constexpr int kBPer = (kBUnits + kThreads - 1) / kThreads;  // per thread
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 9 * p.cin;
   const int krow0 = blockIdx.x * kM;
@@ -251,6 +291,45 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p)
   const long long pbeg = (long long)blockIdx.y * chunk;
   const long long pend = min(npix, pbeg + chunk);
   const int n_stages = pend > pbeg ? (int)((pend - pbeg + kStageK - 1) / kStageK) : 0;
+
+  // this thread's A block: rows rg*8 .. rg*8+7 (one tap, channels c .. c+7), pixels pg*8 .. pg*8+7
+  const int rg = tid & 15, pg = tid >> 4;
+  const int k_a = krow0 + rg * 8;
+  const int tap = k_a / p.cin, c_a = k_a - tap * p.cin;
+  const int ddy = tap / 3 - 1, ddx = tap % 3 - 1;
+  const bool row_ok = k_a < K;
+
+  auto load_a = [&](int st, uint4 (&v)[8]) {
+    const long long qs = pbeg + (long long)st * kStageK + pg * 8;
+    long long t = qs / p.w;
+    int qx = (int)(qs - t * p.w);
+    int qy = (int)(t % p.h);
+    long long qn = t / p.h;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      v[jj] = make_uint4(0u, 0u, 0u, 0u);
+      const int yy = qy + ddy, xx = qx + ddx;
+      if (row_ok && qs + jj < pend && yy >= 0 && yy < p.h && xx >= 0 && xx < p.w)
+        v[jj] = __ldg(reinterpret_cast<const uint4*>(p.x + ((qn * p.h + yy) * p.w + xx) * p.cin + c_a));
+      if (++qx == p.w) {
+        qx = 0;
+        if (++qy == p.h) {
+          qy = 0;
+          ++qn;
+        }
+      }
+    }
+  };
+  auto load_b = [&](int st, int u, uint4 (&v)[8]) {
+    const int cg = u % (N / 8), bp = u / (N / 8);
+    const long long qs = pbeg + (long long)st * kStageK + bp * 8;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      v[jj] = make_uint4(0u, 0u, 0u, 0u);
+      if (qs + jj < pend && cg * 8 < p.cout)
+        v[jj] = __ldg(reinterpret_cast<const uint4*>(p.dy + (qs + jj) * p.cout + cg * 8));
+    }
+  };
 
   if (warp == 0) tc::tmem_alloc(&tmem_holder, tmem_cols(N));
   if (tid == 0) {
@@ -262,42 +341,42 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p)
   tc::fence_after();
   const uint32_t tmem = tmem_holder;
   bool ok = true;
+  uint4 ra[8], rb[kBPer][8];
+  if (n_stages > 0) {
+    load_a(0, ra);
+#pragma unroll
+    for (int i = 0; i < kBPer; ++i)
+      if (tid + i * kThreads < kBUnits) load_b(0, tid + i * kThreads, rb[i]);
+  }
   for (int st = 0; st < n_stages; ++st) {
     const int buf = st & 1;
     unsigned char* sA = dyn + buf * ConvSmem<N>::stage_bytes;
     unsigned char* sB = sA + ConvSmem<N>::a_bytes;
     if (st >= 2) ok &= tc::mbar_wait(&mbar[buf], (uint32_t)((st >> 1) - 1) & 1u);
-    const long long q0 = pbeg + (long long)st * kStageK;
-    // A[r][j] = X(pixel q0 + j shifted by tap(krow0 + r), channel(krow0 + r)): 16 row groups x 64 pixels
-    for (int item = tid; item < (kM / 8) * kStageK; item += kThreads) {
-      const int j = item % kStageK, rg = item / kStageK;
-      const int k = krow0 + rg * 8;
-      const long long q = q0 + j;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (k < K && q < pend) {
-        const int tap = k / p.cin, c = k - tap * p.cin;
-        const int qx = (int)(q % p.w);
-        const long long t = q / p.w;
-        const int qy = (int)(t % p.h), qn = (int)(t / p.h);
-        const int yy = qy + tap / 3 - 1, xx = qx + tap % 3 - 1;
-        if (yy >= 0 && yy < p.h && xx >= 0 && xx < p.w)
-          v = __ldg(reinterpret_cast<const uint4*>(p.x + (((long long)qn * p.h + yy) * p.w + xx) * p.cin + c));
-      }
-      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+    {
+      uint4 o[8];
+      transpose8x8(ra, o);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        *reinterpret_cast<__nv_bfloat16*>(sA + tc::canon_off(rg * 8 + i, j, kKG)) = e[i];
+        *reinterpret_cast<uint4*>(sA + wg_off(rg * 8 + i, pg * 8)) = o[i];
     }
-    // B[co][j] = dY(pixel q0 + j, co)
-    for (int item = tid; item < (N / 8) * kStageK; item += kThreads) {
-      const int j = item % kStageK, cg = item / kStageK;
-      const long long q = q0 + j;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q < pend && cg * 8 < p.cout) v = __ldg(reinterpret_cast<const uint4*>(p.dy + q * p.cout + cg * 8));
-      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        *reinterpret_cast<__nv_bfloat16*>(sB + tc::canon_off(cg * 8 + i, j, kKG)) = e[i];
+    for (int i = 0; i < kBPer; ++i) {
+      const int u = tid + i * kThreads;
+      if (u < kBUnits) {
+        const int cg = u % (N / 8), bp = u / (N / 8);
+        uint4 o[8];
+        transpose8x8(rb[i], o);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) *reinterpret_cast<uint4*>(sB + wg_off(cg * 8 + r, bp * 8)) = o[r];
+      }
+    }
+    // the next stage's loads overlap the barrier and this stage's MMAs
+    if (st + 1 < n_stages) {
+      load_a(st + 1, ra);
+#pragma unroll
+      for (int i = 0; i < kBPer; ++i)
+        if (tid + i * kThreads < kBUnits) load_b(st + 1, tid + i * kThreads, rb[i]);
     }
     tc::fence_async_smem();
     __syncthreads();
@@ -305,8 +384,9 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p)
       tc::fence_after();
       const uint32_t idesc = tc::idesc_bf16(kM, N);
       for (int ks = 0; ks < kStageK / 16; ++ks) {
-        const uint64_t da = tc::sdesc(tc::saddr(sA) + ks * 256, 128, kKG * 128);
-        const uint64_t db = tc::sdesc(tc::saddr(sB) + ks * 256, 128, kKG * 128);
+        // k-step ks covers core-matrix columns 2 ks, 2 ks + 1
+        const uint64_t da = tc::sdesc(tc::saddr(sA) + ks * 2 * kLbo, kLbo, kSbo);
+        const uint64_t db = tc::sdesc(tc::saddr(sB) + ks * 2 * kLbo, kLbo, kSbo);
         tc::mma_bf16(tmem, da, db, idesc, (st > 0 || ks > 0) ? 1u : 0u);
       }
       tc::commit(&mbar[buf]);
@@ -315,6 +395,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_wgrad(const WgradParams p)
   if (n_stages > 0) {
     const int last = n_stages - 1;
     ok &= tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u);
+    if (n_stages > 1) ok &= tc::mbar_wait(&mbar[(last - 1) & 1], (uint32_t)((last - 1) >> 1) & 1u);
   }
   tc::fence_after();
   if (!ok && tid == 0) atomicOr(p.err, 1);
