@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--vr-eval", action="store_true", help="expected-value vs sampled-type point-detector scoring")
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
     p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
+    p.add_argument("--primary-bench", action="store_true", help="primary images of the correction workload")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
     p.add_argument("--tally", choices=["auto", "global", "shared", "warp", "tiled"], default="auto",
@@ -979,6 +980,64 @@ def run_tally_eval(args):
     print(json.dumps(line), flush=True)
 
 
+def run_primary_bench(args):
+    """Deterministic primary images (eq. Ip) of the correction workload: 512^3 x 0.2 mm
+    cylinder phantom (brick layout, HBM-resident), 2048^2 x 0.1 mm panel, step 0.2 mm,
+    64 angles per call: rays/s and march steps/s."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+    from mc_inputs import cylinder_variant_phantom, default_table_path, mono_spectrum
+
+    mcx.build()
+    tp = default_table_path("full", tempfile.mkdtemp(prefix="mcprim"))
+    nvx, dv, NU, P, step = args.cor_volume, args.cor_voxel, args.cor_detector, args.cor_pixel, args.cor_step
+    vol = cylinder_variant_phantom(args.cor_seed, n=nvx, dv=dv)
+    ctx = mcx.Context(0)
+    ctx.load_tables(tp)
+    ctx.set_spectrum(*mono_spectrum(60.0))
+    ctx.set_geometry(300.0, 600.0, NU, NU, P, P)
+    ctx.load_volume(vol["mat"], vol["rho"], vol["spacing"])
+    n_ang = 64
+    angles = (2.0 * np.pi * np.arange(n_ang) / n_ang).astype(np.float32)
+    out = {"primary": ctx.empty_images(n_ang)}
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ctx.project(angles, 1, step, 1, scatter=False, out=out, stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.project(angles, 1, step, 1, scatter=False, out=out, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rays = NU * NU * n_ang
+    # march steps: each ray's chord through the volume box over the step, summed on the host
+    s_pos = 300.0 * np.stack([np.cos(angles), np.sin(angles), np.zeros(n_ang)], 1)
+    c_pos = -300.0 * np.stack([np.cos(angles), np.sin(angles), np.zeros(n_ang)], 1)
+    u = (np.arange(0, NU, 8) + 0.5 - NU / 2) * P
+    half = nvx * dv / 2
+    steps = 0.0
+    for a in range(n_ang):
+        eu = np.array([-np.sin(angles[a]), np.cos(angles[a]), 0.0])
+        Pp = c_pos[a] + u[:, None, None] * eu + u[None, :, None] * np.array([0.0, 0.0, 1.0])
+        w = Pp - s_pos[a]
+        w /= np.linalg.norm(w, axis=-1, keepdims=True)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1 = (-half - s_pos[a]) / w
+            t2 = (half - s_pos[a]) / w
+        ta = np.nanmax(np.minimum(t1, t2), -1)
+        tb = np.nanmin(np.maximum(t1, t2), -1)
+        L = np.clip(tb - ta, 0, None)
+        steps += float(np.sum(np.where(L > 0, np.maximum(1, np.ceil(L / step)), 0))) * 64  # 8x8 subsampled
+    line = {"metric": "primary rays/s (eq. Ip, exact column masses)", "value": rays / (ms / 1e3), "unit": "rays/s",
+            "higher_is_better": True, "dtype": "f32",
+            "config": {"workload": f"{nvx}^3 x {dv} mm cylinder phantom, {NU}^2 x {P} mm panel, step {step} mm, "
+                                   f"{n_ang} angles per call", "steps": args.steps},
+            "ms_per_call": ms, "ms_per_projection": ms / n_ang, "march_steps_per_s": steps / (ms / 1e3)}
+    print(json.dumps(line), flush=True)
+
+
 def run_mesh_bench(args):
     """Primary images of the triangle-mesh (CAD) cylinder-rod phantom by ray casting
     (eq. Ip with exact path lengths): rays per second through the hierarchy."""
@@ -1051,6 +1110,8 @@ def main():
         run_mesh_bench(args)
     elif args.tally_eval:
         run_tally_eval(args)
+    elif args.primary_bench:
+        run_primary_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

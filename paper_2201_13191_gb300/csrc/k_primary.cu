@@ -12,6 +12,7 @@ namespace mcx {
 namespace {
 
 constexpr float kPi = 3.14159265358979f;
+constexpr int kAhead = 8;  // voxel words in flight per ray
 
 // FP16 bit pattern -> value * 2^24 as an exact integer (finite, non-negative inputs).
 __device__ __forceinline__ unsigned long long fp16_fixed24(uint16_t b) {
@@ -55,24 +56,31 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
     h = L / (float)n;
     VoxRay r;
     r.set(V, ps.s, w);
-    uint32_t word = __ldg(V.vox + r.voxel<LAYOUT>(V, fmaf(0.5f, h, ta)));
-    int cur = vox_mat(word), vprev = -1;
-    unsigned long long run = 0ull, val = 0ull;
-    for (int k = 0; k < n; ++k) {
-      const int v = r.voxel<LAYOUT>(V, fmaf((float)k + 0.5f, h, ta));
-      if (v != vprev) {
-        vprev = v;
-        word = __ldg(V.vox + v);
-        val = fp16_fixed24((uint16_t)(word & 0xffffu));
-        const int m = vox_mat(word);
-        if (m != cur) {
+    int cur = vox_mat(__ldg(V.vox + r.voxel<LAYOUT>(V, fmaf(0.5f, h, ta))));
+    unsigned long long run = 0ull;
+    // the words of the next kAhead midpoints are loaded before any is used (the
+    // step positions are known in advance, so the gathers are independent);
+    // midpoints past the chord's end repeat its last one and are not summed
+    for (int k0 = 0; k0 < n; k0 += kAhead) {
+      uint32_t wd[kAhead];
 #pragma unroll
-          for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
-          cur = m;
-          run = 0ull;
+      for (int u = 0; u < kAhead; ++u) {
+        const int kk = min(k0 + u, n - 1);
+        wd[u] = __ldg(V.vox + r.voxel<LAYOUT>(V, fmaf((float)kk + 0.5f, h, ta)));
+      }
+#pragma unroll
+      for (int u = 0; u < kAhead; ++u) {
+        if (k0 + u < n) {
+          const int m = vox_mat(wd[u]);
+          if (m != cur) {
+#pragma unroll
+            for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+            cur = m;
+            run = 0ull;
+          }
+          run += fp16_fixed24((uint16_t)(wd[u] & 0xffffu));
         }
       }
-      run += val;
     }
 #pragma unroll
     for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
