@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
     p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
     p.add_argument("--primary-bench", action="store_true", help="primary images of the correction workload")
+    p.add_argument("--primary-speckle", type=float, default=0.0, help="fraction of voxels given another material")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
     p.add_argument("--tally", choices=["auto", "global", "shared", "warp", "tiled"], default="auto",
@@ -993,6 +994,12 @@ def run_primary_bench(args):
     tp = default_table_path("full", tempfile.mkdtemp(prefix="mcprim"))
     nvx, dv, NU, P, step = args.cor_volume, args.cor_voxel, args.cor_detector, args.cor_pixel, args.cor_step
     vol = cylinder_variant_phantom(args.cor_seed, n=nvx, dv=dv)
+    if args.primary_speckle > 0:
+        # a segmented reconstruction's misclassified voxels: a fraction of them take another material
+        rng = np.random.default_rng(3)
+        flip = rng.random(vol["mat"].shape) < args.primary_speckle
+        vol = dict(vol, mat=vol["mat"].copy())
+        vol["mat"][flip] = rng.choice(np.array([0, 1, 3], np.uint8), size=int(flip.sum()))
     ctx = mcx.Context(0)
     ctx.load_tables(tp)
     ctx.set_spectrum(*mono_spectrum(60.0))
@@ -1033,7 +1040,7 @@ def run_primary_bench(args):
     line = {"metric": "primary rays/s (eq. Ip, exact column masses)", "value": rays / (ms / 1e3), "unit": "rays/s",
             "higher_is_better": True, "dtype": "f32",
             "config": {"workload": f"{nvx}^3 x {dv} mm cylinder phantom, {NU}^2 x {P} mm panel, step {step} mm, "
-                                   f"{n_ang} angles per call", "steps": args.steps},
+                                   f"{n_ang} angles per call", "speckle": args.primary_speckle, "steps": args.steps},
             "ms_per_call": ms, "ms_per_projection": ms / n_ang, "march_steps_per_s": steps / (ms / 1e3)}
     print(json.dumps(line), flush=True)
 

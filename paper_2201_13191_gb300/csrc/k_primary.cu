@@ -20,10 +20,23 @@ __device__ __forceinline__ unsigned long long fp16_fixed24(uint16_t b) {
   return e == 0 ? (unsigned long long)f : ((unsigned long long)(f | 1024u) << (e - 1));
 }
 
-template <int LAYOUT>
+// Column masses per material: a run of voxels of one material is summed in a
+// register and added to its material's total when the material changes.  With
+// SACC the totals live in shared memory (one add wherever the run ends), which
+// suits volumes whose material changes often (a segmented reconstruction's
+// misclassified voxels); otherwise in registers, selected by a switch, which
+// leaves the L1 cache its full size.  Both sum the same integers exactly.
+template <int LAYOUT, bool SACC>
 __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
-  extern __shared__ float s_mub[];  // [n_bins][n_mat]: 0.1 * mu/rho at each bin energy
+  // shared: [n_bins][n_mat] 0.1 * mu/rho at each bin energy, then (SACC)
+  // [n_mat][blockDim] this block's per-thread totals
+  extern __shared__ __align__(8) unsigned char s_raw[];
   const int nm = P.tab.n_mat, nb = P.spec.n_bins, ns = P.tab.n_stage;
+  float* s_mub = reinterpret_cast<float*>(s_raw);
+  unsigned long long* my_acc =
+      reinterpret_cast<unsigned long long*>(s_raw + (((size_t)nb * nm * 4 + 7) & ~(size_t)7)) + threadIdx.x;
+  if (SACC)
+    for (int m = 0; m < nm; ++m) my_acc[m * blockDim.x] = 0ull;
   for (int q = threadIdx.x; q < nb * nm; q += blockDim.x) {
     const int n = q / nm, m = q % nm;
     const float E = P.spec.energy[n];
@@ -73,8 +86,17 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
         if (k0 + u < n) {
           const int m = vox_mat(wd[u]);
           if (m != cur) {
-#pragma unroll
-            for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+            if (SACC) my_acc[cur * blockDim.x] += run;
+            else switch (cur) {
+              case 0: acc[0] += run; break;
+              case 1: acc[1] += run; break;
+              case 2: acc[2] += run; break;
+              case 3: acc[3] += run; break;
+              case 4: acc[4] += run; break;
+              case 5: acc[5] += run; break;
+              case 6: acc[6] += run; break;
+              default: acc[7] += run; break;
+            }
             cur = m;
             run = 0ull;
           }
@@ -82,12 +104,19 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
         }
       }
     }
+    if (SACC) {
+      my_acc[cur * blockDim.x] += run;
+    } else {
 #pragma unroll
-    for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+      for (int q = 0; q < kMaxMat; ++q) acc[q] += (q == cur) ? run : 0ull;
+    }
   }
   float rl[kMaxMat];
 #pragma unroll
-  for (int m = 0; m < kMaxMat; ++m) rl[m] = (float)acc[m] * 5.9604644775390625e-08f * h;  // 2^-24
+  for (int m = 0; m < kMaxMat; ++m) {
+    const unsigned long long t = SACC ? (m < nm ? my_acc[m * blockDim.x] : 0ull) : acc[m];
+    rl[m] = (float)t * 5.9604644775390625e-08f * h;  // 2^-24
+  }
   float sum = 0.f;
   for (int n = 0; n < nb; ++n) {
     const float S = __ldg(P.spec.sn + n);
@@ -108,12 +137,53 @@ cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s) {
   const int block = 256;
   const int npix = p.geo.nu * p.geo.nv;
   dim3 grid((npix + block - 1) / block, p.n_angles);
-  const int smem = p.spec.n_bins * p.tab.n_mat * 4;
-  if (p.vol.layout == VOX_BRICK) k_primary<VOX_BRICK><<<grid, block, smem, s>>>(p);
-  else k_primary<VOX_LIN><<<grid, block, smem, s>>>(p);
+  const int smem = ((p.spec.n_bins * p.tab.n_mat * 4 + 7) & ~7) + (p.shared_acc ? p.tab.n_mat * block * 8 : 0);
+  const bool brick = p.vol.layout == VOX_BRICK;
+  auto k = brick ? (p.shared_acc ? k_primary<VOX_BRICK, true> : k_primary<VOX_BRICK, false>)
+                 : (p.shared_acc ? k_primary<VOX_LIN, true> : k_primary<VOX_LIN, false>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 
+}  // namespace mcx
+
+// Fraction of x-neighbour voxel pairs whose materials differ (how often a ray
+// meets a material change); chooses the primary kernel's accumulator variant.
+namespace mcx {
+namespace {
+__global__ void k_mat_changes(const uint8_t* __restrict__ mat, size_t n, int nx, unsigned long long* count) {
+  unsigned long long c = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < n; i += (size_t)gridDim.x * blockDim.x)
+    c += (i % (size_t)nx != (size_t)nx - 1) && mat[i] != mat[i + 1];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+}  // namespace
+
+cudaError_t material_change_fraction(const uint8_t* mat, int nx, int ny, int nz, cudaStream_t s, double* frac) {
+  *frac = 0.0;
+  const size_t n = (size_t)nx * ny * nz;
+  const size_t pairs = n - (size_t)ny * nz;
+  if (pairs == 0) return cudaSuccess;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, 8, s);
+  if (e != cudaSuccess) return e;
+  unsigned long long h = 0;
+  e = cudaMemsetAsync(d, 0, 8, s);
+  if (e == cudaSuccess) {
+    k_mat_changes<<<152 * 8, 256, 0, s>>>(mat, n, nx, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *frac = (double)h / (double)pairs;
+  return e;
+}
 }  // namespace mcx
 
 // Device-side validation of a volume given by device pointers: every material

@@ -46,6 +46,7 @@ struct mc_ctx {
   float* d_mesh_rho = nullptr;
   int mesh_nodes = 0, mesh_tris = 0, mesh_bodies = 0;
   double mesh_rmax = 0;  // largest distance of a vertex from the rotation axis
+  double mat_change = 0;  // fraction of x-neighbour voxel pairs of different materials
   float mesh_half[3] = {0.f, 0.f, 0.f};  // half extents of a box about the origin holding every vertex
   // volume
   bool have_volume = false;
@@ -436,6 +437,8 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     pp.n_angles = n_angles;
     pp.step = step;
     pp.out = primary_out;
+    // measured crossover (2048^2 x 512^3): shared totals win above ~7% changing neighbour pairs
+    pp.shared_acc = ctx->mat_change > 0.07 ? 1 : 0;
   }
   if (scatter_out) {
     tp.tab = table_view(ctx);
@@ -849,10 +852,13 @@ int mc_load_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho_fp16, in
   const size_t words = packed_words(nx, ny, nz, layout);
   e = ensure(ctx->d_vox, ctx->vox_cap, words);
   if (e == cudaSuccess) e = pack_volume(st_mat, st_rho, nx, ny, nz, layout, ctx->d_vox, words, s);
+  double change = 0.0;
+  if (e == cudaSuccess) e = material_change_fraction(st_mat, nx, ny, nz, s, &change);
   release();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "volume packing");
   CK(cudaStreamSynchronize(s), "volume load");
   ctx->layout = layout;
+  ctx->mat_change = change;
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz;
   ctx->dx = dx; ctx->dy = dy; ctx->dz = dz;
   ctx->have_volume = true;

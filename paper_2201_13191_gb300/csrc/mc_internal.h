@@ -151,6 +151,7 @@ struct PrimaryParams {
   int n_angles;
   float step;
   float* out;  // [n_angles][nv][nu]
+  int shared_acc = 0;  // per-material totals in shared memory (volumes with frequent material changes)
 };
 
 // launch wrappers (return cudaError_t of the launch)
@@ -161,6 +162,8 @@ int transport_shared_pixels(const TransportParams& p);
 cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh = false);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
+// Fraction of x-neighbour voxel pairs of a device material array whose materials differ (synchronises s).
+cudaError_t material_change_fraction(const uint8_t* mat, int nx, int ny, int nz, cudaStream_t s, double* frac);
 
 // Returns the depth of the deepest leaf (the device descent needs depth < 64).
 int build_mesh_bvh(const float* v, const int* tris, const int* tri_body, int nt, std::vector<float4>& nodes,
