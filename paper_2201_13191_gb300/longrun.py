@@ -15,8 +15,9 @@ finished chunk's image:
   that died (non-zero exit) before summing all chunks in chunk order.
 
 The sum is taken in chunk order in FP64 in both, so with a deterministic range
-runner (the CPU oracle) a run that was interrupted and resumed, or whose
-worker died, gives the same total bit for bit as an uninterrupted one.  The
+runner (one that adds its histories in a fixed order, as a CPU implementation
+does) a run that was interrupted and resumed, or whose worker died, gives the
+same total bit for bit as an uninterrupted one.  The
 GPU's own tally adds in FP64 in a data-dependent order, so its chunk images
 agree to FP64 rounding.  Host logic only: nothing here computes the method.
 """
