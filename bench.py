@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
     p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
     p.add_argument("--primary-bench", action="store_true", help="primary images of the correction workload")
+    p.add_argument("--fdk-bench", action="store_true", help="FDK of 256 projections of the correction workload")
     p.add_argument("--primary-speckle", type=float, default=0.0, help="fraction of voxels given another material")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
@@ -1045,6 +1046,39 @@ def run_primary_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fdk_bench(args):
+    """FDK reconstruction (ramp filter + voxel-driven backprojection) of 256 projections
+    of 2048^2 x 0.1 mm into 512^3 x 0.2 mm: milliseconds and voxel-projection updates/s."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    NU, P, nvx, dv, n_proj = args.cor_detector, args.cor_pixel, args.cor_volume, args.cor_voxel, 256
+    ctx = mcx.Context(0)
+    ctx.set_geometry(300.0, 600.0, NU, NU, P, P)
+    angles = (2.0 * np.pi * np.arange(n_proj) / n_proj).astype(np.float32)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    p = torch.rand((n_proj, NU, NU), device="cuda", generator=g)
+    grid = (nvx, nvx, nvx, dv, dv, dv)
+    for _ in range(max(1, args.warmup)):
+        ctx.fdk(p, angles, NU, NU, grid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.fdk(p, angles, NU, NU, grid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    upd = float(nvx) ** 3 * n_proj
+    line = {"metric": "FDK voxel-projection updates/s", "value": upd / (ms / 1e3), "unit": "updates/s",
+            "higher_is_better": True, "dtype": "f32",
+            "config": {"workload": f"{n_proj} projections of {NU}^2 x {P} mm -> {nvx}^3 x {dv} mm", "steps": args.steps},
+            "ms_per_fdk": ms}
+    print(json.dumps(line), flush=True)
+
+
 def run_mesh_bench(args):
     """Primary images of the triangle-mesh (CAD) cylinder-rod phantom by ray casting
     (eq. Ip with exact path lengths): rays per second through the hierarchy."""
@@ -1119,6 +1153,8 @@ def main():
         run_tally_eval(args)
     elif args.primary_bench:
         run_primary_bench(args)
+    elif args.fdk_bench:
+        run_fdk_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -103,38 +103,57 @@ __global__ void __launch_bounds__(kFiltThreads) k_fdk_filter(const float* __rest
 
 // Voxel-driven backprojection: f(x) = (dbeta / 2) sum_beta (D / (D - x.n))^2 q(u(x), v(x)),
 // q bilinearly interpolated at the voxel's projection (zero outside the panel).
+// Voxel-driven backprojection: each thread owns kZB voxels of one (x, y)
+// column; per projection the source-side terms (depth, magnification, u and
+// its bilinear weights) are computed once for the column, then each voxel adds
+// its bilinear sample (the same expressions as one voxel at a time, so the
+// same sums).
+constexpr int kZB = 4;
 __global__ void k_fdk_backproject(const float* __restrict__ q, const float* __restrict__ cb, const float* __restrict__ sb,
                                   int n_proj, int nu, int nv, float du_iso, float dv_iso, float sod, int nx, int ny,
                                   int nz, float dx, float dy, float dz, float scale, float* __restrict__ vol) {
-  const size_t n = (size_t)nx * ny * nz;
+  const int nzb = (nz + kZB - 1) / kZB;
+  const size_t n = (size_t)nx * ny * nzb;
   for (size_t i = gtid(); i < n; i += gstride()) {
     const int ix = (int)(i % nx);
     const size_t t = i / nx;
-    const int iy = (int)(t % ny), iz = (int)(t / ny);
+    const int iy = (int)(t % ny), iz0 = (int)(t / ny) * kZB;
     const float x = ((float)ix - 0.5f * (float)(nx - 1)) * dx;
     const float y = ((float)iy - 0.5f * (float)(ny - 1)) * dy;
-    const float z = ((float)iz - 0.5f * (float)(nz - 1)) * dz;
-    float acc = 0.f;
+    float z[kZB], acc[kZB];
+#pragma unroll
+    for (int j = 0; j < kZB; ++j) {
+      z[j] = ((float)(iz0 + j) - 0.5f * (float)(nz - 1)) * dz;
+      acc[j] = 0.f;
+    }
     for (int k = 0; k < n_proj; ++k) {
       const float c = __ldg(cb + k), s = __ldg(sb + k);
       const float depth = sod - (x * c + y * s);  // distance from the source along the central ray
       const float mag = sod / depth;
       const float u = (-x * s + y * c) * mag;     // isocentre-plane coordinates
-      const float v = z * mag;
       const float fu = u / du_iso + 0.5f * (float)(nu - 1);
-      const float fv = v / dv_iso + 0.5f * (float)(nv - 1);
-      const int u0 = __float2int_rd(fu), v0 = __float2int_rd(fv);
-      const float au = fu - (float)u0, av = fv - (float)v0;
+      const int u0 = __float2int_rd(fu);
+      const float au = fu - (float)u0;
+      const bool u_in = u0 >= 0 && u0 + 1 < nu;
       const float* qp = q + (size_t)k * nu * nv;
-      float val = 0.f;
-      if (u0 >= 0 && u0 + 1 < nu && v0 >= 0 && v0 + 1 < nv) {
-        const float* r0 = qp + (size_t)v0 * nu + u0;
-        val = (1.f - av) * ((1.f - au) * __ldg(r0) + au * __ldg(r0 + 1)) +
-              av * ((1.f - au) * __ldg(r0 + nu) + au * __ldg(r0 + nu + 1));
+#pragma unroll
+      for (int j = 0; j < kZB; ++j) {
+        const float v = z[j] * mag;
+        const float fv = v / dv_iso + 0.5f * (float)(nv - 1);
+        const int v0 = __float2int_rd(fv);
+        const float av = fv - (float)v0;
+        float val = 0.f;
+        if (u_in && v0 >= 0 && v0 + 1 < nv) {
+          const float* r0 = qp + (size_t)v0 * nu + u0;
+          val = (1.f - av) * ((1.f - au) * __ldg(r0) + au * __ldg(r0 + 1)) +
+                av * ((1.f - au) * __ldg(r0 + nu) + au * __ldg(r0 + nu + 1));
+        }
+        acc[j] = fmaf(mag * mag, val, acc[j]);
       }
-      acc = fmaf(mag * mag, val, acc);
     }
-    vol[i] = acc * scale;
+#pragma unroll
+    for (int j = 0; j < kZB; ++j)
+      if (iz0 + j < nz) vol[((size_t)(iz0 + j) * ny + iy) * nx + ix] = acc[j] * scale;
   }
 }
 
@@ -255,7 +274,7 @@ cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const floa
   if (e != cudaSuccess) return e;
   // full orbit: (dbeta / 2) with dbeta = 2 pi / n_proj
   const float scale = 3.14159265358979f / (float)n_proj;
-  const size_t n = (size_t)nx * ny * nz;
+  const size_t n = (size_t)nx * ny * ((nz + kZB - 1) / kZB);
   k_fdk_backproject<<<blocks_for(n), 256, 0, s>>>(q_tmp, d_cos, d_sin, n_proj, nu, nv, du, dv, sod, nx, ny, nz, dx,
                                                   dy, dz, scale, vol);
   return cudaGetLastError();

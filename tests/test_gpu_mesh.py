@@ -160,3 +160,17 @@ def test_mesh_scatter_histories_one_by_one(gpu, oracle_lib, table_path, tables):
         same += np.abs(g - ref).sum() / max(ref.sum(), 1e-300) < 1e-4
     assert scat >= 100, scat
     assert same >= 0.97 * scat, (same, scat)
+
+
+def test_mesh_tally_modes_and_static_entry(gpu, oracle_lib, table_path, tables):
+    """On meshes every tally mode is the global one (same image to FP64 order); the
+    static-scratch entry point and the autotuner serve voxel volumes only."""
+    mesh, spec = nested_boxes_mesh(), mono_spectrum(60.0)
+    imgs = []
+    for mode in (1, 3, 4):
+        c, _ = _pair(gpu, oracle_lib, table_path, mesh, spec, GEO_NB, tally_mode=mode, tile_u=16, tile_v=16)
+        imgs.append(c.project([0.2], 50_000, 0.5, 4, primary=False)["scatter"].cpu().numpy())
+    for im in imgs[1:]:
+        np.testing.assert_allclose(im, imgs[0], rtol=1e-5, atol=1e-12)
+    with pytest.raises(gpu.MCError, match="STATE"):
+        c.project_scatter_static([0.2], 1000, 0.5, 1)
