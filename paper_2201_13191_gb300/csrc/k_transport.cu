@@ -89,16 +89,13 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 constexpr int kLook = MC_LOOKAHEAD;
 
 template <int LAYOUT>
-__device__ __forceinline__ void gather_ahead(const VolumeView& V, const VoxRay& r, int k0, int n, float h, float ta,
-                                             int& vprev, uint32_t& wprev, uint32_t (&wd)[kLook]) {
+__device__ __forceinline__ void gather_ahead(const VolumeView& V, const VoxRay& r, int k0, float h, float ta,
+                                             uint32_t (&wd)[kLook]) {
   int idx[kLook];
 #pragma unroll
   for (int u = 0; u < kLook; ++u) idx[u] = r.voxel<LAYOUT>(V, fmaf((float)(k0 + u) + 0.5f, h, ta));
 #pragma unroll
   for (int u = 0; u < kLook; ++u) wd[u] = __ldg(V.vox + idx[u]);
-  (void)n;
-  (void)vprev;
-  (void)wprev;
 }
 
 // Optical depth of the fixed-step march x + t w, t in [0, t1] (Sec. II-C.2),
@@ -114,11 +111,10 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   VoxRay r;
   r.set(V, x, w);
   float acc = 0.f, mu = 0.f;
-  int cur = -1, vprev = -1;
-  uint32_t wprev = 0;
+  int cur = -1;
   for (int k0 = 0; k0 < n; k0 += kLook) {
     uint32_t wd[kLook];
-    gather_ahead<LAYOUT>(V, r, k0, n, h, ta, vprev, wprev, wd);
+    gather_ahead<LAYOUT>(V, r, k0, h, ta, wd);
     if (LAYOUT == VOX_LIN) {
       // volume in L2 (the linear layout is chosen while it fits): branch-free,
       // every step reads its material's attenuation from this thread's shared-
@@ -164,11 +160,10 @@ __device__ __forceinline__ float2 march_tau2(const VolumeView& V, float3 x, floa
   VoxRay r;
   r.set(V, x, w);
   float acc_a = 0.f, acc_b = 0.f, mu_a = 0.f, mu_b = 0.f;
-  int cur = -1, vprev = -1;
-  uint32_t wprev = 0;
+  int cur = -1;
   for (int k0 = 0; k0 < n; k0 += kLook) {
     uint32_t wd[kLook];
-    gather_ahead<LAYOUT>(V, r, k0, n, h, ta, vprev, wprev, wd);
+    gather_ahead<LAYOUT>(V, r, k0, h, ta, wd);
 #pragma unroll
     for (int u = 0; u < kLook; ++u) {
       if (k0 + u < n) {
@@ -362,10 +357,6 @@ __device__ __forceinline__ int transport_shared_pixels_dev(const TransportParams
   if (p.tally_mode == TALLY_SHARED) return (int)((size_t)p.n_batches * p.n_angles * p.geo.nu * p.geo.nv);
   if (p.tally_mode == TALLY_TILED) return p.n_batches * p.tile_u * p.tile_v;
   return 0;
-}
-
-__device__ __forceinline__ uint32_t G_npix(const TransportParams& P) {
-  return (uint32_t)P.geo.nu * (uint32_t)P.geo.nv;
 }
 
 // Interaction records queued by the flight phase for the pseudo-particle
@@ -778,11 +769,10 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         VoxRay vr;
         vr.set(V, x, w);
         float tau = 0.f, mu_m = 0.f;
-        int cur = -1, vprev = -1, k = n;
-        uint32_t wprev = 0;
+        int cur = -1, k = n;
         for (int k0 = 0; k0 < n && !hit; k0 += kLook) {
           uint32_t wd[kLook];
-          gather_ahead<LAYOUT>(V, vr, k0, n, hh, ta, vprev, wprev, wd);
+          gather_ahead<LAYOUT>(V, vr, k0, hh, ta, wd);
 #pragma unroll
           for (int u = 0; u < kLook; ++u) {
             if (!hit && k0 + u < n) {
