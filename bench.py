@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
     p.add_argument("--primary-bench", action="store_true", help="primary images of the correction workload")
     p.add_argument("--fdk-bench", action="store_true", help="FDK of 256 projections of the correction workload")
+    p.add_argument("--upsample-bench", action="store_true", help="smoothing + interpolation to 1024 x 2048^2")
     p.add_argument("--primary-speckle", type=float, default=0.0, help="fraction of voxels given another material")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
@@ -1079,6 +1080,43 @@ def run_fdk_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_upsample_bench(args):
+    """Smoothing and dual interpolation of the correction workload (Sec. II-C.3, II-C.4):
+    171 scatter images of 256^2 (every 6th of 1024 angles) -> 1024 angles of 2048^2:
+    milliseconds and output bytes/s against the measured HBM copy peak."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    n_out, NU, n_in, g = args.cor_proj, args.cor_detector, 171, args.cor_sim_grid
+    ctx = mcx.Context(0)
+    ctx.set_geometry(300.0, 600.0, NU, NU, 0.1, 0.1)
+    in_angles = (2.0 * np.pi * np.arange(n_in) / n_in).astype(np.float32)
+    out_angles = (2.0 * np.pi * np.arange(n_out) / n_out).astype(np.float32)
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    img = torch.rand((n_in, g, g), device="cuda", generator=gen)
+    out = torch.empty((n_out, NU, NU), device="cuda")
+    for _ in range(max(1, args.warmup)):
+        ctx.smooth_upsample(img, in_angles, out_angles, NU, NU, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.smooth_upsample(img, in_angles, out_angles, NU, NU, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    written = 4.0 * n_out * NU * NU
+    peak = float(measured_peaks().get("hbm_gbs", 6801.0))
+    line = {"metric": "scatter smoothing + angular lerp + cubic up-sampling, output GB/s", "unit": "GB/s",
+            "value": written / (ms / 1e3) / 1e9, "higher_is_better": True, "dtype": "f32",
+            "config": {"workload": f"{n_in} images of {g}^2 -> {n_out} x {NU}^2", "steps": args.steps},
+            "ms": ms, "roofline": {"bound": "hbm", "peak": peak, "frac": written / (ms / 1e3) / 1e9 / peak,
+                                   "unit": "GB/s"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_mesh_bench(args):
     """Primary images of the triangle-mesh (CAD) cylinder-rod phantom by ray casting
     (eq. Ip with exact path lengths): rays per second through the hierarchy."""
@@ -1155,6 +1193,8 @@ def main():
         run_primary_bench(args)
     elif args.fdk_bench:
         run_fdk_bench(args)
+    elif args.upsample_bench:
+        run_upsample_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

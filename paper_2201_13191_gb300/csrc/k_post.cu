@@ -6,6 +6,8 @@
 // coefficient matrix lives in shared memory.
 #include <stdint.h>
 
+#include <cmath>
+
 #include "mc_internal.h"
 
 namespace mcx {
@@ -123,6 +125,83 @@ __global__ void k_lerp_upsample(const float* __restrict__ in, int nv, int nu, fl
   }
 }
 
+// The same interpolation, separable and row-tiled: a block makes kUpRows
+// output rows of one output angle.  It first interpolates along x (and between
+// the two angles) every low-resolution row those output rows touch, into
+// shared memory (rows[j][X] for input row r0 + j, clamped), then each output
+// pixel takes its four y taps from there.  The sums run in the same order as
+// in k_lerp_upsample (x taps inside, y taps outside), so the images agree bit
+// for bit, with 4 instead of 16 taps per output pixel and the low-resolution
+// reads shared by the block.
+constexpr int kUpRows = 32;
+__global__ void __launch_bounds__(256) k_lerp_upsample_rows(const float* __restrict__ in, int nv, int nu,
+                                                            float* __restrict__ out, int NV, int NU,
+                                                            const int* __restrict__ a0s, const int* __restrict__ a1s,
+                                                            const float* __restrict__ fas, float a) {
+  extern __shared__ __align__(16) float xr[];  // [rows][NU]
+  const int o = blockIdx.y;
+  const int Y0 = blockIdx.x * kUpRows, Y1 = min(Y0 + kUpRows, NV);
+  const float sx = (float)nu / (float)NU, sy = (float)nv / (float)NV;
+  const int r0 = (int)floorf(fmaf((float)Y0 + 0.5f, sy, -0.5f)) - 1;
+  const int r1 = (int)floorf(fmaf((float)(Y1 - 1) + 0.5f, sy, -0.5f)) + 2;
+  const int nrows = r1 - r0 + 1;
+  const float* A = in + (size_t)__ldg(a0s + o) * nu * nv;
+  const float* B = in + (size_t)__ldg(a1s + o) * nu * nv;
+  const float f = __ldg(fas + o);
+  // x pass: a column's taps and weights once, then every row
+  for (int X = threadIdx.x; X < NU; X += blockDim.x) {
+    const float xx = fmaf((float)X + 0.5f, sx, -0.5f);
+    const float xf = floorf(xx);
+    float wx[4];
+    keys_weights(xx - xf, a, wx);
+    int xi[4];
+#pragma unroll
+    for (int kx = 0; kx < 4; ++kx) xi[kx] = min(max((int)xf - 1 + kx, 0), nu - 1);
+    for (int j = 0; j < nrows; ++j) {
+      const size_t ro = (size_t)min(max(r0 + j, 0), nv - 1) * nu;
+      float racc = 0.f;
+#pragma unroll
+      for (int kx = 0; kx < 4; ++kx) {
+        const float v = fmaf(f, __ldg(B + ro + xi[kx]) - __ldg(A + ro + xi[kx]), __ldg(A + ro + xi[kx]));
+        racc = fmaf(wx[kx], v, racc);
+      }
+      xr[j * NU + X] = racc;
+    }
+  }
+  __syncthreads();
+  // y pass: a row's weights once, then four consecutive outputs per thread (one 16-byte store)
+  const bool vec = (NU & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  for (int Y = Y0; Y < Y1; ++Y) {
+    const float yy = fmaf((float)Y + 0.5f, sy, -0.5f);
+    const float yf = floorf(yy);
+    float wy[4];
+    keys_weights(yy - yf, a, wy);
+    const float* rows = xr + ((int)yf - 1 - r0) * NU;
+    float* dst = out + ((size_t)o * NV + Y) * NU;
+    if (vec) {
+      for (int X = 4 * threadIdx.x; X < NU; X += 4 * blockDim.x) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+          const float4 v = *reinterpret_cast<const float4*>(rows + ky * NU + X);
+          acc[0] = fmaf(wy[ky], v.x, acc[0]);
+          acc[1] = fmaf(wy[ky], v.y, acc[1]);
+          acc[2] = fmaf(wy[ky], v.z, acc[2]);
+          acc[3] = fmaf(wy[ky], v.w, acc[3]);
+        }
+        *reinterpret_cast<float4*>(dst + X) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      }
+    } else {
+      for (int X = threadIdx.x; X < NU; X += blockDim.x) {
+        float acc = 0.f;
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) acc = fmaf(wy[ky], rows[ky * NU + X], acc);
+        dst[X] = acc;
+      }
+    }
+  }
+}
+
 int grid_for(size_t n, int block) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -150,6 +229,19 @@ cudaError_t launch_sg_cols(const float* in, float* out, int n_img, int h, int w,
 
 cudaError_t launch_lerp_upsample(const float* in, int nv, int nu, float* out, int n_out, int NV, int NU,
                                  const int* a0, const int* a1, const float* fa, float cubic_a, cudaStream_t s) {
+  // row-tiled form when the low-resolution rows one block touches fit in shared memory
+  const double sy = (double)nv / (double)NV;
+  const int rows = (int)std::ceil((kUpRows - 1) * sy) + 5;
+  const size_t smem = (size_t)rows * NU * 4;
+  if (n_out <= 65535 && smem <= 160 * 1024) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_lerp_upsample_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_lerp_upsample_rows<<<dim3((NV + kUpRows - 1) / kUpRows, n_out), 256, smem, s>>>(in, nv, nu, out, NV, NU, a0, a1,
+                                                                                        fa, cubic_a);
+    return cudaGetLastError();
+  }
   const size_t total = (size_t)n_out * NV * ((NU + 3) / 4);
   k_lerp_upsample<<<grid_for(total, 256), 256, 0, s>>>(in, nv, nu, out, n_out, NV, NU, a0, a1, fa, cubic_a);
   return cudaGetLastError();
