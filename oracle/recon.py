@@ -5,7 +5,8 @@ Sec. II-E: line integrals a = -ln(I/I0); FDK for a circular orbit (cosine
 pre-weighting, discrete Ram-Lak ramp filter in the isocentre plane,
 voxel-driven backprojection with bilinear interpolation and the (D/(D-x.n))^2
 weight, dbeta/2 for a full orbit); multi-level Otsu thresholds by exhaustive
-search of the between-class variance; and eq. (Correction).
+search of the between-class variance; eq. (Correction); and the down-sampling
+of the segmented volume for the Monte Carlo step (Sec. II-C.2, Sec. II-E).
 """
 
 from __future__ import annotations
@@ -94,3 +95,27 @@ def otsu(hist, classes):
 def correct(a, ip, is_):
     """Eq. (Correction): c = a - ln(Ip / (Ip + Is))."""
     return a - np.log(ip / (ip + is_))
+
+
+def bin_volume(mat, rho, murho):
+    """Down-sampling of a segmented volume by 2 along each axis for the Monte Carlo step (Sec. II-C.2:
+    the number of voxels is down-sampled to cut the ray-tracing time; Sec. II-E).
+
+    mat [nz][ny][nx] material ids, rho the same shape in g/cm^3 (FP64), murho[m] the mass attenuation of
+    material m at the correction's effective energy; even dimensions.  Each 2x2x2 block becomes one voxel of
+    the material holding the block's largest mass (ties to the lower id), with the density that keeps the
+    block's summed attenuation at the effective energy:
+        rho_b = sum_v murho[m_v] rho_v / (8 murho[m_b]).
+    Returns (mat_b, rho_b) as FP64."""
+    nz, ny, nx = mat.shape
+    if nx % 2 or ny % 2 or nz % 2:
+        raise ValueError("even dimensions needed")
+    nm = len(murho)
+    blk = lambda t: t.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).transpose(0, 2, 4, 1, 3, 5).reshape(
+        nz // 2, ny // 2, nx // 2, 8)
+    m8, r8 = blk(mat.astype(np.int64)), blk(np.asarray(rho, dtype=np.float64))
+    mass = np.stack([np.where(m8 == m, r8, 0.0).sum(-1) for m in range(nm)], -1)
+    mat_b = np.argmax(mass, axis=-1)  # first maximum: the lowest id on ties
+    mu = (np.asarray(murho, dtype=np.float64)[m8] * r8).sum(-1)
+    rho_b = mu / (8.0 * np.asarray(murho, dtype=np.float64)[mat_b])
+    return mat_b.astype(np.uint8), rho_b

@@ -2,6 +2,7 @@
 FDK of analytic projections of a uniform cylinder, Otsu thresholds, eq. (Correction)."""
 
 import numpy as np
+import pytest
 
 from oracle import recon
 
@@ -76,3 +77,39 @@ def test_correction_formula():
     a = -np.log((ip + is_) / i0)
     np.testing.assert_allclose(recon.correct(a, ip, is_), -np.log(ip / i0), atol=1e-12)
     np.testing.assert_allclose(recon.correct(a, ip, np.zeros(100)), a, atol=0)
+
+
+def test_bin_volume_pins():
+    """2x2x2 down-sampling for the Monte Carlo step: a uniform block keeps its material and density; the
+    attenuation at the effective energy is conserved block by block; the block's material is the one with
+    the largest mass, ties to the lower id."""
+    from oracle.recon import bin_volume
+
+    murho = np.array([0.19, 0.206, 0.2, 0.278, 0.29])
+    rng = np.random.default_rng(4)
+    mat = rng.choice(np.array([0, 1, 3]), size=(6, 8, 4)).astype(np.uint8)
+    rho = np.where(mat == 0, 0.0012, np.where(mat == 1, 1.0, 2.7)) * rng.uniform(0.8, 1.2, mat.shape)
+    mb, rb = bin_volume(mat, rho, murho)
+    assert mb.shape == (3, 4, 2) and rb.shape == (3, 4, 2)
+    mu_f = (murho[mat] * rho).reshape(3, 2, 4, 2, 2, 2).sum(axis=(1, 3, 5))
+    np.testing.assert_allclose(8.0 * murho[mb] * rb, mu_f, rtol=1e-12)
+    # the largest mass per block, by brute force
+    for z in range(3):
+        for y in range(4):
+            for x in range(2):
+                m = mat[2 * z:2 * z + 2, 2 * y:2 * y + 2, 2 * x:2 * x + 2].ravel()
+                r = rho[2 * z:2 * z + 2, 2 * y:2 * y + 2, 2 * x:2 * x + 2].ravel()
+                masses = {k: r[m == k].sum() for k in set(m.tolist())}
+                best = max(sorted(masses), key=lambda k: masses[k])
+                assert mb[z, y, x] == best
+    # uniform blocks are unchanged; ties go to the lower id
+    u = np.full((2, 2, 2), 3, np.uint8)
+    mb, rb = bin_volume(u, np.full((2, 2, 2), 2.5), murho)
+    assert mb[0, 0, 0] == 3 and abs(rb[0, 0, 0] - 2.5) < 1e-15
+    t = np.zeros((2, 2, 2), np.uint8)
+    t.ravel()[:4] = 1
+    t.ravel()[4:] = 2
+    mb, _ = bin_volume(t, np.ones((2, 2, 2)), murho)
+    assert mb[0, 0, 0] == 1
+    with pytest.raises(ValueError):
+        bin_volume(np.zeros((3, 2, 2), np.uint8), np.ones((3, 2, 2)), murho)
