@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--cor-meas-photons", type=float, default=1e8)
     p.add_argument("--cor-total-photons", type=float, default=1e10)
     p.add_argument("--cor-sim-grid", type=int, default=256)
+    p.add_argument("--cor-mc-bin", type=int, choices=[0, 2], default=0,
+                   help="2: Monte Carlo on the segmented volume down-sampled by 2 per axis (the paper's speed-up)")
     p.add_argument("--cor-sim-angles", type=int, default=180)
     p.add_argument("--cor-sim-photons", type=float, default=1e6)
     p.add_argument("--cor-iters", type=int, default=3)
@@ -824,7 +826,7 @@ def run_correct_eval(args):
     prm = mcx.CorrectParams(nx=nvx, ny=nvx, nz=nvx, dx=dv, dy=dv, dz=dv, sim_nu=args.cor_sim_grid,
                             sim_nv=args.cor_sim_grid, sim_angle_stride=stride, photons=int(args.cor_sim_photons),
                             step_mm=step, seed=11, classes=3, class_material=(0, 1, 3), class_density0=0.001205,
-                            e_eff_keV=60.0, mu_lo=-0.01, mu_hi=0.12, primary_full_res=1)
+                            e_eff_keV=60.0, mu_lo=-0.01, mu_hi=0.12, primary_full_res=1, mc_bin=args.cor_mc_bin)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     out, v_cor, secs = ctx.correct_iter(raw, I0, angles, NU, NV, args.cor_iters, prm)
@@ -873,6 +875,7 @@ def run_correct_eval(args):
                    "measurements": f"exact primary + Monte Carlo scatter at {len(meas_angles)} angles x "
                                    f"{args.cor_meas_photons:.0e} photons on {g}^2, smoothed and interpolated; Poisson "
                                    f"noise with {args.cor_total_photons:.0e} photons per projection",
+                   "mc_volume": f"{nvx // 2}^3 x {2 * dv} mm (down-sampled)" if args.cor_mc_bin == 2 else f"{nvx}^3",
                    "iteration": f"FDK to {nvx}^3, Otsu 3 classes, primary on the full panel, scatter at "
                                 f"{len(range(0, n_proj, stride))} angles x {args.cor_sim_photons:.0e} photons on "
                                 f"{args.cor_sim_grid}^2, Savitzky-Golay, angular lerp + cubic up-sampling, eq. Correction",

@@ -226,10 +226,26 @@ typedef struct mc_correct_params {
   float mu_lo, mu_hi;
   int primary_full_res; /* 1: primary computed on the NU x NV panel itself (exact, cheap); 0: on the
                            simulation grid and up-sampled with the scatter, as the paper does */
+  int mc_bin;           /* 2: the Monte Carlo scatter (and the low-resolution primary) runs on the segmented
+                           volume down-sampled by 2 per axis (mc_bin_volume; even nx, ny, nz), as the paper
+                           does to cut the ray-tracing time; 0 or 1: on the full volume */
 } mc_correct_params;
 int mc_correct_iter(mc_ctx *ctx, const float *raw_I, const float *I0, int n_proj, const float *angles_rad, int NU,
                     int NV, int n_iter, const mc_correct_params *prm, float *corrected_a_out, float *volume_out,
                     double *iter_seconds, void *stream);
+
+/* Down-sampling of a segmented volume for the Monte Carlo step (Sec. II-C.2:
+ * the number of voxels is down-sampled to cut the ray-tracing time; Sec.
+ * II-E).  Device mat [nz][ny][nx] (ids < the table's materials) and rho
+ * (binary16 g/cm^3), even dimensions -> mat_out, rho_out [nz/2][ny/2][nx/2]
+ * (device, caller-owned): each 2x2x2 block becomes one voxel of the material
+ * holding the block's largest mass (ties to the lower id), with the density
+ * that keeps the block's summed attenuation at e_eff_keV (tables linear
+ * between nodes): rho = sum_v mu/rho(m_v) rho_v / (8 mu/rho(m)).  Enqueued on
+ * `stream`.  Errors: STATE (no tables), INVALID_ARG (odd dimension, energy
+ * outside the table), CUDA/OOM. */
+int mc_bin_volume(mc_ctx *ctx, const uint8_t *mat, const uint16_t *rho, int nx, int ny, int nz, float e_eff_keV,
+                  uint8_t *mat_out, uint16_t *rho_out, void *stream);
 
 /* Plain FDK reconstruction (step 1 above) of line-integral projections p
  * (device [n_proj][NV][NU], the context's panel geometry) into vol (device

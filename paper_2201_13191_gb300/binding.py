@@ -34,7 +34,7 @@ EXPORTED = [
     "mc_load_volume", "mc_set_spectrum", "mc_set_geometry", "mc_project", "mc_project_histories",
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
-    "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk",
+    "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk", "mc_bin_volume",
     "mc_probe_gather", "mc_set_detector_response", "mc_probe_mma", "mc_load_mesh",
 ]
 
@@ -73,6 +73,7 @@ class CorrectParams(C.Structure):
         ("e_eff_keV", C.c_float),
         ("mu_lo", C.c_float), ("mu_hi", C.c_float),
         ("primary_full_res", C.c_int),
+        ("mc_bin", C.c_int),
     ]
 
 
@@ -144,6 +145,7 @@ def library():
         L.mc_nn_conv3x3_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
         L.mc_correct_iter.argtypes = [P, vp, vp, i, vp, i, i, i, C.POINTER(CorrectParams), vp, vp, vp, vp]
         L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
+        L.mc_bin_volume.argtypes = [P, vp, vp, i, i, i, f, vp, vp, vp]
         L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
         L.mc_set_detector_response.argtypes = [P, vp, i]
         L.mc_probe_mma.argtypes = [i, i, i, vp, vp]
@@ -402,6 +404,17 @@ class Context:
         self._check(self.L.mc_fdk(self.h, _t_ptr(p.contiguous()), len(a), _np_ptr(a), NU, NV, nx, ny, nz, dx, dy, dz,
                                   _t_ptr(vol), _stream_handle(stream)))
         return vol
+
+    def bin_volume(self, mat, rho, e_eff_keV, stream=None):
+        """2x2x2 down-sampling of a segmented volume (device uint8 mat, int16/uint16 binary16 rho, [nz][ny][nx],
+        even dims) for the Monte Carlo step -> (mat, rho) device tensors [nz/2][ny/2][nx/2]."""
+        torch = self.torch
+        nz, ny, nx = mat.shape
+        mo = torch.empty((nz // 2, ny // 2, nx // 2), dtype=torch.uint8, device=mat.device)
+        ro = torch.empty((nz // 2, ny // 2, nx // 2), dtype=torch.int16, device=mat.device)
+        self._check(self.L.mc_bin_volume(self.h, _t_ptr(mat.contiguous()), _t_ptr(rho.contiguous()), nx, ny, nz,
+                                         float(e_eff_keV), _t_ptr(mo), _t_ptr(ro), _stream_handle(stream)))
+        return mo, ro
 
     def correct_iter(self, raw_I, I0, angles, NU, NV, n_iter, prm, stream=None):
         """Iterative scatter correction; returns (corrected line integrals, last volume, seconds per iteration)."""

@@ -241,6 +241,38 @@ __global__ void k_segment(const float* __restrict__ vol, size_t n, float lo, flo
   }
 }
 
+// Down-sampling by 2 per axis for the Monte Carlo step (Sec. II-C.2, II-E):
+// each 2x2x2 block becomes one voxel of the material with the block's largest
+// mass (ties to the lower id) and the density that keeps the block's summed
+// attenuation at the effective energy, sum_v murho[m_v] rho_v / (8 murho[m_b]).
+__global__ void k_bin_volume(const uint8_t* __restrict__ mat, const uint16_t* __restrict__ rho, int nx, int ny,
+                             int nz, const float* __restrict__ murho, int n_mat, uint8_t* __restrict__ mat_b,
+                             uint16_t* __restrict__ rho_b) {
+  const int bx = nx / 2, by = ny / 2, bz = nz / 2;
+  const size_t n = (size_t)bx * by * bz;
+  for (size_t i = gtid(); i < n; i += gstride()) {
+    const int x = (int)(i % bx), y = (int)((i / bx) % by), z = (int)(i / ((size_t)bx * by));
+    float mass[kMaxMat];
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) mass[m] = 0.f;
+    float mu = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t v = ((size_t)(2 * z + (q >> 2)) * ny + (2 * y + ((q >> 1) & 1))) * nx + (2 * x + (q & 1));
+      const int m = mat[v];
+      const float r = __half2float(__ushort_as_half(rho[v]));
+#pragma unroll
+      for (int k = 0; k < kMaxMat; ++k) mass[k] += (k == m) ? r : 0.f;
+      mu = fmaf(__ldg(murho + m), r, mu);
+    }
+    int best = 0;
+    for (int m = 1; m < n_mat; ++m)
+      if (mass[m] > mass[best]) best = m;
+    mat_b[i] = (uint8_t)best;
+    rho_b[i] = __half_as_ushort(__float2half_rn(mu / (8.f * __ldg(murho + best))));
+  }
+}
+
 // c = a - ln(Ip / (Ip + Is)) (eq. Correction).
 __global__ void k_correct(const float* __restrict__ a, const float* __restrict__ ip, const float* __restrict__ is,
                           float is_scale, size_t n, float* __restrict__ c) {
@@ -251,6 +283,14 @@ __global__ void k_correct(const float* __restrict__ a, const float* __restrict__
 }
 
 }  // namespace
+
+cudaError_t recon_bin_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, const float* murho,
+                             int n_mat, uint8_t* mat_b, uint16_t* rho_b, cudaStream_t s) {
+  if (nx % 2 || ny % 2 || nz % 2 || n_mat < 1 || n_mat > kMaxMat) return cudaErrorInvalidValue;
+  const size_t n = (size_t)(nx / 2) * (ny / 2) * (nz / 2);
+  k_bin_volume<<<blocks_for(n), 256, 0, s>>>(mat, rho, nx, ny, nz, murho, n_mat, mat_b, rho_b);
+  return cudaGetLastError();
+}
 
 cudaError_t recon_log_norm(const float* I, const float* I0, size_t img, size_t n, float* a, cudaStream_t s) {
   k_log_norm<<<blocks_for(n), 256, 0, s>>>(I, I0, img, n, a);

@@ -1198,6 +1198,46 @@ int mc_fdk(mc_ctx* ctx, const float* p, int n_proj, const float* angles, int NU,
   return MC_OK;
 }
 
+namespace {
+// Total mass attenuation (cm^2/g) of every table material at energy E (linear between nodes).
+std::vector<float> murho_at(const mc_ctx* ctx, double E) {
+  const double x = (E - ctx->E0) / ctx->dE;
+  const int i = std::max(0, std::min((int)std::floor(x), ctx->n_E - 2));
+  const double f = x - i;
+  std::vector<float> out(ctx->n_mat);
+  for (int m = 0; m < ctx->n_mat; ++m) {
+    auto tot = [&](int j) {
+      const size_t q = (size_t)m * ctx->n_E + j;
+      return ctx->pe[q] + ctx->in[q] + ctx->co[q];
+    };
+    out[m] = (float)(tot(i) + f * (tot(i + 1) - tot(i)));
+  }
+  return out;
+}
+}  // namespace
+
+int mc_bin_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, float e_eff_keV,
+                  uint8_t* mat_out, uint16_t* rho_out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "tables not loaded");
+  if (!mat || !rho || !mat_out || !rho_out || nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2)
+    return fail(ctx, MC_ERR_INVALID_ARG, "bin_volume needs even dimensions and device buffers");
+  if (!(e_eff_keV >= ctx->E0) || !(e_eff_keV <= ctx->E0 + ctx->dE * (ctx->n_E - 1)))
+    return fail(ctx, MC_ERR_INVALID_ARG, "energy outside the table");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<float> mr = murho_at(ctx, e_eff_keV);
+  float* d = nullptr;
+  CK(cudaMallocAsync((void**)&d, mr.size() * 4, s), "bin_volume table");
+  cudaError_t e = cudaMemcpyAsync(d, mr.data(), mr.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = recon_bin_volume(mat, rho, nx, ny, nz, d, ctx->n_mat, mat_out, rho_out, s);
+  cudaFreeAsync(d, s);
+  // the host table must outlive the copy
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bin_volume");
+  return MC_OK;
+}
+
 int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj, const float* angles, int NU, int NV,
                     int n_iter, const mc_correct_params* prm, float* c_out, float* vol_out, double* iter_seconds,
                     void* stream) {
@@ -1211,6 +1251,9 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
       P.sim_angle_stride < 1 || P.photons < 1 || !(P.step_mm > 0) || (P.classes != 2 && P.classes != 3) ||
       !(P.mu_hi > P.mu_lo) || !(P.e_eff_keV >= ctx->E0) || !(P.e_eff_keV <= ctx->E0 + ctx->dE * (ctx->n_E - 1)))
     return fail(ctx, MC_ERR_INVALID_ARG, "bad correction parameters");
+  const bool binned = P.mc_bin == 2;
+  if (P.mc_bin < 0 || P.mc_bin > 2 || (binned && (P.nx % 2 || P.ny % 2 || P.nz % 2)))
+    return fail(ctx, MC_ERR_INVALID_ARG, "mc_bin must be 0, 1 or 2 (even volume dimensions)");
   for (int k = 0; k < P.classes; ++k)
     if (P.class_material[k] < 0 || P.class_material[k] >= ctx->n_mat)
       return fail(ctx, MC_ERR_INVALID_ARG, "class material outside the table");
@@ -1249,7 +1292,12 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
   float* is_sim = (float*)alloc((size_t)n_sim * simg * 4);
   unsigned int* hist = (unsigned int*)alloc(256 * 4);
   int* thr = (int*)alloc(2 * 4 + 3 * 4 + 6 * 4);
-  if (bufs.size() != 11) return release(fail(ctx, MC_ERR_OOM, "correction buffers"));
+  const size_t nbin = binned ? nvox / 8 : 1;
+  uint8_t* mat_b = (uint8_t*)alloc(nbin);
+  uint16_t* rho_b = (uint16_t*)alloc(nbin * 2);
+  float* d_murho = (float*)alloc((size_t)ctx->n_mat * 4);
+  if (bufs.size() != 14) return release(fail(ctx, MC_ERR_OOM, "correction buffers"));
+  const std::vector<float> murho_eff = murho_at(ctx, P.e_eff_keV);
   int* d_cls_mat = thr + 2;
   float* d_cls_murho = reinterpret_cast<float*>(thr + 5);
   float* d_cls_rho0 = d_cls_murho + 3;
@@ -1273,6 +1321,8 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
     cmu[4] = cmu[5] = 0.f;
     cudaError_t e = cudaMemcpyAsync(d_cls_mat, cm, sizeof(cm), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cls_murho, cmu, sizeof(cmu), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_murho, murho_eff.data(), murho_eff.size() * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return release(cuda_fail(ctx, e, "class tables"));
   }
   // geometry of the simulation grid over the same panel
@@ -1301,6 +1351,14 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
         restore();
         return release(rc);
       }
+    }
+    if (binned) {
+      // the Monte Carlo step runs on the volume down-sampled by 2 per axis (Sec. II-C.2, II-E)
+      e = recon_bin_volume(mat, rho, P.nx, P.ny, P.nz, d_murho, ctx->n_mat, mat_b, rho_b, s);
+      if (e != cudaSuccess) return release(cuda_fail(ctx, e, "down-sampling"));
+      rc = mc_load_volume(ctx, mat_b, rho_b, P.nx / 2, P.ny / 2, P.nz / 2, 2.f * P.dx, 2.f * P.dy, 2.f * P.dz, 1,
+                          stream);
+      if (rc) return release(rc);
     }
     rc = mc_set_geometry(ctx, sod, sdd, P.sim_nu, P.sim_nv, spu, spv);
     if (rc) return release(rc);

@@ -218,6 +218,10 @@ cudaError_t recon_fdk(const float* p, int n_proj, const float* d_cos, const floa
 cudaError_t recon_otsu_segment(const float* vol, size_t n, float lo, float hi, int classes, const int* d_cls_mat,
                                const float* d_cls_murho, const float* d_cls_rho0, float rho_max, unsigned int* d_hist,
                                int* d_thr, uint8_t* mat, uint16_t* rho, cudaStream_t s);
+// 2x2x2 down-sampling of a segmented volume (even dims): largest-mass material, attenuation-conserving density
+// at the effective energy (murho: device [n_mat] mass attenuation there).
+cudaError_t recon_bin_volume(const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, const float* murho,
+                             int n_mat, uint8_t* mat_b, uint16_t* rho_b, cudaStream_t s);
 // c = a - ln(ip / (ip + is_scale * is)): is_scale converts the scatter image's
 // per-pixel values to the panel's pixel area when it was simulated on another grid.
 cudaError_t recon_correct(const float* a, const float* ip, const float* is, float is_scale, size_t n, float* c,
