@@ -425,7 +425,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
   // ---- kernel parameters (zeroed first: they also form the graph key)
   PrimaryParams pp;
   TransportParams tp;
-  std::memset(&pp, 0, sizeof(pp));
+  std::memset((void*)&pp, 0, sizeof(pp));
   std::memset((void*)&tp, 0, sizeof(tp));
   int grid = 0, block = 0;
   if (primary_out) {
