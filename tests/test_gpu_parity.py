@@ -415,3 +415,22 @@ def test_smoothing_windows_and_edges(gpu):
         out = c.smooth_upsample(torch.tensor(img, dtype=torch.float32, device="cuda"), [0.0, 3.0], [0.0, 3.0], 37, 31)
         for k in range(2):
             np.testing.assert_allclose(out[k].cpu().numpy(), post.sg_smooth_2d(img[k], win, order), atol=3e-5)
+
+
+@pytest.mark.parametrize("shape", [(96, 700, 64, 1024), (64, 96, 512, 384), (96, 130, 64, 100)])
+def test_upsample_tiled_and_fallback_paths(gpu, shape):
+    """The row-tiled up-sampling (its low-resolution rows fit in shared memory) and the
+    per-pixel kernel it falls back to (96 -> 64 rows at 1024 columns would need 52 rows
+    of 4 KB) both match the oracle's angle lerp + Keys cubic."""
+    from oracle import post
+
+    torch = pytest.importorskip("torch")
+    nv, nu, NV, NU = shape
+    rng = np.random.default_rng(12)
+    imgs = rng.normal(1.0, 0.1, size=(2, nv, nu)).astype(np.float32)
+    ia = np.array([0.0, 3.0], np.float32)
+    oa = np.array([1.3], np.float32)
+    c = gpu.Context(0, denoise_mode=2)
+    out = c.smooth_upsample(torch.tensor(imgs, device="cuda"), ia, oa, NU, NV).cpu().numpy()
+    ref = post.smooth_upsample(imgs, ia, oa, NU, NV, a=-0.5, smooth=False)
+    np.testing.assert_allclose(out, ref, rtol=2e-5, atol=2e-5)
