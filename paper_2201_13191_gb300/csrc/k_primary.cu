@@ -12,7 +12,10 @@ namespace mcx {
 namespace {
 
 constexpr float kPi = 3.14159265358979f;
-constexpr int kAhead = 8;  // voxel words in flight per ray
+#ifndef MC_PRIMARY_AHEAD
+#define MC_PRIMARY_AHEAD 16
+#endif
+constexpr int kAhead = MC_PRIMARY_AHEAD;  // voxel words in flight per ray
 
 // FP16 bit pattern -> value * 2^24 as an exact integer (finite, non-negative inputs).
 __device__ __forceinline__ unsigned long long fp16_fixed24(uint16_t b) {
