@@ -16,9 +16,12 @@
  *     e_u = (-sin b, cos b, 0), e_v = (0, 0, 1); images are [nv][nu] row
  *     major, pixel (i, j) centred at (i - (nu-1)/2) pu e_u + (j - (nv-1)/2) pv e_v
  *     from the panel centre;
- *   - detector response eta(E) = E (energy integrating); both images are the
- *     expected detector energy per pixel per source photon emitted into 4 pi
- *     (keV), the source being collimated to the detector pyramid;
+ *   - detector response eta(E) = E (energy integrating) unless
+ *     mc_set_detector_response sets another; both images are the expected
+ *     detector signal per pixel per source photon emitted into 4 pi (keV for
+ *     eta = E), the source being collimated to the detector pyramid;
+ *   - the object is a voxel volume (mc_load_volume) or closed triangulated
+ *     bodies (mc_load_mesh), whichever was loaded last;
  *   - device pointers belong to the caller, who keeps ownership; the library
  *     copies what it needs at load time and owns only its internal buffers;
  *   - every call returns MC_OK or a negative status; mc_last_error() gives
