@@ -6,10 +6,14 @@
 // n_split pseudo-particles aimed at random pixels (arXiv 2201.13191 Sec. II-A,
 // eqs. Th, pmueforIncoherent, pmueforcoherent, Is; Sec. II-C.1, II-C.2).
 //
-// Each thread runs whole histories; history h of angle a draws its random
-// numbers from Philox4x32-10 keyed by (seed, a, h), in a fixed order, so any
-// history can be recomputed on its own.  The cross-section tables are staged
-// once per block into shared memory by a bulk asynchronous copy (TMA engine,
+// Wavefront structure: each thread carries one photon's walk and runs one free
+// flight per iteration; an interaction queues a record in shared memory, and
+// the block then shares out all queued pseudo-particles among its warps
+// (longest chords first) before the next flight.  History h of angle a draws
+// its random numbers from Philox4x32-10 keyed by (seed, a, h), in a fixed
+// order, with each pseudo-particle on its own counter block, so any history
+// can be recomputed on its own.  The cross-section tables are staged once per
+// block into shared memory by a bulk asynchronous copy (TMA engine,
 // cp.async.bulk) completing on an mbarrier.
 #include <cuda_fp16.h>
 #include <stdint.h>
