@@ -1,9 +1,11 @@
 // Smoothing and dual interpolation of the simulated scatter (arXiv 2201.13191
 // Sec. II-C.3 and II-C.4): separable Savitzky-Golay smoothing, then linear
 // interpolation between simulated angles fused with separable Keys cubic
-// up-sampling.  All passes are bandwidth bound: each thread owns consecutive
-// outputs along the fastest axis so loads and stores coalesce, and the small
-// coefficient matrix lives in shared memory.
+// up-sampling.  All passes are bandwidth bound: the smoothing keeps its small
+// coefficient matrix in shared memory and each thread owns consecutive outputs
+// along the fastest axis; the up-sampling runs separable and row-tiled (the
+// low-resolution rows a block needs are interpolated along x into shared
+// memory once), with a per-pixel fallback when those rows do not fit.
 #include <stdint.h>
 
 #include <cmath>

@@ -2,7 +2,9 @@
 // ray from the source to the pixel centre is marched with the fixed step
 // (Sec. II-C.2); the per-material column masses rho*L are summed exactly in
 // 64-bit fixed point (each FP16 density is an integer multiple of 2^-24), and
-// the spectrum sum S(E) eta(E) exp(-mu(E) L) runs over the energy bins.
+// the spectrum sum S(E) eta(E) exp(-mu(E) L) runs over the energy bins.  The
+// file also builds the packed voxel words and measures, at volume load, how
+// often neighbouring voxels change material.
 #include <cuda_fp16.h>
 #include <stdint.h>
 

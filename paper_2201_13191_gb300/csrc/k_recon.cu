@@ -2,7 +2,8 @@
 // flowchart, eq. Correction): conversion of intensities to line integrals,
 // FDK (cone-beam filtered backprojection) for the circular orbit of this
 // library's geometry, multi-level Otsu segmentation, conversion of the
-// segmented volume to material ids and densities, and the correction
+// segmented volume to material ids and densities, its 2x2x2 down-sampling for
+// the Monte Carlo step (Sec. II-C.2), and the correction
 // c = a - ln(Ip / (Ip + Is)).
 #include <cuda_fp16.h>
 #include <stdint.h>

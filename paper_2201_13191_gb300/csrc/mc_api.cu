@@ -1,7 +1,8 @@
 // C ABI of the GB300 Monte Carlo scatter forward projection (include/mc.h):
 // context, argument validation, table/volume/spectrum staging, launches.
 // Host code only marshals inputs and sequences kernels; every step of the
-// method runs in the kernels of k_transport.cu, k_primary.cu and k_post.cu.
+// method runs in the kernels of k_transport.cu, k_primary.cu, k_mesh.cu,
+// k_post.cu and k_recon.cu (and the denoiser's in k_conv.cu / k_nn.cu).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
