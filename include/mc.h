@@ -200,7 +200,9 @@ int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_a
  *   3. Monte Carlo on a sim_nu x sim_nv grid over the same panel: scatter
  *      (photons histories each) at every sim_angle_stride-th angle; the
  *      primary at every angle, on the same grid or (primary_full_res) on the
- *      NU x NV panel;
+ *      NU x NV panel; with mc_bin = 2 the Monte Carlo (and the primary on the
+ *      simulation grid) runs on the segmented volume down-sampled by 2 per
+ *      axis (mc_bin_volume), the full-panel primary on the full volume;
  *   4. smoothing (options.denoise_mode) of the scatter, linear interpolation
  *      to every angle and cubic up-sampling to NU x NV (of the primary too
  *      unless it was computed at full resolution);
@@ -212,7 +214,8 @@ int mc_smooth_upsample(mc_ctx *ctx, const float *in, int n_in, const float *in_a
  * corrected projections when n_iter >= 1); iter_seconds (host [n_iter],
  * nullable) the wall time of each iteration.  angles_rad (host) must cover a
  * full orbit in increasing order.  The context's volume is replaced by the
- * segmented reconstruction.  Allocates temporary device buffers.
+ * segmented reconstruction (its down-sampled form with mc_bin = 2).
+ * Allocates temporary device buffers.
  * Errors: STATE, INVALID_ARG, CUDA/OOM, and those of mc_project. */
 typedef struct mc_correct_params {
   int nx, ny, nz;
