@@ -22,7 +22,11 @@
  *     roulette, summed per eq. (Is);
  *   - the same histories through closed triangulated bodies (the CAD surface
  *     model of Sec. II-A) with exact path lengths: free flights over the
- *     sorted surface crossings, point-detector attenuation by exact chords.
+ *     sorted surface crossings, point-detector attenuation by exact chords;
+ *   - options: a detector response table (Sec. II-D.2), expected-value
+ *     scoring over the interaction type (Sec. II-C.1), the bound-electron
+ *     scattering function and Doppler broadening (Sec. II-A), and tile-
+ *     stratified point-detector pixels.
  *
  * Readings of the paper that it implements (all listed in the design notes):
  * lengths in mm, energies in keV, eta(E) = E unless a detector response
