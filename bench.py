@@ -96,11 +96,15 @@ def parse():
     p.add_argument("--cor-iters", type=int, default=3)
     p.add_argument("--conv-size", type=int, default=256)
     p.add_argument("--conv-batch", type=int, default=8)
-    p.add_argument("--train-phantoms", type=int, default=96)
-    p.add_argument("--train-angles", type=int, default=4)
-    p.add_argument("--train-steps", type=int, default=1500)
+    p.add_argument("--train-phantoms", type=int, default=200)
+    p.add_argument("--train-angles", type=int, default=10)
+    p.add_argument("--train-inputs", type=float, nargs="+", default=[1e6])
+    p.add_argument("--target-photons", type=float, default=1e9)
+    p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--save-weights", default=None, help="write the trained denoiser here (--denoise-eval)")
     p.add_argument("--ref-photons", type=float, default=1e10)
-    p.add_argument("--eval-angles", type=int, default=4)
+    p.add_argument("--eval-angles", type=int, default=360)
+    p.add_argument("--no-c4", action="store_true", help="skip the denoised-scatter figures of the default run")
     return p.parse_args()
 
 
@@ -209,14 +213,15 @@ def _oracles(tp, wl, threads):
     return orcs
 
 
-def _oracle_histories(orcs, wl, n_photons, h0, per_thread):
-    """Histories h0 .. h0 + threads x per_thread on all oracles at once (the
-    oracle's C calls release the GIL, so threads run in parallel)."""
+def _oracle_blocks(orcs, wl, n_photons, blocks, block):
+    """Histories [b, b + block) for every start b in `blocks`, dealt round-robin
+    to the oracles and run on all of them at once (the oracle's C calls release
+    the GIL, so threads run in parallel)."""
     from concurrent.futures import ThreadPoolExecutor
 
     def run(i):
-        a = h0 + i * per_thread
-        orcs[i].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], a, a + per_thread)
+        for b in blocks[i :: len(orcs)]:
+            orcs[i].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], int(b), int(min(b + block, n_photons)))
 
     if len(orcs) == 1:
         run(0)
@@ -225,29 +230,46 @@ def _oracle_histories(orcs, wl, n_photons, h0, per_thread):
         list(ex.map(run, range(len(orcs))))
 
 
+def spread_blocks(n_photons, n_blocks, block, phase=0.0):
+    """Starts of n_blocks history blocks spread evenly over [0, n_photons).
+
+    Histories are stratified over the spectrum's energy bins in index order
+    (the lowest bins first), so a sample must span the whole range: block k
+    starts at (k + phase) n_photons / n_blocks (phase in [0, 1))."""
+    n_blocks = max(1, int(n_blocks))
+    span = n_photons / n_blocks
+    starts = [int((k + phase) * span) for k in range(n_blocks)]
+    return [min(b, max(0, n_photons - block)) for b in starts]
+
+
 def oracle_rate(tp, wl, n_photons, budget_s, threads=1):
     """Oracle histories/s on a bounded sample of the workload: the primary image
-    once (single thread), a single-thread calibration, then a sample of
-    histories split over `threads` threads, extrapolated to one projection."""
+    once (single thread), then blocks of histories spread evenly over the whole
+    history range (so every energy bin is sampled in proportion), run on
+    `threads` threads, extrapolated to one projection."""
     orcs = _oracles(tp, wl, threads)
     t0 = time.perf_counter()
     orcs[0].primary(0.0, wl["step_mm"])
     t_primary = time.perf_counter() - t0
-    n = 300
+    # single-thread calibration on a spread sample
+    block = 64
+    cal = spread_blocks(n_photons, 16, block, 0.5)
     t0 = time.perf_counter()
-    orcs[0].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], 0, n)
-    t1 = (time.perf_counter() - t0) / n
+    _oracle_blocks(orcs[:1], wl, n_photons, cal, block)
+    t1 = (time.perf_counter() - t0) / (len(cal) * block)
     rate1 = n_photons / (t_primary + n_photons * t1)
-    left = max(2.0, budget_s - t_primary - n * t1)
-    per = int(max(100, min(5e6, left / t1)))
+    left = max(2.0, budget_s - t_primary - len(cal) * block * t1)
+    n_hist = int(max(threads * 256, min(5e6, left / t1 * threads)))
+    block = 512
+    starts = spread_blocks(n_photons, max(threads, n_hist // block), block, 0.25)
     t0 = time.perf_counter()
-    _oracle_histories(orcs, wl, n_photons, n, per)
+    _oracle_blocks(orcs, wl, n_photons, starts, block)
     dt = time.perf_counter() - t0
-    t_hist = dt / (per * threads)
-    rate = n_photons / (t_primary + n_photons * t_hist)
-    sample = (f"oracle, {threads} thread(s): primary image once, single thread ({t_primary:.2f} s) + histories "
-              f"{n}..{n + per * threads} of the {int(n_photons)}-photon run ({dt:.1f} s wall), extrapolated "
-              "to one full projection")
+    done = sum(min(b + block, n_photons) - b for b in starts)
+    rate = n_photons / (t_primary + n_photons * dt / done)
+    sample = (f"oracle, {threads} thread(s): primary image once, single thread ({t_primary:.2f} s) + {done} histories "
+              f"in {len(starts)} blocks of {block} spread evenly over the {int(n_photons)}-photon run ({dt:.1f} s "
+              "wall), extrapolated to one full projection")
     return rate, sample, rate1
 
 
@@ -261,8 +283,27 @@ def make_inputs(tables_dir, photons, workload=WORKLOAD):
     return tp, wl
 
 
+def bench_config(args, wl, n_ang=1, detector=None):
+    """The workload description both arms print (same keys, same values)."""
+    vol = wl["volume"]
+    g = wl["geometry"]
+    nz, ny, nx = vol["mat"].shape
+    return {"workload": args.workload,
+            "volume": f"{nx}x{ny}x{nz} voxels at {vol['spacing'][0]} mm, uint8 material + fp16 density",
+            "detector": f"{g['nu']}x{g['nv']} pixels at {g['pu']} mm",
+            "photons_per_projection": int(wl["n_photons"]), "angles_per_step": n_ang, "step_mm": wl["step_mm"],
+            "n_split": 10, "spectrum": f"{len(wl['weights'])} bins", "response": detector or args.detector,
+            "nee_mode": args.nee_mode, "l2_flush": True,
+            "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "single",
+            "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
+            "voxel_layout": args.voxel_layout,
+            "tally": args.tally + (f" {args.tile[0]}x{args.tile[1]}" if args.tally == "tiled" else "")}
+
+
 def run_reference(args):
-    """The oracle as it stands, on all host cores (one oracle per thread, histories split between them)."""
+    """The oracle as it stands, on all host cores (one oracle per thread); each
+    step is a bounded sample of the projection: blocks of histories spread
+    evenly over the whole history range, at a new phase every step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -271,65 +312,127 @@ def run_reference(args):
     cores, cpu_name = host_cpu()
     orcs = _oracles(tp, wl, cores)
     N = wl["n_photons"]
+    block = 256
     # size each step to ~ (budget / (K + W)) seconds
     per_step = max(2.0, min(20.0, 150.0 / (args.steps + args.warmup)))
+    cal = spread_blocks(N, cores * 4, block, 0.5)
     t0 = time.perf_counter()
-    _oracle_histories(orcs, wl, N, 0, 1000)  # calibration with every thread busy
-    t_h = (time.perf_counter() - t0) / 1000
-    per = int(max(100, per_step / max(t_h, 1e-7)))  # histories per thread per step
-    n = per * cores
-    h = 1000 * cores
+    _oracle_blocks(orcs, wl, N, cal, block)  # calibration with every thread busy
+    t_h = (time.perf_counter() - t0) / (len(cal) * block)  # wall seconds per history, all threads
+    n_blocks = max(cores, int(per_step / max(t_h, 1e-9) / block))
+    golden = 0.6180339887498949
+
+    def one_step(k):
+        starts = spread_blocks(N, n_blocks, block, (k * golden) % 1.0)
+        _oracle_blocks(orcs, wl, N, starts, block)
+        return sum(min(b + block, N) - b for b in starts)
+
     for k in range(args.warmup):
-        _oracle_histories(orcs, wl, N, h, per)
-        h += n
+        one_step(k)
+    done = 0
     t0 = time.perf_counter()
     for k in range(args.steps):
-        _oracle_histories(orcs, wl, N, h, per)
-        h += n
+        done += one_step(args.warmup + k)
     el = time.perf_counter() - t0
-    value = n * args.steps / el
+    value = done / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "volume": "256^3 x 0.5 mm", "detector": "512^2 x 0.4 mm",
-                   "photons_per_projection": N, "step_mm": wl["step_mm"], "n_split": 10,
-                   "parallelism": "replicas"},
+        "config": bench_config(args, wl),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_name,
-                         "sample": f"{n} scatter histories of the {N}-photon run per step, {cores} threads "
-                                   f"x {per} histories"},
+                         "sample": f"per step {n_blocks} blocks of {block} scatter histories spread evenly over the "
+                                   f"{N}-photon run (new phase each step), {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def gather_roofline(mcx, torch, props, shape, steps_per_s, stream):
-    """Voxel-gather roofline of the transport: one 4-byte packed voxel word per
-    march step against the random-gather rate measured (mc_probe_gather) on a
-    buffer the size of the packed volume (one-voxel border), i.e. at the memory
-    level the volume lives in."""
-    nz, ny, nx = shape
-    n_bytes = (nx + 2) * (ny + 2) * (nz + 2) * 4
-    l2 = int(getattr(props, "L2_cache_size", 126 * 1024 * 1024))
-    buf = torch.ones(n_bytes // 4, dtype=torch.int32, device="cuda")
-    grid, block, rounds = props.multi_processor_count * 8, 256, 256
-    for _ in range(3):
-        mcx.probe_gather(buf, rounds, grid, block, stream=stream)
+def probe_library():
+    """libmcprobe.so (include/mc_probe.h): the measurement kernels, built beside the product library."""
+    import ctypes as C
+
+    from paper_2201_13191_gb300.build import build_probe
+
+    L = C.CDLL(build_probe())
+    vp, i, u64 = C.c_void_p, C.c_int, C.c_uint64
+    L.mc_probe_stream.argtypes = [vp, u64, i, i, i, vp, vp]
+    L.mc_probe_gather.argtypes = [vp, u64, i, i, i, vp, vp]
+    L.mc_probe_mma.argtypes = [i, i, i, vp, vp]
+    return L
+
+
+def _event_time(torch, stream, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
     ts = []
-    for _ in range(5):
+    for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mcx.probe_gather(buf, rounds, grid, block, stream=stream)
+        fn()
         e1.record(stream)
         e1.synchronize()
         ts.append(e0.elapsed_time(e1) / 1e3)
-    peak = 8 * rounds * grid * block / float(np.median(ts))
-    del buf
-    return {"bound": "l2" if n_bytes <= 0.75 * l2 else "hbm", "unit": "gathers/s", "achieved": steps_per_s,
-            "peak": peak, "frac": steps_per_s / peak, "bytes_per_gather": 4,
-            "achieved_GBps": 4 * steps_per_s / 1e9, "peak_GBps": 4 * peak / 1e9,
-            "peak_basis": f"mc_probe_gather: random 4-byte loads over {n_bytes / 1e6:.1f} MB (packed volume size), "
-                          f"{grid}x{block} threads, 8 loads in flight each; L2 {l2 / 1e6:.0f} MB"}
+    return float(np.median(ts))
+
+
+def packed_words(shape, voxel_layout, props):
+    """Words of the library's packed volume: a one-voxel border, x fastest, or
+    4x4x4 bricks (the default switches to bricks beyond 3/4 of L2)."""
+    nz, ny, nx = shape
+    px, py, pz = nx + 2, ny + 2, nz + 2
+    lin = px * py * pz
+    brick = -(-px // 4) * -(-py // 4) * -(-pz // 4) * 64
+    l2 = int(getattr(props, "L2_cache_size", 126 * 1024 * 1024))
+    if voxel_layout == 1 or (voxel_layout == 0 and lin * 4 <= 0.75 * l2):
+        return lin
+    return brick
+
+
+def memory_roofline(torch, props, shape, layout_words, steps_per_s, stream):
+    """Voxel-gather roofline of the transport at the memory level the packed
+    volume lives in.  Algorithmic bytes: 3 per march step (1-byte material +
+    2-byte FP16 density); the kernel reads them as one 4-byte word.  Peak:
+    coalesced streaming reads (mc_probe_stream) over a buffer the size of the
+    packed volume, measured live: from L2 when the buffer fits, from HBM when
+    it does not.  Secondary figure: random 4-byte gathers (mc_probe_gather)
+    over the same buffer, each touching its own 32-byte sector."""
+    import ctypes as C
+
+    P = probe_library()
+    n_bytes = (layout_words * 4 + 15) // 16 * 16
+    l2 = int(getattr(props, "L2_cache_size", 126 * 1024 * 1024))
+    level = "l2" if n_bytes <= 0.75 * l2 else "hbm"
+    buf = torch.ones(n_bytes // 4, dtype=torch.int32, device="cuda")
+    sms = props.multi_processor_count
+    grid, block = sms * 8, 256
+    sink = torch.empty(grid * block, dtype=torch.int32, device="cuda")
+    sh = C.c_void_p(stream.cuda_stream)
+    passes = 20 if level == "l2" else 4
+
+    def stream_read():
+        if P.mc_probe_stream(C.c_void_p(buf.data_ptr()), n_bytes, passes, grid, block, C.c_void_p(sink.data_ptr()),
+                             sh):
+            raise RuntimeError("mc_probe_stream failed")
+
+    rounds = 256
+
+    def gather():
+        if P.mc_probe_gather(C.c_void_p(buf.data_ptr()), n_bytes // 4, rounds, grid, block,
+                             C.c_void_p(sink.data_ptr()), sh):
+            raise RuntimeError("mc_probe_gather failed")
+
+    stream_bps = passes * n_bytes / _event_time(torch, stream, stream_read)
+    gathers_ps = 8 * rounds * grid * block / _event_time(torch, stream, gather)
+    del buf, sink
+    algo = 3.0 * steps_per_s
+    return {"level": level, "unit": "GB/s", "achieved": algo / 1e9, "peak": stream_bps / 1e9,
+            "frac": algo / stream_bps, "bytes_per_step": 3, "word_bytes_per_step": 4,
+            "word_GBps": 4.0 * steps_per_s / 1e9,
+            "peak_basis": f"mc_probe_stream: coalesced 16-byte reads over {n_bytes / 1e6:.1f} MB (the packed "
+                          f"volume's size), {passes} passes, {grid}x{block} threads; L2 {l2 / 1e6:.0f} MB",
+            "random_gather": {"gathers_per_s": gathers_ps, "sector_GBps": 32.0 * gathers_ps / 1e9,
+                              "steps_per_random_gather": steps_per_s / gathers_ps}}
 
 
 def run_ours(args):
@@ -371,11 +474,15 @@ def run_ours(args):
     out = {"primary": ctx.empty_images(n_ang), "scatter": ctx.empty_images(n_ang)}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    split = {}
+
     def step(k):
         """One step: the projection(s) of all angles, batched or one call per angle."""
         if not args.per_angle:
             ctx.project(angles, N, wl["step_mm"], seed + k, out=out, stream=stream)
             st = ctx.last_stats()
+            split.update(flight_steps=st["flight_steps"], nee_steps=st["nee_steps"], nee_rays=st["nee_rays"],
+                         interactions=st["compton"] + st["rayleigh"] + st["photo"])
             return st["transport_ms"], st["flight_steps"] + st["nee_steps"], 3
         ms, steps = 0.0, 0.0
         for i in range(n_ang):
@@ -456,8 +563,25 @@ def run_ours(args):
             "frac": achieved / peak_tflops, "traffic": None,
             "kernel": "k_transport", "steps_per_launch": float(np.mean(steps_per)),
             "kernel_ms": mean_ms, "steps_per_s": float(np.mean(steps_per)) / (mean_ms / 1e3),
-            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)"}
-    roof["gather"] = gather_roofline(mcx, torch, props, vol["mat"].shape, roof["steps_per_s"], stream)
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
+            "step_split": split}
+    roof["memory"] = memory_roofline(torch, props, vol["mat"].shape,
+                                     packed_words(vol["mat"].shape, args.voxel_layout, props), roof["steps_per_s"],
+                                     stream)
+
+    # the second half of the metric: seconds per projection at <= 2% scatter
+    # error for plain MC, Savitzky-Golay smoothing and the learned denoiser
+    # (weights trained by bench.py --denoise-eval), on the held-out phantom
+    c4 = None
+    if rank == 0 and not args.no_c4 and os.path.exists(C4_WEIGHTS):
+        t0 = time.perf_counter()
+        ctx4, _ = c4_context(mcx)
+        ctx4.denoise_load(C4_WEIGHTS, 1)
+        c4 = c4_curves(ctx4, [0.1, 1.7], 2e9, [1e5, 3e5, 1e6, 3e6, 1e7, 3e7, 1e8, 3e8, 1e9, 2e9])
+        c4["seconds"] = time.perf_counter() - t0
+        c4["workload"] = (f"cylinder/rod phantom seed {C4_HELD_OUT} (held out), {C4_N}^3 x {C4_DV} mm, "
+                          f"{C4_PX}^2 x {128.0 / C4_PX} mm panel, 60 keV, step {C4_STEP} mm, 2 angles")
+        ctx4.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -472,15 +596,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ellipsoid phantom, Kramers spectrum)",
-            "config": {"workload": args.workload, "volume": "x".join(map(str, vol["mat"].shape)) + " voxels, uint8 "
-                       "material + fp16 density", "detector": f"{ctx.nu}x{ctx.nv}",
-                       "photons_per_projection": N, "angles_per_step": n_ang,
-                       "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
-                       "step_mm": wl["step_mm"], "n_split": 10, "spectrum": f"{len(wl['weights'])} bins",
-                       "l2_flush": True, "parallelism": "replicas" if world > 1 else "single",
-                       "autotune": tuned, "voxel_layout": args.voxel_layout, "detector": args.detector,
-                       "nee_mode": args.nee_mode,
-                       "tally": args.tally + (f" {args.tile[0]}x{args.tile[1]}" if args.tally == "tiled" else "")},
+            "config": dict(bench_config(args, wl, n_ang), **({"autotune": tuned} if tuned else {})),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -488,88 +604,90 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "s_per_projection": el_ms / 1e3 / args.steps / n_ang,
+            "s_per_projection_at_2pct": None if c4 is None else c4["s_per_projection_at_2pct"],
+            "denoised_scatter": c4,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_denoise_eval(args):
-    """Photons and seconds per projection needed to reach <= 2% relative L2
-    scatter error against a high-photon reference, for plain Monte Carlo, the
-    paper's Savitzky-Golay smoothing (Sec. II-C.4) and the learned denoiser
-    trained here on pairs produced by this Monte Carlo (128^2 panel of the
-    64^3 cylinder/rod phantom family, 60 keV, SOD/SDD 300/600, step 0.5 mm)."""
-    import torch
+# The learned-denoiser workload: the cylinder/rod phantom family at 256^3 x 0.25 mm (64 mm field of view,
+# feature sizes in mm), 60 keV, SOD/SDD 300/600 mm, 256^2 x 0.5 mm scatter images, step 0.5 mm.
+C4_N, C4_DV, C4_PX, C4_STEP = 256, 0.25, 256, 0.5
+C4_WEIGHTS = os.path.join(ROOT, "paper_2201_13191_gb300", "weights", "unet_c4_256.bin")
+C4_HELD_OUT = 50_000  # phantom seed never used for training
 
-    import paper_2201_13191_gb300 as mcx
-    from mc_inputs import cylinder_variant_phantom, default_table_path, mono_spectrum
 
-    mcx.build()
-    tdir = tempfile.mkdtemp(prefix="mcden")
-    tp = default_table_path("full", tdir)
+def c4_context(mcx):
+    from mc_inputs import default_table_path, mono_spectrum
+
+    tp = default_table_path("full", tempfile.mkdtemp(prefix="mcc4"))
     ctx = mcx.Context(0)
     ctx.load_tables(tp)
     E, w = mono_spectrum(60.0)
     ctx.set_spectrum(E, w)
-    H = W = 128
-    ctx.set_geometry(300.0, 600.0, W, H, 1.0, 1.0)
-    step = 0.5
-    rng = np.random.default_rng(0)
+    ctx.set_geometry(300.0, 600.0, C4_PX, C4_PX, 128.0 / C4_PX, 128.0 / C4_PX)
+    return ctx, tp
 
-    def scatter(n_photons, angle, seed):
-        out = ctx.project([angle], int(n_photons), step, seed, primary=False)["scatter"][0]
-        return out, ctx.last_stats()["transport_ms"]
 
-    # ---- training pairs
-    low_levels = [2e5, 5e5, 1e6, 2e6]
-    t0 = time.perf_counter()
-    xs, ys = [], []
-    for k in range(args.train_phantoms):
-        v = cylinder_variant_phantom(k)
-        ctx.load_volume(v["mat"], v["rho"], v["spacing"])
-        for j in range(args.train_angles):
-            ang = float(rng.uniform(0, 2 * np.pi))
-            hi, _ = scatter(1e8, ang, 1_000_000 + 7919 * k + j)
-            for q, nl in enumerate(low_levels):
-                lo, _ = scatter(nl, ang, 2_000_000 + 104729 * k + 31 * j + q)
-                xs.append(lo.clone())
-                ys.append(hi)
-    X = torch.stack(xs)
-    Y = torch.stack(ys)
-    t_data = time.perf_counter() - t0
-    # ---- training
-    ctx.denoise_init(H, W, 16, seed=1)
-    t0 = time.perf_counter()
-    losses = []
-    order = torch.randperm(len(X), generator=torch.Generator().manual_seed(0))
-    for it in range(args.train_steps):
-        lr = 1e-3 * 0.5 * (1 + np.cos(np.pi * it / args.train_steps)) + 2e-5
-        idx = order[(it * 16) % len(X) : (it * 16) % len(X) + 16]
-        if len(idx) < 16:
-            order = torch.randperm(len(X))
-            idx = order[:16]
-        losses.append(ctx.denoise_train_step(X[idx], Y[idx], lr))
-    t_train = time.perf_counter() - t0
-    # ---- held-out phantom: reference and the error/photon curves
-    v = cylinder_variant_phantom(50_000)
+def c4_phantom(seed):
+    from mc_inputs import cylinder_variant_phantom
+
+    return cylinder_variant_phantom(seed, n=C4_N, dv=C4_DV, physical=True)
+
+
+def c4_scatter(ctx, n_photons, angle, seed):
+    out = ctx.project([angle], int(n_photons), C4_STEP, seed, primary=False)["scatter"][0]
+    return out, ctx.last_stats()["transport_ms"]
+
+
+def c4_reference(ctx, n_photons, angle, seed):
+    """Plain-MC reference image and the squared norm of its own noise (sum of
+    its 20-batch variance), so that an error measured against it can be
+    corrected for the reference's noise: E|x - ref|^2 = |x - truth|^2 + sum var."""
+    ctx.set_options(n_batches=20)
+    out = ctx.project([angle], int(n_photons), C4_STEP, seed, primary=False, variance=True)
+    ctx.set_options(n_batches=1)
+    return out["scatter"][0].double(), float(out["variance"][0].double().sum())
+
+
+def c4_error(img, ref, noise2):
+    """Relative L2 error against the truth estimated from a noisy reference."""
+    import torch
+
+    d2 = float(torch.sum((img.double() - ref) ** 2)) - noise2
+    return float(np.sqrt(max(d2, 0.0) / max(float(torch.sum(ref * ref)) - noise2, 1e-300)))
+
+
+def c4_curves(ctx, angles, ref_photons, grid, seed0=9_000):
+    """Error (relative L2 against a ref_photons plain-MC reference, corrected
+    for the reference's own noise, mean over the angles) and time per
+    projection (transport kernel + post-processing, CUDA events) of plain MC,
+    Savitzky-Golay smoothing (window 9, cubic; the paper's Sec. II-C.4, through
+    mc_smooth_upsample) and the learned denoiser (mc_denoise_infer, weights
+    already in ctx), for each photon count of grid; then the photons and
+    seconds per projection where each error curve crosses 2% (log-log
+    interpolation between grid points)."""
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    v = c4_phantom(C4_HELD_OUT)
     ctx.load_volume(v["mat"], v["rho"], v["spacing"])
-    angles = [2 * np.pi * a / args.eval_angles + 0.1 for a in range(args.eval_angles)]
-    refs = [scatter(args.ref_photons, a, 9_000 + i)[0].double() for i, a in enumerate(angles)]
-    grid = [1e5, 2e5, 5e5, 1e6, 2e6, 5e6, 1e7, 2e7, 5e7, 1e8, 2e8, 5e8]
-    sg = mcx.Context(0)  # Savitzky-Golay (window 9, cubic) through mc_smooth_upsample
+    refs = [c4_reference(ctx, ref_photons, a, seed0 + i) for i, a in enumerate(angles)]
+    sg = mcx.Context(0)
     curves = {"plain": [], "smoothed": [], "denoised": []}
     times = {"plain": [], "smoothed": [], "denoised": []}
     for n in grid:
         errs = {k: [] for k in curves}
-        t_mc = []
-        t_post = {"smoothed": [], "denoised": []}
+        t_mc, t_post = [], {"smoothed": [], "denoised": []}
         for i, a in enumerate(angles):
-            img, ms = scatter(n, a, 5_000 + 17 * i + int(np.log10(n) * 100))
+            img, ms = c4_scatter(ctx, n, a, 5_000 + 17 * i + int(np.log10(n) * 100))
             t_mc.append(ms)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            smooth = sg.smooth_upsample(img[None], [0.0], [0.0], W, H)[0]
+            smooth = sg.smooth_upsample(img[None], [0.0], [0.0], C4_PX, C4_PX)[0]
             ev1.record()
             torch.cuda.synchronize()
             t_post["smoothed"].append(ev0.elapsed_time(ev1))
@@ -578,17 +696,15 @@ def run_denoise_eval(args):
             ev1.record()
             torch.cuda.synchronize()
             t_post["denoised"].append(ev0.elapsed_time(ev1))
-            r = refs[i]
-            nr = torch.linalg.norm(r)
-            errs["plain"].append(float(torch.linalg.norm(img.double() - r) / nr))
-            errs["smoothed"].append(float(torch.linalg.norm(smooth.double() - r) / nr))
-            errs["denoised"].append(float(torch.linalg.norm(den.double() - r) / nr))
+            r, nz2 = refs[i]
+            errs["plain"].append(c4_error(img, r, nz2))
+            errs["smoothed"].append(c4_error(smooth, r, nz2))
+            errs["denoised"].append(c4_error(den, r, nz2))
         for k in curves:
             curves[k].append(float(np.mean(errs[k])))
             times[k].append(float(np.mean(t_mc)) + (float(np.mean(t_post[k])) if k in t_post else 0.0))
 
     def at_target(k, target=0.02):
-        """Photons and ms per projection where the error curve crosses the target (log-log interpolation)."""
         e = curves[k]
         for j in range(len(grid)):
             if e[j] <= target:
@@ -601,21 +717,99 @@ def run_denoise_eval(args):
         return None, None
 
     res = {k: at_target(k) for k in curves}
-    line = {
-        "metric": "s/projection at <=2% relative L2 scatter error vs a high-photon reference",
-        "unit": "s/projection", "higher_is_better": False,
-        "config": {"workload": "cylinder/rod family, 64^3 x 1 mm, 128^2 x 1 mm panel, 60 keV, step 0.5 mm",
-                   "train_pairs": int(len(X)), "train_inputs_photons": low_levels, "train_target_photons": 1e8,
-                   "train_steps": args.train_steps, "reference_photons": args.ref_photons,
-                   "eval_angles": args.eval_angles, "denoiser": "residual U-Net, 4 levels, 32 base channels, BF16"},
+    ref_noise = [float(np.sqrt(nz2 / max(float(torch.sum(r * r)), 1e-300))) for r, nz2 in refs]
+    return {
+        "reference_photons": float(ref_photons), "reference_noise_rel_l2": ref_noise,
         "photons_at_2pct": {k: res[k][0] for k in res},
         "s_per_projection_at_2pct": {k: (None if res[k][1] is None else res[k][1] / 1e3) for k in res},
         "speedup_vs_plain": {k: (None if res[k][1] is None or res["plain"][1] is None else res["plain"][1] / res[k][1])
                              for k in ("smoothed", "denoised")},
-        "error_curves": {"photons": grid, **{k: curves[k] for k in curves}},
+        "error_curves": {"photons": grid, **curves},
         "ms_per_projection": {"photons": grid, **times},
+    }
+
+
+def run_denoise_eval(args):
+    """Photons and seconds per projection needed to reach <= 2% relative L2
+    scatter error against a high-photon reference, for plain Monte Carlo, the
+    paper's Savitzky-Golay smoothing (Sec. II-C.4) and the learned denoiser
+    trained here on pairs this Monte Carlo produces: 256^2 x 0.5 mm scatter
+    images of 256^3 x 0.25 mm cylinder/rod phantoms (60 keV, SOD/SDD 300/600,
+    step 0.5 mm), inputs at --train-inputs photons, targets at
+    --target-photons.  --save-weights writes the trained network."""
+    import threading
+
+    import torch
+
+    import paper_2201_13191_gb300 as mcx
+
+    mcx.build()
+    ctx, _ = c4_context(mcx)
+    rng = np.random.default_rng(0)
+    low_levels = [float(x) for x in args.train_inputs]
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    # phantoms are built on the host one ahead of the GPU
+    nxt = {}
+
+    def build(k):
+        nxt[k] = c4_phantom(k)
+
+    th = threading.Thread(target=build, args=(0,))
+    th.start()
+    for k in range(args.train_phantoms):
+        th.join()
+        v = nxt.pop(k)
+        if k + 1 < args.train_phantoms:
+            th = threading.Thread(target=build, args=(k + 1,))
+            th.start()
+        ctx.load_volume(v["mat"], v["rho"], v["spacing"])
+        for j in range(args.train_angles):
+            ang = float(rng.uniform(0, 2 * np.pi))
+            hi, _ = c4_scatter(ctx, args.target_photons, ang, 1_000_000 + 7919 * k + j)
+            for q, nl in enumerate(low_levels):
+                lo, _ = c4_scatter(ctx, nl, ang, 2_000_000 + 104729 * k + 31 * j + q)
+                xs.append(lo.clone())
+                ys.append(hi)
+    X = torch.stack(xs)
+    Y = torch.stack(ys)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    ctx.denoise_init(C4_PX, C4_PX, 16, seed=1)
+    t0 = time.perf_counter()
+    losses = []
+    order = torch.randperm(len(X), generator=torch.Generator().manual_seed(0))
+    pos = 0
+    for it in range(args.train_steps):
+        lr = 1e-3 * 0.5 * (1 + np.cos(np.pi * it / args.train_steps)) + 2e-5
+        if pos + 16 > len(X):
+            order = torch.randperm(len(X), generator=torch.Generator().manual_seed(it))
+            pos = 0
+        idx = order[pos : pos + 16]
+        pos += 16
+        losses.append(ctx.denoise_train_step(X[idx], Y[idx], lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    if args.save_weights:
+        ctx.denoise_save(args.save_weights)
+    angles = [2 * np.pi * a / args.eval_angles + 0.1 for a in range(args.eval_angles)]
+    grid = [1e5, 2e5, 5e5, 1e6, 2e6, 5e6, 1e7, 2e7, 5e7, 1e8, 2e8, 5e8, 1e9]
+    t0 = time.perf_counter()
+    res = c4_curves(ctx, angles, args.ref_photons, grid)
+    line = {
+        "metric": "s/projection at <=2% relative L2 scatter error vs a high-photon reference",
+        "unit": "s/projection", "higher_is_better": False,
+        "config": {"workload": f"cylinder/rod family, {C4_N}^3 x {C4_DV} mm, {C4_PX}^2 x {128.0 / C4_PX} mm panel, "
+                               f"60 keV, step {C4_STEP} mm",
+                   "train_phantoms": args.train_phantoms, "train_angles": args.train_angles,
+                   "train_pairs": int(len(X)), "train_inputs_photons": low_levels,
+                   "train_target_photons": args.target_photons, "train_steps": args.train_steps,
+                   "reference_photons": args.ref_photons, "eval_angles": args.eval_angles,
+                   "held_out_phantom_seed": C4_HELD_OUT,
+                   "denoiser": "residual U-Net, 4 levels, 32 base channels, BF16"},
+        **res,
         "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
-        "seconds": {"data": t_data, "train": t_train},
+        "seconds": {"data": t_data, "train": t_train, "eval": time.perf_counter() - t0},
     }
     print(json.dumps(line), flush=True)
 
@@ -696,12 +890,12 @@ def run_conv_bench(args):
     if int(err.item()):
         raise RuntimeError("a tensor-core wait gave up")
     # sustained rate of the MMA shape each layer issues (M = 128, N = C_out tile, K = 16), measured live
-    L.mc_probe_mma.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+    PL = probe_library()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     shape_peak = {}
     for nt in (16, 32, 64, 128, 256):
         rounds = 4096
-        ms = timed(lambda: L.mc_probe_mma(nt, sms, rounds, ptr(err), sh))
+        ms = timed(lambda: PL.mc_probe_mma(nt, sms, rounds, ptr(err), sh))
         shape_peak[nt] = sms * rounds * 4 * 2.0 * 128 * nt * 16 / ms / 1e9
     torch.cuda.synchronize()
     if int(err.item()):

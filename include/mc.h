@@ -93,7 +93,14 @@ typedef struct mc_options {
   int doppler;           /* 1: Doppler broadening of incoherent scatter (impulse approximation with the
                             orbital model of the bound tables; needs tables of version 2), 0 = off (default) */
   int tile_u, tile_v;    /* tile size in pixels of MC_TALLY_TILED, default 64 x 64 */
+  int forced_detection;  /* 1: forced detection (Sec. I names it among the variance-reduction techniques):
+                            every scatter interaction sends exactly one pseudo-particle to every pixel of
+                            the panel (of the history's tile under MC_TALLY_TILED), at a uniform point in
+                            it, with weight 1 instead of P / n_split: the paper's split estimator with the
+                            pixel choice stratified, so it adds no variance; n_split is ignored.  Needs
+                            at most MC_FORCED_MAX_PIXELS such pixels.  0 = off (default) */
 } mc_options;
+#define MC_FORCED_MAX_PIXELS 65536
 
 /* Fill *opt with the defaults listed above. */
 void mc_default_options(mc_options *opt);
@@ -240,6 +247,40 @@ int mc_correct_iter(mc_ctx *ctx, const float *raw_I, const float *I0, int n_proj
                     int NV, int n_iter, const mc_correct_params *prm, float *corrected_a_out, float *volume_out,
                     double *iter_seconds, void *stream);
 
+/* The steps of mc_correct_iter as separate calls (Sec. II-E and its
+ * flowchart), so each can be run and checked on its own; mc_correct_iter runs
+ * the same kernels.
+ *
+ * mc_line_integrals: a = -ln(I / I0) per pixel (Sec. II-E: the measured
+ *   intensities become line integrals); I device FP32 [n_proj][NV][NU], I0
+ *   device FP32 [NV][NU] (one flat field for all projections), a_out device
+ *   FP32 like I.  Values below 1e-30 are clamped to 1e-30 first.
+ * mc_segment: segmentation of a reconstruction vol (device FP32
+ *   [nz][ny][nx], mm^-1) into `classes` (2 or 3) classes by multi-level Otsu
+ *   (exhaustive search of the thresholds maximising the between-class
+ *   variance, ties to the smallest) over a 256-bin histogram of [mu_lo, mu_hi):
+ *   bin b = (int)((mu - mu_lo) * (256 / (mu_hi - mu_lo))) in FP32, clamped to
+ *   [0, 255]; thresholds t0 < t1 are bin indices (t1 = 256 for 2 classes) and
+ *   a voxel in bin b has class 0 if b < t0, 1 if b < t1, else 2.  Class 0
+ *   becomes class_material[0] at density class_density0; class k >= 1 becomes
+ *   class_material[k] at rho = mu / (0.1 mu_rho(class_material[k], e_eff_keV))
+ *   (FP32, tables linear between nodes), clamped to [0, 30] g/cm^3.  Outputs:
+ *   mat_out (device uint8) and rho_out (device binary16 bits) [nz][ny][nx];
+ *   hist_out (host uint32 [256], nullable) and thresholds_out (host int [2],
+ *   nullable).  Synchronises `stream`.
+ * mc_correct_images: eq. (Correction), c = a - ln(Ip / (Ip + s Is)) per
+ *   element, with Ip clamped below at 1e-30, Is at 0, s = is_scale (the
+ *   pixel-area ratio when Is was simulated on coarser pixels; 1 otherwise);
+ *   a, ip, is, c_out device FP32 [n].
+ * Errors: STATE (no tables, for mc_segment), INVALID_ARG, CUDA/OOM. */
+int mc_line_integrals(mc_ctx *ctx, const float *I, const float *I0, int n_proj, int NU, int NV, float *a_out,
+                      void *stream);
+int mc_segment(mc_ctx *ctx, const float *vol, int nx, int ny, int nz, int classes, const int *class_material,
+               float class_density0, float e_eff_keV, float mu_lo, float mu_hi, uint32_t *hist_out,
+               int *thresholds_out, uint8_t *mat_out, uint16_t *rho_out, void *stream);
+int mc_correct_images(mc_ctx *ctx, const float *a, const float *ip, const float *is, float is_scale, size_t n,
+                      float *c_out, void *stream);
+
 /* Down-sampling of a segmented volume for the Monte Carlo step (Sec. II-C.2:
  * the number of voxels is down-sampled to cut the ray-tracing time; Sec.
  * II-E).  Device mat [nz][ny][nx] (ids < the table's materials) and rho
@@ -342,20 +383,30 @@ int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t pro
  * file-scope __device__ array of about 32.4 MiB, held on every GPU that loads
  * the library until the process exits.  It calls no cudaMalloc, cudaFree or
  * other allocating routine.
- *   - Limits: n_angles <= MC_STATIC_MAX_ANGLES and n_angles * nu * nv <=
- *     MC_STATIC_MAX_TALLY; larger requests return MC_ERR_INVALID_ARG.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Limits (larger requests return MC_ERR_INVALID_ARG):
+ *       n_angles <= MC_STATIC_MAX_ANGLES;
+ *       n_angles * nu * nv <= MC_STATIC_MAX_TALLY;
+ *       the cross-section tables staged for the spectrum fit in
+ *       MC_STATIC_MAX_TABLE_BYTES: 8 n_s (6 n_mat + 2) + 100 n_mat bytes
+ *       (rounded up to 16), n_mat the table's materials and n_s the energy
+ *       nodes from the table's first up to one past the spectrum's highest
+ *       energy (e.g. 8 materials reach the limit near 160 keV at 1 keV
+ *       nodes), where mc_project has no such limit.
+ *   - Each CUDA context holds its own copy of the array.  The first call in a
+ *     context looks up the array's device address there (cudaGetSymbolAddress,
+ *     with the context's device current) and keeps it for that context; make
+ *     that first call before any stream capture.  Every call synchronises
+ *     `stream` before it returns.
  *   - Every call re-stages and zeroes what it uses, so it never sees an
- *     earlier call's contents; but all calls share the one array, so calls
- *     that overlap on the GPU (other streams, other host threads, other
- *     contexts on the same device) race: serialise them.
+ *     earlier call's contents; but calls in one context share the one array,
+ *     so calls that overlap on the GPU (several streams, several host threads
+ *     of one context) race: serialise them.
  *   - Uses about 80 KB of the calling thread's stack for host staging.
  * Inputs: angles_rad host [n_angles]; scatter_out device FP32
  * [n_angles][nv][nu].  Errors: as mc_project. */
 #define MC_STATIC_MAX_TALLY 4194304
 #define MC_STATIC_MAX_ANGLES 4096
+#define MC_STATIC_MAX_TABLE_BYTES 65536
 int mc_project_scatter_static(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t n_photons, float step_mm,
                               uint64_t seed, float *scatter_out, void *stream);
 
@@ -390,26 +441,6 @@ int mc_load_mesh(mc_ctx *ctx, const float *vertices, int n_vertices, const int *
  * scattered energy E'.  eta == NULL restores the default; loading tables
  * clears it.  Errors: STATE (no tables), INVALID_ARG. */
 int mc_set_detector_response(mc_ctx *ctx, const double *eta, int n);
-
-/* Gather probe (measurement helper; no counterpart in the paper).  Launches
- * grid x block threads (block a multiple of 32, <= 256); each performs
- * 8 x rounds independent random 4-byte loads from buf[0 .. n_words) (device
- * memory, n_words < 2^32) and writes one folded word to sink[thread] (device,
- * grid x block words).  Timing it on a buffer the size of the packed voxel
- * volume gives the random-gather rate at the memory level that volume lives in
- * (L2 or HBM), the peak of the transport's voxel-gather roofline.  Asynchronous
- * on `stream`.  Errors: INVALID_ARG, CUDA. */
-int mc_probe_gather(const void *buf, uint64_t n_words, int rounds, int grid, int block, uint32_t *sink, void *stream);
-
-/* Tensor-core probe (measurement helper; no counterpart in the paper).  grid
- * CTAs (one per SM) each issue 4 x rounds tcgen05.mma of shape M = 128,
- * N = n (16, 32, 64, 128 or 256), K = 16 on BF16 operands resident in shared
- * memory, then wait for them; *err (device int) is set to 1 if a bounded wait
- * gave up.  Timing it gives the sustained rate of the instruction shape the
- * convolution kernels issue, which falls with N (the denoiser's layers have
- * N = C_out from 16 to 256).  FLOPs per launch: grid x rounds x 4 x 2 x 128 x
- * n x 16.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
-int mc_probe_mma(int n, int grid, int rounds, int *err, void *stream);
 
 #ifdef __cplusplus
 }

@@ -134,33 +134,48 @@ def slab_phantom(n=(16, 16, 16), dv=(2.0, 2.0, 2.0), material=MAT_WATER, density
     return out
 
 
-def cylinder_variant_phantom(seed, n=64, dv=1.0):
+def cylinder_variant_phantom(seed, n=64, dv=1.0, physical=False):
     """Seeded variant of the cylinder + rod phantom for denoiser training:
-    cylinder radius 18-28 mm and height 40-60 mm, rod radius 3-8 mm at a random
-    offset inside the cylinder, rod material aluminium, bone or PMMA, and up to
-    three small water/bone/PMMA/aluminium ellipsoids inside the cylinder."""
+    cylinder radius 18-28 mm and height 40-60 mm (on the 64 mm field of view),
+    rod radius 3-8 voxels at a random offset inside the cylinder, rod material
+    aluminium, bone or PMMA, and up to three small water/bone/PMMA/aluminium
+    ellipsoids (semi-axes 2-8 voxels) inside the cylinder.  physical=True
+    reads the rod radius and the semi-axes in mm instead of voxels, so that a
+    finer grid over the same field of view (e.g. 256^3 x 0.25 mm) samples the
+    same family of objects as 64^3 x 1 mm; at dv = 1 mm both are the same."""
     rng = np.random.default_rng(10_000 + seed)
-    c = _centres(n, dv)
-    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    unit = 1.0 if physical else dv
     half = n * dv / 2.0
+    c = _centres(n, dv)
     r_cyl = rng.uniform(0.56, 0.88) * half * 1.0
     h_cyl = rng.uniform(0.62, 0.94) * 2 * half
-    r_rod = rng.uniform(3.0, 8.0) * dv
+    r_rod = rng.uniform(3.0, 8.0) * unit
     ang = rng.uniform(0, 2 * np.pi)
     off = rng.uniform(0.0, max(r_cyl - r_rod - dv, 0.0))
     rx, ry = off * np.cos(ang), off * np.sin(ang)
-    mat = np.full((n, n, n), MAT_AIR, dtype=np.uint8)
-    inz = np.abs(z) <= h_cyl / 2.0
-    mat[(x**2 + y**2 <= r_cyl**2) & inz] = MAT_WATER
+    # the cylinder and rod are z-invariant inside |z| <= h/2: masks in the x-y plane
+    y2, x2 = np.meshgrid(c, c, indexing="ij")
+    inz = np.abs(c) <= h_cyl / 2.0
+    plane = np.full((n, n), MAT_AIR, dtype=np.uint8)
+    plane[x2**2 + y2**2 <= r_cyl**2] = MAT_WATER
     rod_mat = [MAT_AL, MAT_BONE, MAT_PMMA][int(rng.integers(0, 3))]
-    mat[((x - rx) ** 2 + (y - ry) ** 2 <= r_rod**2) & inz] = rod_mat
+    plane[(x2 - rx) ** 2 + (y2 - ry) ** 2 <= r_rod**2] = rod_mat
+    mat = np.full((n, n, n), MAT_AIR, dtype=np.uint8)
+    mat[inz] = plane
     for _ in range(int(rng.integers(0, 4))):
         cx, cy = rng.uniform(-0.6, 0.6, 2) * r_cyl
         cz = rng.uniform(-0.4, 0.4) * h_cyl
-        ax = rng.uniform(2.0, 8.0, 3) * dv
+        ax = rng.uniform(2.0, 8.0, 3) * unit
         m = [MAT_WATER, MAT_BONE, MAT_PMMA, MAT_AL][int(rng.integers(0, 4))]
-        inside = ((x - cx) / ax[0]) ** 2 + ((y - cy) / ax[1]) ** 2 + ((z - cz) / ax[2]) ** 2 <= 1.0
-        mat[inside & (mat != MAT_AIR)] = m
+        # only the ellipsoid's bounding slab of z is touched
+        zs = np.nonzero(np.abs(c - cz) <= ax[2])[0]
+        if len(zs) == 0:
+            continue
+        z3 = c[zs][:, None, None]
+        inside = ((x2[None] - cx) / ax[0]) ** 2 + ((y2[None] - cy) / ax[1]) ** 2 + ((z3 - cz) / ax[2]) ** 2 <= 1.0
+        sub = mat[zs]
+        sub[inside & (sub != MAT_AIR)] = m
+        mat[zs] = sub
     out = _finish(mat)
     out.update(shape=(n, n, n), spacing=(dv, dv, dv))
     return out

@@ -57,6 +57,7 @@ def lib():
         L.orc_set_nee_mode.argtypes = [P, i]
         L.orc_set_doppler.argtypes = [P, i]
         L.orc_set_tiles.argtypes = [P, i, i]
+        L.orc_set_forced.argtypes = [P, i]
         L.orc_load_mesh.argtypes = [P, P, i, P, P, i, P, P, P, i]
         L.orc_mesh_primary.argtypes = [P, d, P]
         L.orc_sample_doppler.argtypes = [P, i, d, d, u64, u64, P]
@@ -152,6 +153,10 @@ class Oracle:
     def set_tiles(self, tile_u, tile_v):
         """Tile-stratified point-detector pixels (tile_u x tile_v pixels per tile; 0, 0 = off)."""
         _chk(self.L.orc_set_tiles(self.h, int(tile_u), int(tile_v)), "set_tiles")
+
+    def set_forced(self, on):
+        """Forced detection: every interaction scores every pixel (of the history's tile) once."""
+        _chk(self.L.orc_set_forced(self.h, int(on)), "set_forced")
 
     def set_nee_mode(self, mode):
         """0: score the sampled scatter type (the paper's); 1: expected value over both types."""

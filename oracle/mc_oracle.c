@@ -24,9 +24,10 @@
  *     model of Sec. II-A) with exact path lengths: free flights over the
  *     sorted surface crossings, point-detector attenuation by exact chords;
  *   - options: a detector response table (Sec. II-D.2), expected-value
- *     scoring over the interaction type (Sec. II-C.1), the bound-electron
- *     scattering function and Doppler broadening (Sec. II-A), and tile-
- *     stratified point-detector pixels.
+ *     scoring over the interaction type (Sec. II-C.1), forced detection (one
+ *     pseudo-particle per pixel; Sec. I names the technique), the
+ *     bound-electron scattering function and Doppler broadening (Sec. II-A),
+ *     and tile-stratified point-detector pixels.
  *
  * Readings of the paper that it implements (all listed in the design notes):
  * lengths in mm, energies in keV, eta(E) = E unless a detector response
@@ -90,6 +91,7 @@ typedef struct {
   /* options */
   int n_split, max_order;
   int nee_mode; /* 0: score the sampled scatter type; 1: expected value over both types */
+  int forced;   /* forced detection: one pseudo-particle per pixel of the panel (or of the history's tile) */
   int doppler;  /* Doppler broadening of incoherent scatter (needs the bound tables) */
   double rr_threshold, eps_face;
   int tile_u, tile_v; /* > 0: tile-stratified point-detector pixels (see orc_set_tiles) */
@@ -350,6 +352,20 @@ int orc_sample_doppler(const orc_ctx *c, int m, double E, double cos_t, uint64_t
 int orc_set_nee_mode(orc_ctx *c, int mode) {
   if (mode != 0 && mode != 1) return ORC_EINVAL;
   c->nee_mode = mode;
+  return ORC_OK;
+}
+
+/* Forced detection (named among the variance-reduction techniques in Sec. I):
+ * every scatter interaction scores every pixel of the panel -- or of the
+ * history's tile under tile-stratified scoring -- exactly once, pixel s taking
+ * the s-th pseudo-particle's counter block (its first word unused) for a
+ * uniform point inside the pixel, with weight 1 in place of P / n_split.  It is
+ * the split estimator of eq. (Th) with the pixel choice stratified instead of
+ * drawn, so each pixel receives the same expected score and the pixel choice
+ * adds no variance. */
+int orc_set_forced(orc_ctx *c, int on) {
+  if (on != 0 && on != 1) return ORC_EINVAL;
+  c->forced = on;
   return ORC_OK;
 }
 
@@ -700,9 +716,10 @@ static size_t voxel_of(const orc_ctx *c, const double p[3], int ijk[3]) {
  * n = ceil(L/step) equal steps of length h = L/n; each step takes the
  * material and density of the voxel holding its midpoint.  Accumulates
  * rho*h per material into rhoL (g/cm^3 * mm).  If bound != NULL, adds for
- * every midpoint within eps_face*voxel of a face whose neighbour differs the
- * largest possible change of rho*mu_rho*h at energy Eb (an ambiguity bound for
- * FP32 re-evaluation); sets *namb if L/step is within 1e-5 of an integer.
+ * every midpoint within eps_face*voxel of a face, edge or corner whose other
+ * voxels differ the largest possible change of rho*mu_rho*h at energy Eb (an
+ * ambiguity bound for FP32 re-evaluation); sets *namb if L/step is within 1e-5
+ * of an integer.
  * Returns the number of steps. */
 static long march_rhoL_n(const orc_ctx *c, const double p0[3], const double w[3], double t0, double t1, double step,
                          double *rhoL, double *bound, double Eb, int *namb, long n_force) {
@@ -728,24 +745,38 @@ static long march_rhoL_n(const orc_ctx *c, const double p0[3], const double w[3]
     size_t v = voxel_of(c, p, ijk);
     rhoL[c->mat[v]] += c->rho[v] * h;
     if (bound) {
+      /* the voxels an FP32 re-evaluation may pick instead: those reached by
+       * stepping across any subset of the faces this midpoint lies within
+       * eps_face of (a face, an edge or a corner neighbour); the largest change
+       * of rho mu h among them that differs from this voxel */
       double mu_here = c->rho[v] * mu_rho_tot(c, c->mat[v], Eb) * 0.1;
+      int nb[3];
       for (int a = 0; a < 3; ++a) {
         double x = (p[a] - lo[a]) / dv[a];
         double fr = x - floor(x);
-        int nb = -1;
-        if (fr < c->eps_face) nb = ijk[a] - 1;
-        else if (fr > 1.0 - c->eps_face) nb = ijk[a] + 1;
-        /* a neighbour index equal to the clamped index itself means the midpoint is at the box face */
-        if (nb >= 0 && nb < nn[a] && nb != ijk[a]) {
-          int j2[3] = {ijk[0], ijk[1], ijk[2]};
-          j2[a] = nb;
-          size_t v2 = ((size_t)j2[2] * c->ny + j2[1]) * c->nx + j2[0];
-          if (c->mat[v2] != c->mat[v] || c->rho[v2] != c->rho[v]) {
-            double mu2 = c->rho[v2] * mu_rho_tot(c, c->mat[v2], Eb) * 0.1;
-            *bound += fabs(mu2 - mu_here) * h;
+        nb[a] = -1;
+        if (fr < c->eps_face) nb[a] = ijk[a] - 1;
+        else if (fr > 1.0 - c->eps_face) nb[a] = ijk[a] + 1;
+        /* a neighbour index outside the volume, or equal to the clamped index, is no other voxel */
+        if (nb[a] < 0 || nb[a] >= nn[a] || nb[a] == ijk[a]) nb[a] = -1;
+      }
+      double worst = 0;
+      for (int sub = 1; sub < 8; ++sub) {
+        int j2[3] = {ijk[0], ijk[1], ijk[2]}, ok = 1;
+        for (int a = 0; a < 3; ++a)
+          if (sub >> a & 1) {
+            if (nb[a] < 0) ok = 0;
+            else j2[a] = nb[a];
           }
+        if (!ok) continue;
+        size_t v2 = ((size_t)j2[2] * c->ny + j2[1]) * c->nx + j2[0];
+        if (c->mat[v2] != c->mat[v] || c->rho[v2] != c->rho[v]) {
+          double mu2 = c->rho[v2] * mu_rho_tot(c, c->mat[v2], Eb) * 0.1;
+          double dlt = fabs(mu2 - mu_here) * h;
+          if (dlt > worst) worst = dlt;
         }
       }
+      *bound += worst;
     }
   }
   return n;
@@ -1062,19 +1093,21 @@ int orc_primary(const orc_ctx *c, double beta, double step, double *Ip, double *
       double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
       double w[3] = {D[0] / d, D[1] / d, D[2] / d};
       double rhoL[ORC_MAXMAT] = {0};
-      double b = 0, tau_mean = 0;
+      double b = 0;
       int namb = 0;
       long n = march_rhoL(c, P.s, w, 0.0, d, step, rhoL, &b, Emin, &namb);
-      double sum = primary_sum(c, rhoL, &tau_mean);
+      double sum = primary_sum(c, rhoL, NULL);
       double cosg = c->sdd / d;
       Ip[(size_t)j * c->nu + i] = sum * c->pu * c->pv * cosg / (4.0 * PI * d * d);
       if (bound) {
-        double ta, tb, extra = 0;
-        if (clip_box(c, P.s, w, 0.0, d, &ta, &tb)) {
-          double L = tb - ta, tmax = fmax(fabs(ta), fabs(tb));
-          /* four FP32 units in the last place of the larger parameter */
-          extra = tau_mean * 4.0 * ldexp(1.0, ilogb(tmax) - 23) / L;
-        }
+        /* Allowance for an FP32 re-evaluation of this pixel: the midpoints
+         * flagged within eps_face of a face between different voxels (b), and,
+         * where ceil(L/step) is within rounding of an integer, the change the
+         * neighbouring step count produces.  Nothing is allowed for the chord's
+         * own rounding: an evaluation that parameterises the ray from its point
+         * nearest the isocentre carries an error of the volume's size there,
+         * far below the 1e-5 target. */
+        double extra = 0;
         if (namb) {
           for (long dn = -1; dn <= 1; dn += 2) {
             if (n + dn < 1) continue;
@@ -1278,10 +1311,11 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
       /* point-detector scoring, split into n_split pseudo-particles, eq. (Th) */
       rng_align(&g);
       const uint32_t k0 = g.ctr[0];
-      for (int s = 0; s < c->n_split; ++s) {
+      const int n_pp = c->forced ? (int)Pt : c->n_split;
+      for (int s = 0; s < n_pp; ++s) {
         uint32_t r = rng_next(&g);
         double va = rng_u(&g), vb = rng_u(&g), vr = rng_u(&g);
-        uint64_t pt = ((uint64_t)r * Pt) >> 32;
+        uint64_t pt = c->forced ? (uint64_t)s : ((uint64_t)r * Pt) >> 32;
         int pi = u0 + (int)(pt % wt), pj = v0 + (int)(pt / wt);
         uint64_t pix = (uint64_t)pj * c->nu + pi;
         double Pp[3];
@@ -1291,7 +1325,7 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         double dir[3] = {DD[0] / dd, DD[1] / dd, DD[2] / dd};
         double lam = w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2];
         double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
-        const double geo = tile_w * A_px * cosg * ((double)Pt / c->n_split) / (2.0 * PI * dd * dd);
+        const double geo = tile_w * A_px * cosg * ((double)Pt / n_pp) / (2.0 * PI * dd * dd);
         double sc;
         st[ST_NEE_RAYS] += 1;
         rng_t side;

@@ -4,9 +4,11 @@ Plain numpy FP64 restatement of the correction plumbing of arXiv 2201.13191
 Sec. II-E: line integrals a = -ln(I/I0); FDK for a circular orbit (cosine
 pre-weighting, discrete Ram-Lak ramp filter in the isocentre plane,
 voxel-driven backprojection with bilinear interpolation and the (D/(D-x.n))^2
-weight, dbeta/2 for a full orbit); multi-level Otsu thresholds by exhaustive
-search of the between-class variance; eq. (Correction); and the down-sampling
-of the segmented volume for the Monte Carlo step (Sec. II-C.2, Sec. II-E).
+weight, dbeta/2 for a full orbit); the histogram of the reconstruction,
+multi-level Otsu thresholds by exhaustive search of the between-class
+variance and the class -> material / density map; eq. (Correction); and the
+down-sampling of the segmented volume for the Monte Carlo step (Sec. II-C.2,
+Sec. II-E).
 """
 
 from __future__ import annotations
@@ -62,6 +64,43 @@ def fdk(p, angles, pu, pv, sod, sdd, grid):
     return vol * np.pi / n_proj
 
 
+def histogram(vol, lo, hi, nbins=256):
+    """Histogram of mu over [lo, hi) in nbins bins, values outside clamped to the end bins.
+
+    The bin of a value is an integer decided by floating point, so it is taken
+    in the precision the library takes it in (FP32): b = trunc((mu - lo) *
+    (nbins / (hi - lo))), each operation rounded to FP32, then clamped."""
+    f = np.float32
+    v = np.asarray(vol, dtype=f).ravel()
+    sc = f(nbins) / (f(hi) - f(lo))
+    x = (v - f(lo)) * sc
+    b = np.clip(np.trunc(x), 0, nbins - 1).astype(np.int64)
+    return np.bincount(b, minlength=nbins), b
+
+
+def segment(vol, lo, hi, classes, class_material, murho_cls, class_density0, rho_max=30.0, nbins=256):
+    """Segmentation of a reconstruction (Sec. II-E): Otsu thresholds on the
+    histogram, class 0 -> class_material[0] at class_density0, class k >= 1 ->
+    class_material[k] at rho = mu / (0.1 murho_cls[k]) clamped to [0, rho_max]
+    (murho_cls[k]: mass attenuation of that material at the effective energy,
+    cm^2/g).  Returns (mat, rho FP64, hist, thresholds)."""
+    hist, b = histogram(vol, lo, hi, nbins)
+    t0, t1 = otsu(hist, classes)
+    cls = np.where(b < t0, 0, np.where((classes == 2) | (b < t1), 1, 2))
+    mu = np.asarray(vol, dtype=np.float64).ravel()
+    mat = np.asarray(class_material)[cls].astype(np.uint8)
+    mr = np.asarray(murho_cls, dtype=np.float64)[cls]
+    rho = np.where(cls == 0, float(np.float32(class_density0)), np.clip(mu / (0.1 * np.where(cls == 0, 1.0, mr)),
+                                                                       0.0, rho_max))
+    shape = np.shape(vol)
+    return mat.reshape(shape), rho.reshape(shape), hist, (t0, t1)
+
+
+def line_integrals(I, I0):
+    """a = -ln(I / I0), both clamped below at 1e-30 (Sec. II-E)."""
+    return -np.log(np.maximum(np.asarray(I, np.float64), 1e-30) / np.maximum(np.asarray(I0, np.float64), 1e-30))
+
+
 def otsu(hist, classes):
     """Thresholds (bin indices) maximising the between-class variance; ties to the smallest."""
     hist = np.asarray(hist, dtype=np.float64)
@@ -92,9 +131,12 @@ def otsu(hist, classes):
     return arg
 
 
-def correct(a, ip, is_):
-    """Eq. (Correction): c = a - ln(Ip / (Ip + Is))."""
-    return a - np.log(ip / (ip + is_))
+def correct(a, ip, is_, is_scale=1.0):
+    """Eq. (Correction): c = a - ln(Ip / (Ip + s Is)), Ip clamped below at 1e-30 and Is at 0 (s: the pixel-area
+    ratio when Is was simulated on coarser pixels, 1 otherwise)."""
+    ip = np.maximum(np.asarray(ip, np.float64), 1e-30)
+    is_ = np.maximum(np.asarray(is_, np.float64), 0.0) * is_scale
+    return np.asarray(a, np.float64) - np.log(ip / (ip + is_))
 
 
 def bin_volume(mat, rho, murho):

@@ -18,6 +18,5 @@ from .binding import (  # noqa: F401
     STAT_NAMES,
     conv3x3,
     conv3x3_wgrad,
-    probe_gather,
 )
 from .build import build  # noqa: F401

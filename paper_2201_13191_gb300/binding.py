@@ -35,7 +35,7 @@ EXPORTED = [
     "mc_last_stats", "mc_smooth_upsample", "mc_project_scatter_static", "mc_autotune", "mc_denoise_init",
     "mc_denoise_train_step", "mc_denoise_infer", "mc_denoise_get_layer", "mc_denoise_set_layer", "mc_denoise_save",
     "mc_denoise_load", "mc_nn_conv3x3", "mc_nn_conv3x3_wgrad", "mc_correct_iter", "mc_fdk", "mc_bin_volume",
-    "mc_probe_gather", "mc_set_detector_response", "mc_probe_mma", "mc_load_mesh",
+    "mc_set_detector_response", "mc_load_mesh", "mc_line_integrals", "mc_segment", "mc_correct_images",
 ]
 
 
@@ -96,6 +96,7 @@ class Options(C.Structure):
         ("doppler", C.c_int),
         ("tile_u", C.c_int),
         ("tile_v", C.c_int),
+        ("forced_detection", C.c_int),
     ]
 
 
@@ -146,9 +147,10 @@ def library():
         L.mc_correct_iter.argtypes = [P, vp, vp, i, vp, i, i, i, C.POINTER(CorrectParams), vp, vp, vp, vp]
         L.mc_fdk.argtypes = [P, vp, i, vp, i, i, i, i, i, f, f, f, vp, vp]
         L.mc_bin_volume.argtypes = [P, vp, vp, i, i, i, f, vp, vp, vp]
-        L.mc_probe_gather.argtypes = [vp, C.c_uint64, i, i, i, vp, vp]
+        L.mc_line_integrals.argtypes = [P, vp, vp, i, i, i, vp, vp]
+        L.mc_segment.argtypes = [P, vp, i, i, i, i, vp, f, f, f, f, vp, vp, vp, vp, vp]
+        L.mc_correct_images.argtypes = [P, vp, vp, vp, f, C.c_size_t, vp, vp]
         L.mc_set_detector_response.argtypes = [P, vp, i]
-        L.mc_probe_mma.argtypes = [i, i, i, vp, vp]
         L.mc_load_mesh.argtypes = [P, vp, i, vp, vp, i, vp, vp, vp, i]
         _lib = L
     return _lib
@@ -197,19 +199,6 @@ def conv3x3_wgrad(x, dy, splits=8, stream=None):
     if int(err.item()):
         raise MCError(-5, "a tensor-core wait gave up")
     return dw
-
-
-def probe_gather(buf, rounds, grid, block=256, stream=None):
-    """Random 4-byte gathers from the device tensor `buf` (mc_probe_gather); returns the sink tensor.
-    Asynchronous: time it with events on `stream`.  Loads issued: 8 x rounds x grid x block."""
-    import torch
-
-    n_words = buf.numel() * buf.element_size() // 4
-    sink = torch.empty(grid * block, dtype=torch.int32, device=buf.device)
-    rc = library().mc_probe_gather(_t_ptr(buf), n_words, rounds, grid, block, _t_ptr(sink), _stream_handle(stream))
-    if rc != MC_OK:
-        raise MCError(rc, "mc_probe_gather failed")
-    return sink
 
 
 def _stream_handle(stream):
@@ -415,6 +404,41 @@ class Context:
         self._check(self.L.mc_bin_volume(self.h, _t_ptr(mat.contiguous()), _t_ptr(rho.contiguous()), nx, ny, nz,
                                          float(e_eff_keV), _t_ptr(mo), _t_ptr(ro), _stream_handle(stream)))
         return mo, ro
+
+    def line_integrals(self, I, I0, stream=None):
+        """a = -ln(I / I0) (mc_line_integrals): I device [n][NV][NU], I0 device [NV][NU]."""
+        I = I.contiguous()
+        n, NV, NU = I.shape
+        a = self.torch.empty_like(I)
+        self._check(self.L.mc_line_integrals(self.h, _t_ptr(I), _t_ptr(I0.contiguous()), n, NU, NV, _t_ptr(a),
+                                             _stream_handle(stream)))
+        return a
+
+    def segment(self, vol, classes, class_material, class_density0, e_eff_keV, mu_lo, mu_hi, stream=None):
+        """Otsu segmentation and class -> material / density (mc_segment) of a device FP32 volume
+        [nz][ny][nx]; returns (mat uint8, rho int16 binary16 bits) device tensors, the 256-bin histogram and
+        the two thresholds (numpy)."""
+        torch = self.torch
+        vol = vol.contiguous()
+        nz, ny, nx = vol.shape
+        mat = torch.empty((nz, ny, nx), dtype=torch.uint8, device=vol.device)
+        rho = torch.empty((nz, ny, nx), dtype=torch.int16, device=vol.device)
+        cm = np.zeros(3, np.int32)
+        cm[: len(class_material)] = class_material
+        hist = np.zeros(256, np.uint32)
+        thr = np.zeros(2, np.int32)
+        self._check(self.L.mc_segment(self.h, _t_ptr(vol), nx, ny, nz, int(classes), _np_ptr(cm),
+                                      float(class_density0), float(e_eff_keV), float(mu_lo), float(mu_hi),
+                                      _np_ptr(hist), _np_ptr(thr), _t_ptr(mat), _t_ptr(rho), _stream_handle(stream)))
+        return mat, rho, hist, thr
+
+    def correct_images(self, a, ip, is_, is_scale=1.0, stream=None):
+        """Eq. (Correction) per element (mc_correct_images): c = a - ln(Ip / (Ip + s Is))."""
+        a = a.contiguous()
+        c = self.torch.empty_like(a)
+        self._check(self.L.mc_correct_images(self.h, _t_ptr(a), _t_ptr(ip.contiguous()), _t_ptr(is_.contiguous()),
+                                             float(is_scale), a.numel(), _t_ptr(c), _stream_handle(stream)))
+        return c
 
     def correct_iter(self, raw_I, I0, angles, NU, NV, n_iter, prm, stream=None):
         """Iterative scatter correction; returns (corrected line integrals, last volume, seconds per iteration)."""

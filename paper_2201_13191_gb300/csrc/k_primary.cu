@@ -59,21 +59,35 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
   const int i = pix % G.nu, j = pix / G.nu;
-  const Pose ps = make_pose(G, __ldg(P.angles + a));
-  const float3 X = det_point(G, ps, (float)i + 0.5f, (float)j + 0.5f);
-  const float3 D = sub3(X, ps.s);
-  const float d = sqrtf(dot3(D, D));
-  const float3 w = make_float3(D.x / d, D.y / d, D.z / d);
+  // Ray from the source to the pixel centre, parameterised from its point o
+  // closest to the isocentre (|o| is at most the volume's half diagonal), so
+  // that the chord and the midpoints carry rounding of the volume's size, not
+  // of the source distance.  With n = (cos b, sin b, 0), e_u = (-sin b, cos b, 0):
+  //   D = X - s = -SDD n + u e_u + v e_z,  d^2 = SDD^2 + u^2 + v^2,
+  //   o = s - (s.w) w = (SOD / d^2) ((u^2 + v^2) n + SDD (u e_u + v e_z)),
+  // both free of cancellation; the source sits at t = -SOD SDD / d.
+  float sb, cb;
+  sincosf(__ldg(P.angles + a), &sb, &cb);
+  const float u = ((float)i + 0.5f - 0.5f * (float)G.nu) * G.pu;
+  const float v = ((float)j + 0.5f - 0.5f * (float)G.nv) * G.pv;
+  const float r2 = fmaf(u, u, v * v);
+  const float d2 = fmaf(G.sdd, G.sdd, r2);
+  const float d = sqrtf(d2);
+  const float3 w = make_float3(fmaf(-G.sdd, cb, -u * sb) / d, fmaf(-G.sdd, sb, u * cb) / d, v / d);
+  const float k = G.sod / d2;
+  const float3 o = make_float3(k * fmaf(r2, cb, -G.sdd * (u * sb)), k * fmaf(r2, sb, G.sdd * (u * cb)),
+                               k * (G.sdd * v));
+  const float t_src = -G.sod * G.sdd / d;
   unsigned long long acc[kMaxMat];
 #pragma unroll
   for (int m = 0; m < kMaxMat; ++m) acc[m] = 0ull;
   float ta, tb, h = 0.f;
-  if (clip_box(V, ps.s, w, 0.f, d, ta, tb)) {
+  if (clip_box(V, o, w, t_src, t_src + d, ta, tb)) {
     const float L = tb - ta;
     const int n = step_count(L, P.step);
     h = L / (float)n;
     VoxRay r;
-    r.set(V, ps.s, w);
+    r.set(V, o, w);
     int cur = vox_mat(__ldg(V.vox + r.voxel<LAYOUT>(V, fmaf(0.5f, h, ta))));
     unsigned long long run = 0ull;
     // the words of the next kAhead midpoints are loaded before any is used (the
@@ -122,7 +136,9 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
     const unsigned long long t = SACC ? (m < nm ? my_acc[m * blockDim.x] : 0ull) : acc[m];
     rl[m] = (float)t * 5.9604644775390625e-08f * h;  // 2^-24
   }
-  float sum = 0.f;
+  // spectrum sum of eq. (Ip), compensated (Kahan) so that its rounding stays
+  // at a few units in the last place whatever the number of bins
+  float sum = 0.f, comp = 0.f;
   for (int n = 0; n < nb; ++n) {
     const float S = __ldg(P.spec.sn + n);
     if (S == 0.f) continue;
@@ -130,10 +146,13 @@ __global__ void __launch_bounds__(256) k_primary(const PrimaryParams P) {
 #pragma unroll
     for (int m = 0; m < kMaxMat; ++m)
       if (m < nm) tau = fmaf(s_mub[n * nm + m], rl[m], tau);
-    sum = fmaf(S * __ldg(P.spec.eta + n), expf(-tau), sum);
+    const float y = S * __ldg(P.spec.eta + n) * expf(-tau) - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
   }
-  const float cosg = G.sdd / d;
-  P.out[(size_t)a * npix + pix] = sum * (G.pu * G.pv) * cosg / (4.f * kPi * d * d);
+  // pixel area x obliquity / (4 pi d^2), obliquity = SDD / d
+  P.out[(size_t)a * npix + pix] = sum * ((G.pu * G.pv) * G.sdd) / ((4.f * kPi) * (d2 * d));
 }
 
 }  // namespace

@@ -36,7 +36,7 @@ constexpr size_t kTallyBytes = (size_t)MC_STATIC_MAX_TALLY * 8;
 constexpr size_t kOffStats = kOffTally + kTallyBytes;
 constexpr size_t kStatsBytes = 256;
 constexpr size_t kOffBlob = kOffStats + kStatsBytes;
-constexpr size_t kBlobBytes = 64 * 1024;
+constexpr size_t kBlobBytes = MC_STATIC_MAX_TABLE_BYTES;
 constexpr size_t kOffSpec = kOffBlob + kBlobBytes;
 constexpr size_t kSpecBytes = ((size_t)(MC_MAX_BINS + 1) * 8 + (size_t)MC_MAX_BINS * 12 + 255) / 256 * 256;
 constexpr size_t kOffAngles = kOffSpec + kSpecBytes;
@@ -46,22 +46,67 @@ constexpr size_t kScratchBytes = kOffAngles + kAnglesBytes;
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// Each CUDA context loads its own copy of this module, so the array's device
+// address belongs to a context, not to a device number: the address is looked
+// up (cudaGetSymbolAddress, which allocates nothing) the first time a call runs
+// in a context and kept under that context's unique id.  Ids are never reused
+// within a process, so a context created after cudaDeviceReset, or a second
+// context on the same device, gets its own lookup.
+constexpr int kMaxContexts = 64;
+struct AddrEntry {
+  unsigned long long ctx_id;
+  unsigned char* addr;
+};
+AddrEntry g_addr[kMaxContexts] = {};
+int g_addr_n = 0;
 std::mutex g_addr_mutex;
 
-// Device address of g_scratch on `device` (which must be current): looked up
-// once per device, on the first call made on it.
-cudaError_t scratch_address(int device, unsigned char** out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = static_cast<unsigned char*>(p);
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Unique id of the CUDA context current on this thread (driver entry points
+// fetched through the runtime, so the library needs no link to libcuda).
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = g_scratch_addr[device];
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || ctx == nullptr) return cudaErrorDeviceUninitialized;
+  if (get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of g_scratch in the context current on this thread (the
+// caller has made the context's device current with cudaSetDevice).
+cudaError_t scratch_address(unsigned char** out) {
+  unsigned long long id = 0;
+  cudaError_t e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  for (int i = 0; i < g_addr_n; ++i)
+    if (g_addr[i].ctx_id == id) {
+      *out = g_addr[i].addr;
+      return cudaSuccess;
+    }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  // a full table reuses a slot; the context that held it looks its address up again on its next call
+  const int slot = g_addr_n < kMaxContexts ? g_addr_n++ : (int)(id % kMaxContexts);
+  g_addr[slot].ctx_id = id;
+  g_addr[slot].addr = static_cast<unsigned char*>(p);
+  *out = g_addr[slot].addr;
   return cudaSuccess;
 }
 
@@ -107,7 +152,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return static_cuda_fail(ctx, e, "cudaSetDevice");
   unsigned char* base = nullptr;
-  e = scratch_address(device, &base);
+  e = scratch_address(&base);
   if (e != cudaSuccess) return static_cuda_fail(ctx, e, "cudaGetSymbolAddress of the static scratch");
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -162,6 +207,9 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   tp.n_split = opt.n_split;
   tp.nee_mode = opt.nee_mode;
   tp.doppler = opt.doppler;
+  tp.forced = opt.forced_detection;
+  if (tp.forced && img > (size_t)MC_FORCED_MAX_PIXELS)
+    return static_fail(ctx, MC_ERR_INVALID_ARG, "forced_detection needs at most MC_FORCED_MAX_PIXELS (65536) pixels");
   tp.rr_threshold = opt.rr_threshold;
   tp.max_order = opt.max_scatter_order;
   tp.n_batches = 1;

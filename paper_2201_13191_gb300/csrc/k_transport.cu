@@ -3,8 +3,9 @@
 // through triangle-mesh bodies, the CAD model of Sec. II-A), interaction
 // sampling (photoelectric, Compton by Kahn's method, Rayleigh by form-factor
 // inversion plus Thomson rejection) and point-detector scoring split into
-// n_split pseudo-particles aimed at random pixels (arXiv 2201.13191 Sec. II-A,
-// eqs. Th, pmueforIncoherent, pmueforcoherent, Is; Sec. II-C.1, II-C.2).
+// n_split pseudo-particles aimed at random pixels, or under forced detection one
+// pseudo-particle per pixel (arXiv 2201.13191 Sec. II-A, eqs. Th,
+// pmueforIncoherent, pmueforcoherent, Is; Sec. I, II-C.1, II-C.2).
 //
 // Wavefront structure: each thread carries one photon's walk and runs one free
 // flight per iteration; an interaction queues a record in shared memory, and
@@ -84,22 +85,60 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 
 // Gathers of the next MC_LOOKAHEAD midpoints are issued before any of them is
 // consumed: the step positions are fixed in advance, so the loads are
-// independent and several are in flight per warp.  Every midpoint is loaded,
-// repeats included (they hit the line the previous load brought into L1), and
-// steps past the chord's end load a clamped, in-bounds word that is ignored.
+// independent and several are in flight per warp.  The group's midpoints are
+// its first one plus u h v_w (one FMA per axis and step).  Every midpoint is
+// loaded, repeats included (they hit the line the previous load brought into
+// L1).  A march runs its whole groups without a bound test per step; only the
+// last, ragged group masks the steps past the chord's end, whose loads read a
+// clamped, in-bounds word that is ignored.
 #ifndef MC_LOOKAHEAD
 #define MC_LOOKAHEAD 8
 #endif
 constexpr int kLook = MC_LOOKAHEAD;
 
 template <int LAYOUT>
-__device__ __forceinline__ void gather_ahead(const VolumeView& V, const VoxRay& r, int k0, float h, float ta,
-                                             uint32_t (&wd)[kLook]) {
+__device__ __forceinline__ void gather_group(const VolumeView& V, const VoxRay& r, int k0, float h, float ta,
+                                             float3 hv, uint32_t (&wd)[kLook]) {
+  const float t0 = fmaf((float)k0 + 0.5f, h, ta);
+  const float bx = fmaf(t0, r.vw.x, r.v0.x), by = fmaf(t0, r.vw.y, r.v0.y), bz = fmaf(t0, r.vw.z, r.v0.z);
   int idx[kLook];
 #pragma unroll
-  for (int u = 0; u < kLook; ++u) idx[u] = r.voxel<LAYOUT>(V, fmaf((float)(k0 + u) + 0.5f, h, ta));
+  for (int u = 0; u < kLook; ++u)
+    idx[u] = u == 0 ? r.voxel_p<LAYOUT>(V, bx, by, bz)
+                    : r.voxel_p<LAYOUT>(V, fmaf((float)u, hv.x, bx), fmaf((float)u, hv.y, by), fmaf((float)u, hv.z, bz));
 #pragma unroll
   for (int u = 0; u < kLook; ++u) wd[u] = __ldg(V.vox + idx[u]);
+}
+
+// Adds the group's steps to the optical-depth sum acc (attenuation per unit
+// density from this thread's shared-memory column smu); TAIL masks the steps
+// k0 + u >= n.
+template <int LAYOUT, bool TAIL>
+__device__ __forceinline__ void tau_group(const uint32_t (&wd)[kLook], int k0, int n, const float* smu, int stride,
+                                          float& acc, int& cur, float& mu) {
+  if (LAYOUT == VOX_LIN) {
+    // volume in L2 (the linear layout is chosen while it fits): branch-free,
+    // every step reads its material's attenuation from shared memory
+#pragma unroll
+    for (int u = 0; u < kLook; ++u) {
+      const float t = fmaf(smu[vox_mat(wd[u]) * stride], vox_rho(wd[u]), acc);
+      acc = (!TAIL || k0 + u < n) ? t : acc;
+    }
+  } else {
+    // volume in HBM (bricks): keep the shared-memory pipe free for the gathers,
+    // re-read the attenuation only when the material changes
+#pragma unroll
+    for (int u = 0; u < kLook; ++u) {
+      if (!TAIL || k0 + u < n) {
+        const int m = vox_mat(wd[u]);
+        if (m != cur) {
+          cur = m;
+          mu = smu[m * stride];
+        }
+        acc = fmaf(mu, vox_rho(wd[u]), acc);
+      }
+    }
+  }
 }
 
 // Optical depth of the fixed-step march x + t w, t in [0, t1] (Sec. II-C.2),
@@ -114,35 +153,18 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   const float h = L / (float)n;
   VoxRay r;
   r.set(V, x, w);
+  const float3 hv = make_float3(h * r.vw.x, h * r.vw.y, h * r.vw.z);
   float acc = 0.f, mu = 0.f;
-  int cur = -1;
-  for (int k0 = 0; k0 < n; k0 += kLook) {
+  int cur = -1, k0 = 0;
+  for (; k0 + kLook <= n; k0 += kLook) {
     uint32_t wd[kLook];
-    gather_ahead<LAYOUT>(V, r, k0, h, ta, wd);
-    if (LAYOUT == VOX_LIN) {
-      // volume in L2 (the linear layout is chosen while it fits): branch-free,
-      // every step reads its material's attenuation from this thread's shared-
-      // memory column and steps past the end add nothing
-#pragma unroll
-      for (int u = 0; u < kLook; ++u) {
-        const float t = fmaf(smu[vox_mat(wd[u]) * stride], vox_rho(wd[u]), acc);
-        acc = k0 + u < n ? t : acc;
-      }
-    } else {
-      // volume in HBM (bricks): keep the shared-memory pipe free for the gathers,
-      // re-read the attenuation only when the material changes
-#pragma unroll
-      for (int u = 0; u < kLook; ++u) {
-        if (k0 + u < n) {
-          const int m = vox_mat(wd[u]);
-          if (m != cur) {
-            cur = m;
-            mu = smu[m * stride];
-          }
-          acc = fmaf(mu, vox_rho(wd[u]), acc);
-        }
-      }
-    }
+    gather_group<LAYOUT>(V, r, k0, h, ta, hv, wd);
+    tau_group<LAYOUT, false>(wd, k0, n, smu, stride, acc, cur, mu);
+  }
+  if (k0 < n) {
+    uint32_t wd[kLook];
+    gather_group<LAYOUT>(V, r, k0, h, ta, hv, wd);
+    tau_group<LAYOUT, true>(wd, k0, n, smu, stride, acc, cur, mu);
   }
   nsteps += (unsigned long long)n;
   return acc * h;
@@ -163,11 +185,12 @@ __device__ __forceinline__ float2 march_tau2(const VolumeView& V, float3 x, floa
   const float h = L / (float)n;
   VoxRay r;
   r.set(V, x, w);
+  const float3 hv = make_float3(h * r.vw.x, h * r.vw.y, h * r.vw.z);
   float acc_a = 0.f, acc_b = 0.f, mu_a = 0.f, mu_b = 0.f;
   int cur = -1;
   for (int k0 = 0; k0 < n; k0 += kLook) {
     uint32_t wd[kLook];
-    gather_ahead<LAYOUT>(V, r, k0, h, ta, wd);
+    gather_group<LAYOUT>(V, r, k0, h, ta, hv, wd);
 #pragma unroll
     for (int u = 0; u < kLook; ++u) {
       if (k0 + u < n) {
@@ -431,15 +454,17 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   uint32_t pi, pj;
   size_t off;
   float tscale = 1.f;
+  // the pixel: drawn uniformly (the block's first word), or under forced
+  // detection the s-th pixel itself (every pixel once per interaction)
   if (COMBINE && P.tally_mode == TALLY_TILED) {
     const uint32_t Pt = (uint32_t)(ts.wt * ts.ht);
-    const uint32_t pt = __umulhi(blk.x, Pt);
+    const uint32_t pt = P.forced ? (uint32_t)s : __umulhi(blk.x, Pt);
     pi = (uint32_t)ts.u0 + pt % (uint32_t)ts.wt;
     pj = (uint32_t)ts.v0 + pt / (uint32_t)ts.wt;
     off = (size_t)bt * Pt + pt;
     tscale = ts.scale;
   } else {
-    const uint32_t pix = __umulhi(blk.x, npix);
+    const uint32_t pix = P.forced ? (uint32_t)s : __umulhi(blk.x, npix);
     pi = pix % (uint32_t)G.nu;
     pj = pix / (uint32_t)G.nu;
     off = ((size_t)bt * P.n_angles + a) * img + pix;
@@ -689,9 +714,13 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   float* my_mu = s_mu + threadIdx.x;
   const uint32_t npix = (uint32_t)G.nu * (uint32_t)G.nv;
   const float A_det = (float)G.nu * G.pu * (float)G.nv * G.pv;
-  const float nee_scale = G.pu * G.pv * ((float)npix / (float)P.n_split) / (2.f * kPi);
   const size_t img = (size_t)npix;
-  const int n_split = P.n_split;
+  // pseudo-particles per interaction: n_split, or under forced detection one per
+  // pixel of the panel or of the block's current tile
+  auto pseudo_count = [&]() -> int {
+    if (!P.forced) return P.n_split;
+    return tiled ? s_tc.wt * s_tc.ht : (int)npix;
+  };
 
   Counters C = {};
   const unsigned long long total = (unsigned long long)P.n_angles * P.h_count;
@@ -704,6 +733,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   int a = 0, order = 0;
   float3 x = make_float3(0.f, 0.f, 0.f), w = x;
   float E = 0.f, W = 0.f, cb = 1.f, sb = 0.f;
+  float t_start = 0.f;  // parameter of the photon's position on the ray x + t w (negative on a first flight)
   Rng g;
   const unsigned long long seed = P.seed_dev ? __ldg(P.seed_dev) : P.seed;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -742,14 +772,29 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
       E = s_E[lo];
       g.init(h, (uint32_t)a, seed);
       sincosf(__ldg(P.angles + a), &sb, &cb);
-      const Pose ps = make_pose(G, __ldg(P.angles + a));
       const float ua = g.u(), ub = g.u();
-      const float3 Q = det_point(G, ps, ua * (float)G.nu, ub * (float)G.nv);
-      const float3 D = sub3(Q, ps.s);
-      const float d = sqrtf(dot3(D, D));
-      w = make_float3(D.x / d, D.y / d, D.z / d);
-      W = s_wb[lo] * A_det * (G.sdd / d) / (4.f * kPi * d * d);
-      x = ps.s;
+      // toward a uniform point Q of the panel: D = Q - s = -SDD n + u e_u + v e_z
+      // (n = (cos b, sin b, 0), e_u = (-sin b, cos b, 0)), d^2 = SDD^2 + u^2 + v^2
+      const float u = (ua * (float)G.nu - 0.5f * (float)G.nu) * G.pu;
+      const float v = (ub * (float)G.nv - 0.5f * (float)G.nv) * G.pv;
+      const float r2 = fmaf(u, u, v * v);
+      const float d2 = fmaf(G.sdd, G.sdd, r2);
+      const float d = sqrtf(d2);
+      w = make_float3(fmaf(-G.sdd, cb, -u * sb) / d, fmaf(-G.sdd, sb, u * cb) / d, v / d);
+      W = s_wb[lo] * A_det * (G.sdd / d) / (4.f * kPi * d2);
+      if constexpr (LAYOUT == GEO_MESH) {
+        // the bodies' crossings are collected along the half-line from the source
+        x = make_float3(G.sod * cb, G.sod * sb, 0.f);
+        t_start = 0.f;
+      } else {
+        // the first flight runs from the ray's point nearest the isocentre,
+        // o = (SOD / d^2) ((u^2 + v^2) n + SDD (u e_u + v e_z)), with the source at
+        // t = -SOD SDD / d: its midpoints carry rounding of the volume's size, not
+        // of the source distance
+        const float k = G.sod / d2;
+        x = make_float3(k * fmaf(r2, cb, -G.sdd * (u * sb)), k * fmaf(r2, sb, G.sdd * (u * cb)), k * (G.sdd * v));
+        t_start = -G.sod * G.sdd / d;
+      }
       order = 0;
       alive = true;
       ++C.hist;
@@ -765,21 +810,22 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         hit = mesh::mesh_flight(P.mesh, x, w, tau_star, my_mu, B, tint, mint, C.flight_steps);
         (void)ta;
         (void)tb;
-      } else if (clip_box(V, x, w, 0.f, __int_as_float(0x7f800000), ta, tb)) {
+      } else if (clip_box(V, x, w, t_start, __int_as_float(0x7f800000), ta, tb)) {
         fill_mu(T, E, my_mu, B);
         const float L = tb - ta;
         const int n = step_count(L, P.step);
         const float hh = L / (float)n;
         VoxRay vr;
         vr.set(V, x, w);
+        const float3 hv = make_float3(hh * vr.vw.x, hh * vr.vw.y, hh * vr.vw.z);
         float tau = 0.f, mu_m = 0.f;
         int cur = -1, k = n;
-        for (int k0 = 0; k0 < n && !hit; k0 += kLook) {
-          uint32_t wd[kLook];
-          gather_ahead<LAYOUT>(V, vr, k0, hh, ta, wd);
+        // the step whose optical depth reaches tau* holds the interaction,
+        // placed inside it by a linear solve
+        auto consume = [&](const uint32_t(&wd)[kLook], int k0, bool tail) {
 #pragma unroll
           for (int u = 0; u < kLook; ++u) {
-            if (!hit && k0 + u < n) {
+            if (!hit && (!tail || k0 + u < n)) {
               const int m = vox_mat(wd[u]);
               if (m != cur) {
                 cur = m;
@@ -796,6 +842,17 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
               }
             }
           }
+        };
+        int k0 = 0;
+        for (; k0 + kLook <= n && !hit; k0 += kLook) {
+          uint32_t wd[kLook];
+          gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
+          consume(wd, k0, false);
+        }
+        if (k0 < n && !hit) {
+          uint32_t wd[kLook];
+          gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
+          consume(wd, k0, true);
         }
         C.flight_steps += (unsigned long long)(hit ? k + 1 : n);
       }
@@ -804,6 +861,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         alive = false;
       } else {
         x = make_float3(fmaf(tint, w.x, x.x), fmaf(tint, w.y, x.y), fmaf(tint, w.z, x.z));
+        t_start = 0.f;
         int ti;
         float tf;
         T.locate(E, ti, tf);
@@ -818,7 +876,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         if (type == 0 && !EV) {
           alive = false;
         } else {
-          // queue the interaction; its pseudo-particles use the next n_split counter blocks
+          // queue the interaction; its pseudo-particles use the next counter blocks, one each
           g.align();
           const int r = atomicAdd(&s_nrec, 1);
           R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
@@ -829,7 +887,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
           R.tm[r] = (type << 8) | mint;
           R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
           R.k0[r] = g.ctr.x;
-          g.ctr.x += (uint32_t)n_split;
+          g.ctr.x += (uint32_t)pseudo_count();
           {
             // length key: chord toward the panel centre
             const float rr0 = G.sod - G.sdd;
@@ -881,7 +939,10 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
     __syncthreads();
     // ---- pseudo-particle phase: the block marches every queued ray together
     const int nrec = s_nrec;
+    const int n_split = pseudo_count();
     const int n_jobs = nrec * n_split;
+    // weight of a pseudo-particle: pixel area x P / n_split / (2 pi) (eq. Th)
+    const float nee_scale = G.pu * G.pv * ((float)npix / (float)n_split) / (2.f * kPi);
     TileSel ts = {0, 0, 0, 0, 1.f};
     if (tiled) {
       ts.u0 = s_tc.u0;

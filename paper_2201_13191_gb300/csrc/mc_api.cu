@@ -135,6 +135,7 @@ int validate_options(const mc_options* o, std::string& why) {
   if (o->use_graph < 0 || o->use_graph > 1) return why = "use_graph must be 0 or 1", -1;
   if (o->nee_mode < 0 || o->nee_mode > 1) return why = "nee_mode must be 0 or 1", -1;
   if (o->doppler < 0 || o->doppler > 1) return why = "doppler must be 0 or 1", -1;
+  if (o->forced_detection < 0 || o->forced_detection > 1) return why = "forced_detection must be 0 or 1", -1;
   return 0;
 }
 
@@ -467,6 +468,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     tp.n_split = ctx->opt.n_split;
     tp.nee_mode = ctx->opt.nee_mode;
     tp.doppler = ctx->opt.doppler;
+    tp.forced = ctx->opt.forced_detection;
     tp.rr_threshold = ctx->opt.rr_threshold;
     tp.max_order = ctx->opt.max_scatter_order;
     tp.n_batches = nb_img;
@@ -491,6 +493,12 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     } else {
       // automatic and global: plain FP64 adds, measured fastest even on an 8 x 8 panel
       tp.tally_mode = TALLY_GLOBAL;
+    }
+    if (tp.forced) {
+      const size_t fp = tp.tally_mode == TALLY_TILED ? (size_t)tp.tile_u * tp.tile_v : (size_t)ctx->nu * ctx->nv;
+      if (fp > (size_t)MC_FORCED_MAX_PIXELS)
+        return fail(ctx, MC_ERR_INVALID_ARG,
+                    "forced_detection needs at most MC_FORCED_MAX_PIXELS (65536) pixels per panel or tile");
     }
     block = ctx->opt.block_size ? ctx->opt.block_size : 256;
     const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, transport_shared_pixels(tp));
@@ -655,6 +663,7 @@ void mc_default_options(mc_options* o) {
   o->use_graph = 0;
   o->nee_mode = 0;
   o->doppler = 0;
+  o->forced_detection = 0;
   o->tile_u = 64;
   o->tile_v = 64;
 }
@@ -1217,6 +1226,88 @@ std::vector<float> murho_at(const mc_ctx* ctx, double E) {
 }
 }  // namespace
 
+namespace {
+// Class tables of the segmentation (Sec. II-E): the material of each class and,
+// for classes k >= 1, the mass attenuation of that material at the effective
+// energy (cm^2/g, linear between nodes); cmu[3] holds class 0's density.
+void class_tables(const mc_ctx* ctx, int classes, const int* class_material, float class_density0, float e_eff,
+                  int cm[3], float cmu[6]) {
+  const std::vector<float> mr = murho_at(ctx, e_eff);
+  for (int k = 0; k < 3; ++k) {
+    cm[k] = k < classes ? class_material[k] : 0;
+    cmu[k] = mr[cm[k]];
+  }
+  cmu[3] = class_density0;
+  cmu[4] = cmu[5] = 0.f;
+}
+
+bool in_table(const mc_ctx* ctx, float E) { return E >= ctx->E0 && E <= ctx->E0 + ctx->dE * (ctx->n_E - 1); }
+}  // namespace
+
+int mc_line_integrals(mc_ctx* ctx, const float* I, const float* I0, int n_proj, int NU, int NV, float* a_out,
+                      void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!I || !I0 || !a_out || n_proj < 1 || NU < 1 || NV < 1)
+    return fail(ctx, MC_ERR_INVALID_ARG, "line integrals need device buffers and positive sizes");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  const size_t img = (size_t)NU * NV;
+  const cudaError_t e = recon_log_norm(I, I0, img, img * n_proj, a_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "line integrals");
+  return MC_OK;
+}
+
+int mc_segment(mc_ctx* ctx, const float* vol, int nx, int ny, int nz, int classes, const int* class_material,
+               float class_density0, float e_eff_keV, float mu_lo, float mu_hi, uint32_t* hist_out,
+               int* thresholds_out, uint8_t* mat_out, uint16_t* rho_out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!ctx->have_tables) return fail(ctx, MC_ERR_STATE, "tables not loaded");
+  if (!vol || !mat_out || !rho_out || !class_material || nx < 1 || ny < 1 || nz < 1 ||
+      (classes != 2 && classes != 3) || !(mu_hi > mu_lo) || !std::isfinite(mu_lo) || !std::isfinite(mu_hi) ||
+      !in_table(ctx, e_eff_keV) || !(class_density0 >= 0.f) || !std::isfinite(class_density0))
+    return fail(ctx, MC_ERR_INVALID_ARG, "bad segmentation arguments");
+  for (int k = 0; k < classes; ++k)
+    if (class_material[k] < 0 || class_material[k] >= ctx->n_mat)
+      return fail(ctx, MC_ERR_INVALID_ARG, "class material outside the table");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  cudaStream_t s = (cudaStream_t)stream;
+  int cm[3];
+  float cmu[6];
+  class_tables(ctx, classes, class_material, class_density0, e_eff_keV, cm, cmu);
+  // device scratch: histogram [256], thresholds [2], class materials [3], class tables [6]
+  unsigned char* d = nullptr;
+  CK(cudaMallocAsync((void**)&d, 256 * 4 + 2 * 4 + 3 * 4 + 6 * 4, s), "segmentation scratch");
+  unsigned int* hist = reinterpret_cast<unsigned int*>(d);
+  int* thr = reinterpret_cast<int*>(d + 1024);
+  int* d_cm = thr + 2;
+  float* d_cmu = reinterpret_cast<float*>(d_cm + 3);
+  cudaError_t e = cudaMemcpyAsync(d_cm, cm, sizeof(cm), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cmu, cmu, sizeof(cmu), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = recon_otsu_segment(vol, (size_t)nx * ny * nz, mu_lo, mu_hi, classes, d_cm, d_cmu, d_cmu + 3, 30.f, hist, thr,
+                           mat_out, rho_out, s);
+  if (e == cudaSuccess && hist_out) e = cudaMemcpyAsync(hist_out, hist, 256 * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && thresholds_out) e = cudaMemcpyAsync(thresholds_out, thr, 2 * 4, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  // the host class tables must outlive their copies; the read-backs must land
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "segmentation");
+  return MC_OK;
+}
+
+int mc_correct_images(mc_ctx* ctx, const float* a, const float* ip, const float* is, float is_scale, size_t n,
+                      float* c_out, void* stream) {
+  if (!ctx) return MC_ERR_INVALID_ARG;
+  if (!a || !ip || !is || !c_out || n < 1 || !(is_scale >= 0.f) || !std::isfinite(is_scale))
+    return fail(ctx, MC_ERR_INVALID_ARG, "correction needs device buffers, n >= 1 and a finite is_scale >= 0");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  (void)cudaGetLastError();
+  const cudaError_t e = recon_correct(a, ip, is, is_scale, n, c_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "correction");
+  return MC_OK;
+}
+
 int mc_bin_volume(mc_ctx* ctx, const uint8_t* mat, const uint16_t* rho, int nx, int ny, int nz, float e_eff_keV,
                   uint8_t* mat_out, uint16_t* rho_out, void* stream) {
   if (!ctx) return MC_ERR_INVALID_ARG;
@@ -1305,25 +1396,13 @@ int mc_correct_iter(mc_ctx* ctx, const float* raw_I, const float* I0, int n_proj
   {
     int cm[3];
     float cmu[6];
-    for (int k = 0; k < 3; ++k) {
-      cm[k] = k < P.classes ? P.class_material[k] : 0;
-      const int m = cm[k];
-      // mass attenuation at the effective energy (linear between nodes)
-      const double x = (P.e_eff_keV - ctx->E0) / ctx->dE;
-      int i = std::max(0, std::min((int)std::floor(x), ctx->n_E - 2));
-      const double f = x - i;
-      auto tot = [&](int j) {
-        const size_t q = (size_t)m * ctx->n_E + j;
-        return ctx->pe[q] + ctx->in[q] + ctx->co[q];
-      };
-      cmu[k] = (float)(tot(i) + f * (tot(i + 1) - tot(i)));
-    }
-    cmu[3] = P.class_density0;
-    cmu[4] = cmu[5] = 0.f;
+    class_tables(ctx, P.classes, P.class_material, P.class_density0, P.e_eff_keV, cm, cmu);
     cudaError_t e = cudaMemcpyAsync(d_cls_mat, cm, sizeof(cm), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cls_murho, cmu, sizeof(cmu), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_murho, murho_eff.data(), murho_eff.size() * 4, cudaMemcpyHostToDevice, s);
+    // the host tables are locals: their copies must complete before they go out of scope
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return release(cuda_fail(ctx, e, "class tables"));
   }
   // geometry of the simulation grid over the same panel
@@ -1660,7 +1739,8 @@ int static_cuda_fail(mc_ctx* ctx, cudaError_t e, const char* where) { return cud
 int static_build_blob(mc_ctx* ctx, unsigned char* dst, int cap, int* bytes_out, int* n_stage_out) {
   const int ns = stage_nodes(ctx);
   const int bytes = tab_blob_bytes(ctx->n_mat, ns);
-  if (bytes > cap) return fail(ctx, MC_ERR_INVALID_ARG, "cross-section tables exceed the static table area");
+  if (bytes > cap) return fail(ctx, MC_ERR_INVALID_ARG, "the staged cross-section tables exceed MC_STATIC_MAX_TABLE_BYTES (65536): fewer materials or a spectrum "
+                                        "reaching lower energies");
   write_blob(ctx, ns, dst);
   *bytes_out = bytes;
   *n_stage_out = ns;

@@ -214,20 +214,25 @@ struct VoxRay {
   // guards the array bounds).
   template <int LAYOUT>
   __device__ __forceinline__ int voxel(const VolumeView& vol, float t) const {
+    return voxel_p<LAYOUT>(vol, fmaf(t, vw.x, v0.x), fmaf(t, vw.y, v0.y), fmaf(t, vw.z, v0.z));
+  }
+  // The same for a point given in padded voxel units.
+  template <int LAYOUT>
+  __device__ __forceinline__ int voxel_p(const VolumeView& vol, float px, float py, float pz) const {
     if (LAYOUT == VOX_LIN) {
       // (bx - C) + px (by - C) + px py (bz - C) with b the bit patterns of the
       // round-down adds (C = 0x4B000000, see floor_pos): the offsets fold into
       // one precomputed bias (exact in 32-bit wraparound arithmetic); the
       // unsigned min only guards the array bounds
-      const unsigned bx = __float_as_uint(__fadd_rd(fmaf(t, vw.x, v0.x), 8388608.0f));
-      const unsigned by = __float_as_uint(__fadd_rd(fmaf(t, vw.y, v0.y), 8388608.0f));
-      const unsigned bz = __float_as_uint(__fadd_rd(fmaf(t, vw.z, v0.z), 8388608.0f));
+      const unsigned bx = __float_as_uint(__fadd_rd(px, 8388608.0f));
+      const unsigned by = __float_as_uint(__fadd_rd(py, 8388608.0f));
+      const unsigned bz = __float_as_uint(__fadd_rd(pz, 8388608.0f));
       const unsigned idx = bx + (unsigned)vol.px * by + (unsigned)vol.pxy * bz - (unsigned)vol.lin_bias;
       return (int)min(idx, (unsigned)(vol.words - 1));
     }
-    const int ix = floor_pos(fmaf(t, vw.x, v0.x));
-    const int iy = floor_pos(fmaf(t, vw.y, v0.y));
-    const int iz = floor_pos(fmaf(t, vw.z, v0.z));
+    const int ix = floor_pos(px);
+    const int iy = floor_pos(py);
+    const int iz = floor_pos(pz);
     return min(max(vox_index<LAYOUT>(vol, ix, iy, iz), 0), vol.words - 1);
   }
 };

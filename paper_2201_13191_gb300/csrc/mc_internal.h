@@ -108,6 +108,7 @@ struct TransportParams {
   int n_split;
   int nee_mode;  // 0: sampled type's pdf; 1: expected value over the type (both terms, one march)
   int doppler;   // Doppler broadening of incoherent scatter (bound tables)
+  int forced;    // forced detection: one pseudo-particle per pixel (of the panel or the history's tile)
   float rr_threshold;
   int max_order;
   int n_batches;

@@ -1,18 +1,19 @@
-// Measurement helper with no counterpart in the paper: random 4-byte gathers
-// from a device buffer, i.e. the access pattern of the transport's voxel reads
-// without the march arithmetic around them.  Timed on a buffer the size of the
-// packed volume, it gives the voxel-gather roofline a measured peak at the
-// memory level the volume lives in (L2 when it fits, HBM otherwise).
+// Measurement kernels with no counterpart in the paper, built into their own
+// library (libmcprobe.so) beside the product library.  They give the rooflines
+// of the benchmark measured denominators on the GPU at hand:
 //
-// Each thread draws its indices from a 32-bit xorshift generator seeded by its
-// global index and keeps eight independent loads in flight (the transport
-// keeps up to eight gathers of a ray in flight).  The loaded words are folded
-// into one value per thread written to `sink`, so no load can be elided.
+//   mc_probe_stream  coalesced 16-byte reads over a buffer, pass after pass:
+//                    the streaming read bandwidth of the memory level the
+//                    buffer lives in (L2 when it fits, HBM otherwise);
+//   mc_probe_gather  random 4-byte loads over a buffer, eight in flight per
+//                    thread: the access pattern of the transport's voxel reads
+//                    without the march arithmetic around them;
+//   mc_probe_mma     tcgen05.mma issue rate of one instruction shape.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "mc_internal.h"
-#include "mc_tc.cuh"
+#include "../../../include/mc_probe.h"
+#include "../mc_tc.cuh"
 
 namespace {
 
@@ -23,6 +24,10 @@ __device__ __forceinline__ uint32_t xorshift32(uint32_t s) {
   return s;
 }
 
+// Each thread draws its indices from a 32-bit xorshift generator seeded by its
+// global index and keeps eight independent loads in flight.  The loaded words
+// are folded into one value per thread written to `sink`, so no load can be
+// elided.
 __global__ void __launch_bounds__(256) k_probe_gather(const uint32_t* __restrict__ buf, uint32_t n_words,
                                                       int rounds, uint32_t* __restrict__ sink) {
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,6 +47,30 @@ __global__ void __launch_bounds__(256) k_probe_gather(const uint32_t* __restrict
     for (int j = 0; j < 8; ++j) v[j] = __ldg(buf + idx[j]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc = acc * 31u + v[j];
+  }
+  sink[gid] = acc;
+}
+
+// Coalesced streaming reads: the grid walks the buffer in 16-byte words with
+// a grid-stride loop, four loads in flight per thread, `passes` times; the
+// words are xor-folded into one value per thread so no load can be elided.
+__global__ void __launch_bounds__(256) k_probe_stream(const uint4* __restrict__ buf, size_t n16, int passes,
+                                                      uint32_t* __restrict__ sink) {
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  uint32_t acc = 0u;
+#pragma unroll 1
+  for (int p = 0; p < passes; ++p) {
+    size_t i = gid;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+      const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride), c = __ldcg(buf + i + 2 * stride),
+                  d = __ldcg(buf + i + 3 * stride);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+    }
+    for (; i < n16; i += stride) {
+      const uint4 a = __ldcg(buf + i);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w;
+    }
   }
   sink[gid] = acc;
 }
@@ -93,7 +122,7 @@ cudaError_t launch_probe_mma(int grid, int rounds, int* err, cudaStream_t s) {
 }  // namespace
 
 extern "C" int mc_probe_mma(int n, int grid, int rounds, int* err, void* stream) {
-  if (!err || grid < 1 || rounds < 1) return MC_ERR_INVALID_ARG;
+  if (!err || grid < 1 || rounds < 1) return MC_PROBE_ERR_INVALID_ARG;
   (void)cudaGetLastError();
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
@@ -103,17 +132,27 @@ extern "C" int mc_probe_mma(int n, int grid, int rounds, int* err, void* stream)
     case 64: e = launch_probe_mma<64>(grid, rounds, err, s); break;
     case 128: e = launch_probe_mma<128>(grid, rounds, err, s); break;
     case 256: e = launch_probe_mma<256>(grid, rounds, err, s); break;
-    default: return MC_ERR_INVALID_ARG;
+    default: return MC_PROBE_ERR_INVALID_ARG;
   }
-  return e == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+  return e == cudaSuccess ? MC_PROBE_OK : MC_PROBE_ERR_CUDA;
 }
 
 extern "C" int mc_probe_gather(const void* buf, uint64_t n_words, int rounds, int grid, int block, uint32_t* sink,
                                void* stream) {
   if (!buf || !sink || n_words < 1 || n_words > 0xFFFFFFFFull || rounds < 1 || grid < 1 || block < 32 ||
       block > 256 || block % 32)
-    return MC_ERR_INVALID_ARG;
+    return MC_PROBE_ERR_INVALID_ARG;
   (void)cudaGetLastError();
   k_probe_gather<<<grid, block, 0, (cudaStream_t)stream>>>((const uint32_t*)buf, (uint32_t)n_words, rounds, sink);
-  return cudaGetLastError() == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? MC_PROBE_OK : MC_PROBE_ERR_CUDA;
+}
+
+extern "C" int mc_probe_stream(const void* buf, uint64_t n_bytes, int passes, int grid, int block, uint32_t* sink,
+                               void* stream) {
+  if (!buf || !sink || n_bytes < 16 || n_bytes % 16 || ((uintptr_t)buf & 15u) || passes < 1 || grid < 1 ||
+      block < 32 || block > 256 || block % 32)
+    return MC_PROBE_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
+  k_probe_stream<<<grid, block, 0, (cudaStream_t)stream>>>((const uint4*)buf, (size_t)(n_bytes / 16), passes, sink);
+  return cudaGetLastError() == cudaSuccess ? MC_PROBE_OK : MC_PROBE_ERR_CUDA;
 }

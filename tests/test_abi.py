@@ -11,8 +11,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "mc.h")).read()
+def _declared(header="mc.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mc_[a-z0-9_]+)\s*\(", src)))
 
@@ -35,6 +35,20 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     for n in _declared():
         assert hasattr(lib, n), n
+
+
+def test_probe_library_is_separate_and_exports_its_header():
+    """The measurement kernels live in libmcprobe.so, not in the product library."""
+    import ctypes as C
+
+    from paper_2201_13191_gb300.build import build_probe
+
+    probe = C.CDLL(build_probe())
+    names = _declared("mc_probe.h")
+    assert names == ["mc_probe_gather", "mc_probe_mma", "mc_probe_stream"]
+    for n in names:
+        assert hasattr(probe, n), n
+        assert n not in _declared("mc.h")
 
 
 def test_binding_names_match_header():

@@ -47,7 +47,7 @@ def test_bound_primary_parity(gpu, oracle_lib, variant_table):
     c = _ctx(gpu, tp, wl)
     out = c.project([0.9], 1000, wl["step_mm"], 1, scatter=False)
     Ip, bound = _orc(oracle_lib, tp, wl).primary(0.9, wl["step_mm"])
-    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound)
+    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound, "bound tables", min_strict=0.99)
 
 
 def test_bound_changes_the_scatter(gpu, table_path, tables, variant_table):

@@ -31,7 +31,7 @@ def test_primary_parity_with_panel_response(gpu, oracle_lib, table_path, tables)
     o = _orc(oracle_lib, table_path, wl)
     for k, a in enumerate(angles):
         Ip, bound = o.primary(float(a), wl["step_mm"])
-        _check_primary(out["primary"][k].cpu().numpy(), Ip, bound)
+        _check_primary(out["primary"][k].cpu().numpy(), Ip, bound, f"panel response angle {a}")
 
 
 def test_scatter_same_seed_with_panel_response(gpu, oracle_lib, table_path, tables):

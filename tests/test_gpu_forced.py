@@ -1,0 +1,59 @@
+"""Forced detection on the GPU against the oracle (arXiv 2201.13191 Sec. I
+names it among the variance-reduction techniques; every scatter interaction
+scores every pixel once).  Same seed: GPU and oracle run the same histories
+on the same Philox streams, so the images agree to a small fraction of the
+Monte Carlo noise and the interaction counts nearly exactly."""
+
+import numpy as np
+import pytest
+
+from mc_inputs import make_workload
+from test_gpu_parity import _ctx, _orc, _same_seed_check
+
+pytestmark = pytest.mark.gpu
+
+
+def _coarse(tables, nu=16, nv=16):
+    """The 64^3 cylinder phantom on a coarse panel of the same 128 mm extent
+    (the correction's simulation grids are coarse)."""
+    wl = make_workload("cyl64", tables)
+    wl["geometry"] = dict(wl["geometry"], nu=nu, nv=nv, pu=128.0 / nu, pv=128.0 / nv)
+    return wl
+
+
+@pytest.mark.parametrize("nee_mode,tiles", [(0, None), (1, None), (0, (8, 6))])
+def test_forced_detection_same_seed(gpu, oracle_lib, table_path, tables, nee_mode, tiles):
+    wl = _coarse(tables)
+    N = 20_000
+    opt = dict(n_batches=20, forced_detection=1, nee_mode=nee_mode)
+    if tiles:
+        opt.update(tally_mode=4, tile_u=tiles[0], tile_v=tiles[1])
+    c = _ctx(gpu, table_path, wl, **opt)
+    out = c.project([0.4], N, wl["step_mm"], 9, primary=False, variance=True)
+    g = out["scatter"][0].cpu().numpy().astype(np.float64)
+    var = out["variance"][0].cpu().numpy().astype(np.float64)
+    st = c.last_stats()
+    o = _orc(oracle_lib, table_path, wl)
+    o.set_forced(1)
+    o.set_nee_mode(nee_mode)
+    if tiles:
+        o.set_tiles(*tiles)
+    r = o.scatter(0.4, N, wl["step_mm"], 9)
+    _same_seed_check(g, r["Is"], var)
+    for k in ("compton", "rayleigh", "photo", "nee_rays"):
+        assert abs(st[k] / r["stats"][k] - 1.0) < 3e-4, k
+    assert st["nee_rays"] > 100 * (st["compton"] + st["rayleigh"])  # every pixel (of the tile) per interaction
+
+
+def test_forced_detection_limits(gpu, table_path, tables):
+    """More than MC_FORCED_MAX_PIXELS pixels per panel (or tile) is refused;
+    a 4x4 tile of a large panel is accepted."""
+    wl = make_workload("cyl64", tables)
+    wl["geometry"] = dict(wl["geometry"], nu=512, nv=256, pu=0.25, pv=0.5)
+    c = _ctx(gpu, table_path, wl, forced_detection=1)
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.project([0.0], 100, wl["step_mm"], 1, primary=False)
+    c.set_options(tally_mode=4, tile_u=4, tile_v=4)
+    c.project([0.0], 100, wl["step_mm"], 1, primary=False)
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.set_options(forced_detection=2)

@@ -1,9 +1,10 @@
 """GPU vs oracle parity through the C ABI (arXiv 2201.13191 Sec. II-A, II-C).
 
 Primary images (eq. Ip) must match the FP64 oracle to 1e-5 relative per
-pixel; the only allowance is the oracle's own per-pixel bound of what an FP32
-re-evaluation may legitimately change (midpoints within 2e-4 voxel of a face
-between different voxels, FP32 rounding of the chord length).  Scatter images
+pixel; the only allowance is for the pixels the oracle flags, whose rays have a
+midpoint within 2e-4 voxel of a face between different voxels or a step count
+within rounding of an integer, by what the neighbouring voxel or step count
+changes.  Scatter images
 (eq. Is) are compared two ways: with the same seed, where GPU and oracle run
 the same histories on the same Philox4x32-10 streams and must agree nearly
 history for history; and with independent seeds, where they must agree within
@@ -43,17 +44,27 @@ def _small_poly_workload(tables, n=64, dv=2.0, nu=96, nv=80):
     )
 
 
-def _check_primary(gpu_img, orc_img, bound):
-    """1e-5 relative per pixel; a pixel the oracle flags may also move by what
-    its flagged midpoints, its chord rounding or an ambiguous step count allow
-    (bound is an optical depth: relative change expm1(bound))."""
+def _check_primary(gpu_img, orc_img, bound, label="", min_strict=0.98):
+    """1e-5 relative per pixel.  The oracle flags a pixel (bound > 0) when one
+    of its midpoints lies within 2e-4 voxel of a face between different voxels
+    or when its step count ceil(L/step) is within rounding of an integer; bound
+    is then the optical depth that the neighbouring voxel or step count can
+    change, and the pixel may move by expm1(bound) beyond 1e-5.  Every
+    unflagged pixel meets 1e-5 outright (measured: at most 2.1e-6).  Prints
+    the flagged count; min_strict is the fraction of all pixels meeting 1e-5
+    outright, set at the level measured on each workload (0.985 to 1.0)."""
     rel = np.abs(gpu_img.astype(np.float64) / orc_img - 1.0)
     assert np.all(np.isfinite(bound))
-    assert np.all(rel <= 1e-5 + np.expm1(bound)), (rel - np.expm1(bound)).max()
-    strict = np.mean(rel <= 1e-5)
-    # nearly every pixel meets 1e-5 outright; the rest are flagged ones
-    assert strict >= 0.95, strict
-    assert np.all((rel <= 1e-5) | (bound > 0))
+    flagged = bound > 0
+    n = rel.size
+    worst_u = float(rel[~flagged].max()) if np.any(~flagged) else 0.0
+    worst_f = float(rel[flagged].max()) if np.any(flagged) else 0.0
+    strict = float(np.mean(rel <= 1e-5))
+    print(f"primary parity {label}: {n} pixels, flagged {int(flagged.sum())} ({flagged.mean():.2e}), "
+          f"strict {strict:.6f}, max rel unflagged {worst_u:.2e}, flagged {worst_f:.2e}")
+    assert worst_u <= 1e-5, worst_u
+    assert np.all(rel[flagged] <= 1e-5 + np.expm1(bound[flagged])), (rel - np.expm1(bound)).max()
+    assert strict >= min_strict, strict
     return strict
 
 
@@ -63,7 +74,7 @@ def test_primary_parity_cylinder(gpu, oracle_lib, table_path, tables, angle):
     c = _ctx(gpu, table_path, wl)
     out = c.project([angle], 1000, wl["step_mm"], 1, scatter=False)
     Ip, bound = _orc(oracle_lib, table_path, wl).primary(angle, wl["step_mm"])
-    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound)
+    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound, f"cyl64 angle {angle}")
 
 
 def test_primary_parity_polyenergetic_ragged(gpu, oracle_lib, table_path, tables):
@@ -74,7 +85,17 @@ def test_primary_parity_polyenergetic_ragged(gpu, oracle_lib, table_path, tables
     o = _orc(oracle_lib, table_path, wl)
     for k, a in enumerate(angles):
         Ip, bound = o.primary(float(a), wl["step_mm"])
-        _check_primary(out["primary"][k].cpu().numpy(), Ip, bound)
+        _check_primary(out["primary"][k].cpu().numpy(), Ip, bound, f"ell64 ragged angle {a}")
+
+
+def test_primary_parity_full_size_ell256(gpu, oracle_lib, table_path, tables):
+    """The benchmark's workload at full size (256^3 ellipsoids, 512^2 panel,
+    111-bin spectrum, step 0.25 mm): every pixel against the oracle."""
+    wl = make_workload("ell256", tables)
+    c = _ctx(gpu, table_path, wl)
+    out = c.project([0.0], 1000, wl["step_mm"], 1, scatter=False)
+    Ip, bound = _orc(oracle_lib, table_path, wl).primary(0.0, wl["step_mm"])
+    _check_primary(out["primary"][0].cpu().numpy(), Ip, bound, "ell256 full size", min_strict=0.99)
 
 
 def _same_seed_check(g, ref, var, frac=0.1):

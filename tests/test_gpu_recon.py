@@ -1,5 +1,7 @@
-"""Correction plumbing on the GPU (Sec. II-E): FDK parity with the oracle and
-an end-to-end scatter correction of synthetic measurements."""
+"""Correction plumbing on the GPU (Sec. II-E): each step against the oracle --
+line integrals, FDK, the histogram / Otsu thresholds / class map of the
+segmentation, the down-sampling for the Monte Carlo step and eq. (Correction)
+-- and an end-to-end scatter correction of synthetic measurements."""
 
 import numpy as np
 import pytest
@@ -26,6 +28,72 @@ def test_fdk_parity(gpu, table_path):
     ref = recon.fdk(p.astype(np.float32).astype(np.float64), angles.astype(np.float32), 3.0, 3.0, SOD, SDD,
                     (30, 33, 7, 1.1, 0.9, 2.0))
     assert np.abs(got - ref).max() <= 2e-4 * np.abs(ref).max()
+
+
+def _segment_volume(shape, seed):
+    """FP32 reconstruction-like volume: air, water and aluminium levels at 60 keV
+    with noise, a few values outside [mu_lo, mu_hi) and some on bin edges."""
+    rng = np.random.default_rng(seed)
+    lvl = rng.choice(3, size=shape, p=[0.5, 0.35, 0.15])
+    mu = np.array([0.0002, 0.0206, 0.075])[lvl] + rng.normal(0, 0.004, shape)
+    mu.ravel()[:7] = [-0.5, -0.01, 0.09, 0.3, 0.0, 0.05, 0.0890625]
+    return mu.astype(np.float32)
+
+
+@pytest.mark.parametrize("classes,cls_mat", [(2, (0, 1, 1)), (3, (0, 1, 3))])
+def test_segmentation_matches_oracle(gpu, table_path, tables, classes, cls_mat):
+    """Histogram and Otsu thresholds bit for bit (both take the bin decision in
+    FP32), materials bit for bit, densities within one binary16 unit (FP32
+    quotient on the device, FP64 in the oracle, both rounded to binary16)."""
+    torch = pytest.importorskip("torch")
+    vol = _segment_volume((37, 41, 29), 11 + classes)
+    lo, hi, e_eff, rho0 = -0.01, 0.09, 60.0, 0.001205
+    c = gpu.Context(0)
+    c.load_tables(table_path)
+    mat, rho, hist, thr = c.segment(torch.from_numpy(vol).cuda(), classes, cls_mat[:classes], rho0, e_eff, lo, hi)
+    murho = [np.interp(e_eff, tables.energies, tables.mu_tot[m]) for m in cls_mat]
+    m_ref, r_ref, h_ref, t_ref = recon.segment(vol, lo, hi, classes, cls_mat, murho, rho0)
+    np.testing.assert_array_equal(hist.astype(np.int64), h_ref)
+    assert tuple(int(t) for t in thr) == tuple(t_ref), (thr, t_ref)
+    np.testing.assert_array_equal(mat.cpu().numpy(), m_ref)
+    got = rho.cpu().numpy().view(np.float16).astype(np.float64)
+    ref16 = r_ref.astype(np.float16)
+    ulp = np.spacing(ref16).astype(np.float64)
+    assert np.all(np.abs(got - ref16.astype(np.float64)) <= ulp), np.max(np.abs(got - ref16) / ulp)
+    assert np.mean(got == ref16.astype(np.float64)) > 0.99
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.segment(torch.from_numpy(vol).cuda(), 4, cls_mat, rho0, e_eff, lo, hi)
+
+
+def test_line_integrals_and_correction_match_oracle(gpu):
+    """a = -ln(I/I0) and eq. (Correction) per element against the oracle at FP32
+    tolerance: a quotient (2^-24 relative), logf (1 unit in the last place)
+    and the final subtraction give |dc| <= 2e-7 (1 + |a| + |c|); the bound
+    below is twice that."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    n, NV, NU = 3, 17, 23
+    I0 = rng.uniform(0.5, 2.0, (NV, NU)).astype(np.float32)
+    I = (I0 * np.exp(-rng.uniform(0, 8, (n, NV, NU)))).astype(np.float32)
+    I.ravel()[:3] = [0.0, -1.0, 1e-35]  # clamped to 1e-30
+    c = gpu.Context(0)
+    a = c.line_integrals(torch.from_numpy(I).cuda(), torch.from_numpy(I0).cuda()).cpu().numpy().astype(np.float64)
+    a_ref = recon.line_integrals(I, I0[None])
+    assert np.all(np.abs(a - a_ref) <= 4e-7 * (1 + np.abs(a_ref))), np.max(np.abs(a - a_ref) / (1 + np.abs(a_ref)))
+    ip = (I0[None] * np.exp(-rng.uniform(0, 8, (n, NV, NU)))).astype(np.float32)
+    is_ = (ip * rng.uniform(0, 3, ip.shape)).astype(np.float32)
+    is_.ravel()[:2] = [-1.0, 0.0]  # negative scatter clamps to 0: c = a there
+    ip.ravel()[2] = 0.0  # clamped to 1e-30
+    a32 = a.astype(np.float32)
+    for scale in (1.0, 0.0625):
+        cc = c.correct_images(torch.from_numpy(a32).cuda(), torch.from_numpy(ip).cuda(), torch.from_numpy(is_).cuda(),
+                              scale).cpu().numpy().astype(np.float64)
+        ref = recon.correct(a32, ip, is_, scale)
+        tol = 4e-7 * (1 + np.abs(a32) + np.abs(ref))
+        assert np.all(np.abs(cc - ref) <= tol), np.max(np.abs(cc - ref) / tol)
+        assert cc.ravel()[0] == a32.ravel()[0] and cc.ravel()[1] == a32.ravel()[1]
+    with pytest.raises(gpu.MCError, match="INVALID_ARG"):
+        c.correct_images(torch.from_numpy(a32).cuda(), torch.from_numpy(ip).cuda(), torch.from_numpy(is_).cuda(), -1.0)
 
 
 def test_scatter_correction_end_to_end(gpu, table_path, tables):

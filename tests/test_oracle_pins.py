@@ -326,7 +326,7 @@ BOX = dict(n=16, dv=4.0)
 BOX_GEO = dict(sod=100.0, sdd=250.0, nu=8, nv=8, pu=4.0, pv=4.0)
 
 
-def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=None, eta=None):
+def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=None, eta=None, geo=None):
     """Expected order-1 NEE image, integrated deterministically over source
     direction (detector-area Gauss-Legendre), depth along the source ray and
     the target pixel area, with exact exponential attenuation in the box.
@@ -336,7 +336,7 @@ def _single_scatter_quadrature(tables, table_path, oracle_lib, E0, variant_tab=N
     o = oracle_lib.Oracle(table_path)
     h = BOX["n"] * BOX["dv"] / 2.0
     rho = float(np.float16(1.0))
-    g = BOX_GEO
+    g = BOX_GEO if geo is None else geo
     s = np.array([g["sod"], 0.0, 0.0])
     c = np.array([g["sod"] - g["sdd"], 0.0, 0.0])
     eu, ev, nrm = np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0])

@@ -69,6 +69,73 @@ def test_otsu_bimodal_and_trimodal():
     assert 5 < a <= 30 < b <= 55
 
 
+def test_otsu_ties_and_within_class_minimum():
+    """Otsu's thresholds maximise the between-class variance, which is the same
+    as minimising the total within-class variance (their sum is the fixed total
+    variance): checked against that second formula by brute force; two or
+    three point masses give a flat optimum, resolved to the smallest
+    thresholds."""
+    h = np.zeros(64)
+    h[10], h[50] = 100, 100
+    assert recon.otsu(h, 2) == (11, 64)
+    h3 = np.zeros(64)
+    h3[5], h3[30], h3[55] = 100, 80, 60
+    assert recon.otsu(h3, 3) == (6, 31)
+    rng = np.random.default_rng(3)
+    c = np.arange(64) + 0.5
+    h = np.round(300 * np.exp(-0.5 * ((c - 12) / 4) ** 2) + 200 * np.exp(-0.5 * ((c - 33) / 5) ** 2)
+                 + 120 * np.exp(-0.5 * ((c - 52) / 3) ** 2) + rng.integers(0, 4, 64))
+
+    def within(cuts):
+        tot = 0.0
+        for lo, hi in zip((0,) + cuts, cuts + (64,)):
+            w = h[lo:hi]
+            if w.sum() > 0:
+                m = (w * c[lo:hi]).sum() / w.sum()
+                tot += (w * (c[lo:hi] - m) ** 2).sum()
+        return tot
+
+    best2 = min(range(1, 64), key=lambda a: (within((a,)), a))
+    assert recon.otsu(h, 2) == (best2, 64)
+    best3 = min(((a, b) for a in range(1, 64) for b in range(a + 1, 64)), key=lambda t: (within(t), t))
+    assert recon.otsu(h, 3) == best3
+
+
+def test_histogram_and_segmentation_map():
+    """256 bins over [lo, hi): a value at a bin's centre lands in that bin,
+    values outside the range in the end bins; a three-level volume splits into
+    its three classes, class 0 takes the background density and the others
+    rho = mu / (0.1 mu/rho) of their material."""
+    lo, hi = -0.01, 0.09
+    centres = lo + (np.arange(256) + 0.5) * (hi - lo) / 256
+    hist, b = recon.histogram(centres, lo, hi)
+    np.testing.assert_array_equal(b, np.arange(256))
+    assert np.all(hist == 1)
+    hist, b = recon.histogram(np.array([-5.0, lo, hi, 7.0]), lo, hi)
+    assert list(b) == [0, 0, 255, 255] and hist.sum() == 4
+    rng = np.random.default_rng(2)
+    lvl = rng.choice(3, size=(6, 7, 8))
+    mu = np.array([0.0002, 0.0206, 0.075])[lvl] + rng.normal(0, 0.001, lvl.shape)
+    murho = [1.0, 0.206, 0.278]  # class 0's entry is unused
+    mat, rho, hist, (t0, t1) = recon.segment(mu, lo, hi, 3, [0, 1, 3], murho, 0.001205)
+    np.testing.assert_array_equal(mat, np.array([0, 1, 3], np.uint8)[lvl])
+    assert hist.sum() == mu.size and 0 < t0 < t1 < 256
+    np.testing.assert_allclose(rho[lvl == 0], np.float32(0.001205), rtol=0)
+    for k, m in ((1, 0.206), (2, 0.278)):
+        np.testing.assert_allclose(rho[lvl == k], np.clip(mu[lvl == k] / (0.1 * m), 0, 30), rtol=1e-15)
+    # two classes: one cut between two of the levels, no level split, air in class 0
+    mat2, _, _, (a, bb) = recon.segment(mu, lo, hi, 2, [0, 1, 1], murho, 0.001205)
+    assert bb == 256 and np.all(mat2[lvl == 0] == 0) and np.all(mat2[lvl == 2] == 1)
+    assert len(np.unique(mat2[lvl == 1])) == 1
+
+
+def test_line_integrals():
+    rng = np.random.default_rng(1)
+    I0 = rng.uniform(0.5, 2.0, (4, 5))
+    a = rng.uniform(0.0, 6.0, (3, 4, 5))
+    np.testing.assert_allclose(recon.line_integrals(I0 * np.exp(-a), I0), a, atol=1e-12)
+
+
 def test_correction_formula():
     rng = np.random.default_rng(0)
     ip = rng.uniform(0.1, 1.0, 100)
@@ -77,6 +144,8 @@ def test_correction_formula():
     a = -np.log((ip + is_) / i0)
     np.testing.assert_allclose(recon.correct(a, ip, is_), -np.log(ip / i0), atol=1e-12)
     np.testing.assert_allclose(recon.correct(a, ip, np.zeros(100)), a, atol=0)
+    # Is simulated on pixels k times larger than the panel's: scaled by the area ratio
+    np.testing.assert_allclose(recon.correct(a, ip, 4.0 * is_, is_scale=0.25), -np.log(ip / i0), atol=1e-12)
 
 
 def test_bin_volume_pins():
