@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--primary-speckle", type=float, default=0.0, help="fraction of voxels given another material")
     p.add_argument("--mesh-segments", type=int, default=1024)
     p.add_argument("--nee-mode", type=int, default=0, help="0 sampled-type scoring (the paper's), 1 expected value")
+    p.add_argument("--n-split", type=int, default=10, help="pseudo-particles per scatter interaction")
     p.add_argument("--tally", choices=["auto", "global", "shared", "warp", "tiled"], default="auto",
                    help="how point-detector scores reach the image (tiled: tile-stratified, --tile pixels)")
     p.add_argument("--tile", type=int, nargs=2, default=[64, 64], metavar=("U", "V"))
@@ -292,7 +293,7 @@ def bench_config(args, wl, n_ang=1, detector=None):
             "volume": f"{nx}x{ny}x{nz} voxels at {vol['spacing'][0]} mm, uint8 material + fp16 density",
             "detector": f"{g['nu']}x{g['nv']} pixels at {g['pu']} mm",
             "photons_per_projection": int(wl["n_photons"]), "angles_per_step": n_ang, "step_mm": wl["step_mm"],
-            "n_split": 10, "spectrum": f"{len(wl['weights'])} bins", "response": detector or args.detector,
+            "n_split": args.n_split, "spectrum": f"{len(wl['weights'])} bins", "response": detector or args.detector,
             "nee_mode": args.nee_mode, "l2_flush": True,
             "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", 1)) > 1 else "single",
             "launch": "per-angle" if args.per_angle else "batched", "graph": bool(args.graph),
@@ -455,7 +456,7 @@ def run_ours(args):
     seed = wl["seed"] + 1000 * rank
     tally = {"auto": 0, "global": 1, "shared": 2, "warp": 3, "tiled": 4}[args.tally]
     ctx = mcx.Context(local, voxel_layout=args.voxel_layout, use_graph=int(args.graph), nee_mode=args.nee_mode,
-                      tally_mode=tally, tile_u=args.tile[0], tile_v=args.tile[1])
+                      tally_mode=tally, tile_u=args.tile[0], tile_v=args.tile[1], n_split=args.n_split)
     ctx.load_tables(tp)
     ctx.setup(wl)
     if args.detector == "panel":

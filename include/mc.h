@@ -353,9 +353,14 @@ int mc_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, int n, int h, 
  *    compared by figure of merit 1 / (noise^2 x time), the noise being the
  *    8-batch estimate of the scatter image's relative L2 error; the best
  *    (or none) is kept.
- * The chosen block_size, blocks_per_sm, tally_mode and rr_threshold are
- * written into the context's options; *out receives them with the step, the
- * measured histories/s and the figure-of-merit gain of the roulette.
+ * 4. Tally pixels (tile-stratified point-detector pixels change the noise as
+ *    well as the speed): MC_TALLY_TILED with tiles of 16 x 16 and 32 x 32
+ *    pixels is compared with the configuration of steps 2-3 by the same
+ *    figure of merit; a tile shape is kept only if it beats it.
+ * The chosen block_size, blocks_per_sm, tally_mode (and tile_u, tile_v) and
+ * rr_threshold are written into the context's options; *out receives them
+ * with the step, the measured histories/s and the figure-of-merit gains of the
+ * roulette and of the tiles.
  * Allocates temporary device buffers.  Errors as mc_project. */
 typedef struct mc_tuning {
   float step_mm;
@@ -366,6 +371,8 @@ typedef struct mc_tuning {
   double step_error;   /* relative L2 of the chosen step's primary vs step_min */
   float rr_threshold;  /* chosen Russian-roulette threshold (0: off) */
   double rr_fom_gain;  /* figure of merit with it / without roulette */
+  int tile_u, tile_v;  /* chosen tile of MC_TALLY_TILED (0, 0: not tiled) */
+  double tile_fom_gain; /* best figure of merit of the tiled trials / that of steps 2-3 */
 } mc_tuning;
 int mc_autotune(mc_ctx *ctx, const float *angles_rad, int n_angles, uint64_t probe_photons, float step_min,
                 float step_max, float step_tol, mc_tuning *out, void *stream);

@@ -1323,7 +1323,8 @@ int orc_scatter(const orc_ctx *c, double beta, uint32_t angle_index, uint64_t N,
         double DD[3] = {Pp[0] - x[0], Pp[1] - x[1], Pp[2] - x[2]};
         double dd = sqrt(DD[0] * DD[0] + DD[1] * DD[1] + DD[2] * DD[2]);
         double dir[3] = {DD[0] / dd, DD[1] / dd, DD[2] / dd};
-        double lam = w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2];
+        /* the scattering cosine of two unit vectors, kept within [-1, 1] against rounding */
+        double lam = fmin(fmax(w[0] * dir[0] + w[1] * dir[1] + w[2] * dir[2], -1.0), 1.0);
         double cosg = -(dir[0] * P.n[0] + dir[1] * P.n[1] + dir[2] * P.n[2]);
         const double geo = tile_w * A_px * cosg * ((double)Pt / n_pp) / (2.0 * PI * dd * dd);
         double sc;

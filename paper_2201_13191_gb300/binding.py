@@ -55,6 +55,9 @@ class Tuning(C.Structure):
         ("step_error", C.c_double),
         ("rr_threshold", C.c_float),
         ("rr_fom_gain", C.c_double),
+        ("tile_u", C.c_int),
+        ("tile_v", C.c_int),
+        ("tile_fom_gain", C.c_double),
     ]
 
 
@@ -364,8 +367,12 @@ class Context:
             with open(cache) as f:
                 saved = json.load(f).get(cache_key)
             if saved:
+                extra = {}
+                if saved.get("tile_u", 0) > 0:
+                    extra = dict(tally_mode=4, tile_u=saved["tile_u"], tile_v=saved["tile_v"])
                 self.set_options(block_size=saved["block_size"], blocks_per_sm=saved["blocks_per_sm"],
-                                 tally_mode=saved["tally_mode"], rr_threshold=saved.get("rr_threshold", 0.0))
+                                 tally_mode=saved["tally_mode"], rr_threshold=saved.get("rr_threshold", 0.0),
+                                 **extra)
                 return saved
         a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
         t = Tuning()
@@ -373,6 +380,8 @@ class Context:
                                        float(step_max), float(step_tol), C.byref(t), _stream_handle(stream)))
         self.opt.block_size, self.opt.blocks_per_sm, self.opt.tally_mode = t.block_size, t.blocks_per_sm, t.tally_mode
         self.opt.rr_threshold = t.rr_threshold
+        if t.tile_u > 0:
+            self.opt.tally_mode, self.opt.tile_u, self.opt.tile_v = 4, t.tile_u, t.tile_v
         res = {k: getattr(t, k) for k, _ in Tuning._fields_}
         if cache and cache_key:
             data = {}

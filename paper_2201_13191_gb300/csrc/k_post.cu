@@ -128,19 +128,20 @@ __global__ void k_lerp_upsample(const float* __restrict__ in, int nv, int nu, fl
 }
 
 // The same interpolation, separable and row-tiled: a block makes kUpRows
-// output rows of one output angle.  It first interpolates along x (and between
-// the two angles) every low-resolution row those output rows touch, into
-// shared memory (rows[j][X] for input row r0 + j, clamped), then each output
-// pixel takes its four y taps from there.  The sums run in the same order as
-// in k_lerp_upsample (x taps inside, y taps outside), so the images agree bit
-// for bit, with 4 instead of 16 taps per output pixel and the low-resolution
-// reads shared by the block.
+// output rows of one output angle.  It first interpolates between the two
+// angles every low-resolution row those output rows touch (lr[j][x] for input
+// row r0 + j, clamped: one read of each input value), then along x from there
+// into shared memory (xr[j][X]), then each output pixel takes its four y taps
+// from xr.  The sums run in the same order as in k_lerp_upsample (x taps
+// inside, y taps outside, the angle lerp of each tap first), so the images
+// agree bit for bit, with 4 instead of 16 taps per output pixel and the
+// low-resolution reads shared by the block.
 constexpr int kUpRows = 32;
 __global__ void __launch_bounds__(256) k_lerp_upsample_rows(const float* __restrict__ in, int nv, int nu,
                                                             float* __restrict__ out, int NV, int NU,
                                                             const int* __restrict__ a0s, const int* __restrict__ a1s,
                                                             const float* __restrict__ fas, float a) {
-  extern __shared__ __align__(16) float xr[];  // [rows][NU]
+  extern __shared__ __align__(16) float xr[];  // [rows][NU], then lr [rows][nu]
   const int o = blockIdx.y;
   const int Y0 = blockIdx.x * kUpRows, Y1 = min(Y0 + kUpRows, NV);
   const float sx = (float)nu / (float)NU, sy = (float)nv / (float)NV;
@@ -150,6 +151,14 @@ __global__ void __launch_bounds__(256) k_lerp_upsample_rows(const float* __restr
   const float* A = in + (size_t)__ldg(a0s + o) * nu * nv;
   const float* B = in + (size_t)__ldg(a1s + o) * nu * nv;
   const float f = __ldg(fas + o);
+  // angle pass: the lerped low-resolution rows, each input value read once
+  float* lr = xr + (size_t)nrows * NU;
+  for (int q = threadIdx.x; q < nrows * nu; q += blockDim.x) {
+    const int j = q / nu, x = q - j * nu;
+    const size_t i = (size_t)min(max(r0 + j, 0), nv - 1) * nu + x;
+    lr[q] = fmaf(f, __ldg(B + i) - __ldg(A + i), __ldg(A + i));
+  }
+  __syncthreads();
   // x pass: a column's taps and weights once, then every row
   for (int X = threadIdx.x; X < NU; X += blockDim.x) {
     const float xx = fmaf((float)X + 0.5f, sx, -0.5f);
@@ -160,13 +169,10 @@ __global__ void __launch_bounds__(256) k_lerp_upsample_rows(const float* __restr
 #pragma unroll
     for (int kx = 0; kx < 4; ++kx) xi[kx] = min(max((int)xf - 1 + kx, 0), nu - 1);
     for (int j = 0; j < nrows; ++j) {
-      const size_t ro = (size_t)min(max(r0 + j, 0), nv - 1) * nu;
+      const float* row = lr + j * nu;
       float racc = 0.f;
 #pragma unroll
-      for (int kx = 0; kx < 4; ++kx) {
-        const float v = fmaf(f, __ldg(B + ro + xi[kx]) - __ldg(A + ro + xi[kx]), __ldg(A + ro + xi[kx]));
-        racc = fmaf(wx[kx], v, racc);
-      }
+      for (int kx = 0; kx < 4; ++kx) racc = fmaf(wx[kx], row[xi[kx]], racc);
       xr[j * NU + X] = racc;
     }
   }
@@ -234,7 +240,7 @@ cudaError_t launch_lerp_upsample(const float* in, int nv, int nu, float* out, in
   // row-tiled form when the low-resolution rows one block touches fit in shared memory
   const double sy = (double)nv / (double)NV;
   const int rows = (int)std::ceil((kUpRows - 1) * sy) + 5;
-  const size_t smem = (size_t)rows * NU * 4;
+  const size_t smem = (size_t)rows * (NU + nu) * 4;
   if (n_out <= 65535 && smem <= 160 * 1024) {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k_lerp_upsample_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

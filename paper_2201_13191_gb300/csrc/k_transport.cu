@@ -9,8 +9,11 @@
 //
 // Wavefront structure: each thread carries one photon's walk and runs one free
 // flight per iteration; an interaction queues a record in shared memory, and
-// the block then shares out all queued pseudo-particles among its warps
-// (longest chords first) before the next flight.  History h of angle a draws
+// its pseudo-particles are then shared out (longest chords first) before the
+// next flight: among the warp's own lanes with the plain FP64 tally (no block
+// barrier in the loop, so warps run their phases independently), or among the
+// whole block with the combined tallies, whose shared images need block-wide
+// steps.  History h of angle a draws
 // its random numbers from Philox4x32-10 keyed by (seed, a, h), in a fixed
 // order, with each pseudo-particle on its own counter block, so any history
 // can be recomputed on its own.  The cross-section tables are staged once per
@@ -482,7 +485,9 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
   const float dd2 = dot3(DD, DD);
   const float idd = rsqrtf(dd2);
   const float3 dir = make_float3(DD.x * idd, DD.y * idd, DD.z * idd);
-  const float lam = dot3(w, dir);
+  // the scattering cosine, clamped: two rounded unit vectors can give a dot product a unit past +-1, outside
+  // the domain of the pdfs and of the Doppler kinematics
+  const float lam = fminf(fmaxf(dot3(w, dir), -1.f), 1.f);
   const float cosg = -dot3(dir, ps.n);
   const int tm = R.tm[r];
   const int type = tm >> 8, mint = tm & 255;
@@ -746,7 +751,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   for (;;) {
     if (tiled && s_tc.done) break;
     // ---- flight phase: one free flight per live photon
-    bool fresh = false;
+    bool fresh = false, has_rec = false;
     if (tiled) {
       if (!alive) {
         const unsigned long long j = atomicAdd(&s_tc.j, 1ull);
@@ -878,7 +883,14 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
         } else {
           // queue the interaction; its pseudo-particles use the next counter blocks, one each
           g.align();
-          const int r = atomicAdd(&s_nrec, 1);
+          // block-wide queue (combined tallies) or the lane's own slot (per-warp phases)
+          int r;
+          if constexpr (COMBINE) {
+            r = atomicAdd(&s_nrec, 1);
+          } else {
+            r = threadIdx.x;
+            has_rec = true;
+          }
           R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
           R.wx[r] = w.x; R.wy[r] = w.y; R.wz[r] = w.z;
           R.E[r] = E; R.W[r] = W; R.cb[r] = cb; R.sb[r] = sb;
@@ -935,6 +947,38 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
           }
         }
       }
+    }
+    if constexpr (!COMBINE) {
+      // ---- pseudo-particle phase, per warp (no block barrier): the warp marches
+      // its own lanes' queued rays, records ranked by chord length, longest first
+      const unsigned recmask = __ballot_sync(0xffffffffu, has_rec);
+      const int lane = threadIdx.x & 31, wbase = threadIdx.x - lane;
+      const float my_len = has_rec ? R.len[threadIdx.x] : 0.f;
+      int rank = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float lj = __shfl_sync(0xffffffffu, my_len, j);
+        rank += (((recmask >> j) & 1u) != 0u) && (lj > my_len || (lj == my_len && j < lane));
+      }
+      if (has_rec) s_ord[wbase + rank] = threadIdx.x;
+      __syncwarp();
+      const int n_split = pseudo_count();
+      const int n_jobs = __popc(recmask) * n_split;
+      // weight of a pseudo-particle: pixel area x P / n_split / (2 pi) (eq. Th)
+      const float nee_scale = G.pu * G.pv * ((float)npix / (float)n_split) / (2.f * kPi);
+      const TileSel ts = {0, 0, 0, 0, 1.f};
+      for (int base = 0; base < n_jobs; base += 32) {
+        const int j = base + lane;
+        if (j < n_jobs) {
+          const int q = j / n_split;
+          pseudo_particle<LAYOUT, COMBINE, EV, DOP>(P, T, R, s_ord[wbase + q], j - q * n_split, my_mu, B, nee_scale,
+                                                    npix, img, C, s_img, key, ts);
+        }
+      }
+      // every lane has read the warp's records before they are overwritten
+      __syncwarp();
+      if (!__any_sync(0xffffffffu, alive || next < total)) break;
+      continue;
     }
     __syncthreads();
     // ---- pseudo-particle phase: the block marches every queued ray together

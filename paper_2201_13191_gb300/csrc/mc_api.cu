@@ -1106,13 +1106,14 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   //    batch estimate of the scatter image's relative L2 error; thresholds are multiples of the mean
   //    attenuated pseudo-particle score of a run without roulette
   float best_rr = 0.f;
-  double fom0 = 0, best_fom = 0;
+  double fom0 = 0, best_fom = 0, rr_top = 0, tile_gain = 1.0;
+  int best_tu = 0, best_tv = 0;
   {
     float* d_var = nullptr;
     e = cudaMalloc((void**)&d_var, n * 4);
     if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "autotune allocation"));
     std::vector<float> var(n);
-    const mc_options shape = ctx->opt;
+    mc_options shape = ctx->opt;  // the configuration whose figure of merit fom_of measures
     auto fom_of = [&](float rr, double* mean_score) -> int {
       ctx->opt = shape;
       ctx->opt.rr_threshold = rr;
@@ -1158,6 +1159,35 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
       }
     }
     best_fom = top;
+    rr_top = top;
+    // 4. tally pixels (reading 28): the tile-stratified point-detector pixels change the noise as well as the
+    //    speed, so tile shapes are compared with the tuned configuration by the same figure of merit; a tile
+    //    shape is kept only if it beats it (n_batches x tile pixels must fit the shared tile image)
+    const double untiled = top;
+    const int shapes[2][2] = {{16, 16}, {32, 32}};
+    for (int c = 0; c < 2; ++c) {
+      const int tu = std::min(shapes[c][0], ctx->nu), tv = std::min(shapes[c][1], ctx->nv);
+      if ((size_t)8 * tu * tv > (size_t)kSharedTallyMaxPixels) continue;
+      mc_options trial = shape;
+      trial.tally_mode = MC_TALLY_TILED;
+      trial.tile_u = tu;
+      trial.tile_v = tv;
+      const mc_options keep = shape;
+      shape = trial;
+      rc = fom_of(best_rr, nullptr);
+      shape = keep;
+      if (rc) {
+        cudaFree(d_var);
+        ctx->opt = saved;
+        return finish(rc);
+      }
+      if (best_fom > top) {
+        top = best_fom;
+        best_tu = tu;
+        best_tv = tv;
+      }
+    }
+    tile_gain = untiled > 0 ? top / untiled : 1.0;
     cudaFree(d_var);
   }
   ctx->opt = saved;
@@ -1165,8 +1195,16 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   ctx->opt.blocks_per_sm = best.blocks_per_sm;
   ctx->opt.tally_mode = best.tally_mode;
   ctx->opt.rr_threshold = best_rr;
+  if (best_tu > 0) {
+    ctx->opt.tally_mode = MC_TALLY_TILED;
+    ctx->opt.tile_u = best_tu;
+    ctx->opt.tile_v = best_tv;
+  }
   out->rr_threshold = best_rr;
-  out->rr_fom_gain = fom0 > 0 ? best_fom / fom0 : 1.0;
+  out->rr_fom_gain = fom0 > 0 ? rr_top / fom0 : 1.0;
+  out->tile_u = best_tu;
+  out->tile_v = best_tv;
+  out->tile_fom_gain = tile_gain;
   out->step_mm = best_step;
   out->block_size = best.block_size;
   out->blocks_per_sm = best.blocks_per_sm;

@@ -40,8 +40,11 @@ def test_forced_detection_same_seed(gpu, oracle_lib, table_path, tables, nee_mod
         o.set_tiles(*tiles)
     r = o.scatter(0.4, N, wl["step_mm"], 9)
     _same_seed_check(g, r["Is"], var)
-    for k in ("compton", "rayleigh", "photo", "nee_rays"):
-        assert abs(st[k] / r["stats"][k] - 1.0) < 3e-4, k
+    # a handful of the 2e4 histories take another branch after an FP32 rounding (measured: 1 to 5), each
+    # changing an interaction count by about one and the pseudo-particle count by about one interaction's
+    n_pp = st["nee_rays"] / max(1.0, st["compton"] + st["rayleigh"] + (st["photo"] if nee_mode else 0))
+    for k, unit in (("compton", 1), ("rayleigh", 1), ("photo", 1), ("nee_rays", n_pp)):
+        assert abs(st[k] - r["stats"][k]) <= max(3e-4 * r["stats"][k], 8 * unit), k
     assert st["nee_rays"] > 100 * (st["compton"] + st["rayleigh"])  # every pixel (of the tile) per interaction
 
 
