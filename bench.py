@@ -63,7 +63,10 @@ def parse():
     p.add_argument("--conv-bench", action="store_true",
                    help="tensor-core throughput of the denoiser's convolutions and its inference latency")
     p.add_argument("--correct-eval", action="store_true", help="iterative scatter correction on a large flat panel")
-    p.add_argument("--vr-eval", action="store_true", help="expected-value vs sampled-type point-detector scoring")
+    p.add_argument("--vr-eval", action="store_true",
+                   help="point-detector scoring variants (expected value, forced detection) by figure of merit")
+    p.add_argument("--vr-panel", type=int, default=32, help="coarse panel pixels a side for forced detection")
+    p.add_argument("--vr-photons", type=float, default=2e6, help="photons per projection on the coarse panel")
     p.add_argument("--mesh-bench", action="store_true", help="primary images of the triangle-mesh phantom")
     p.add_argument("--tally-eval", action="store_true", help="figure of merit of the tally modes")
     p.add_argument("--primary-bench", action="store_true", help="primary images of the correction workload")
@@ -124,6 +127,12 @@ class Clocks:
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.first = 0
+
+    def mark(self):
+        """Summarise only the samples taken from now on (the sampler is started
+        ahead of the timed region, so that its start-up stays outside it)."""
+        self.first = len(self.lines)
 
     def start(self):
         try:
@@ -150,7 +159,7 @@ class Clocks:
         self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for l in self.lines[self.first:]:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 8:
                 continue
@@ -349,6 +358,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+TRANSPORT_SOURCES = ("paper_2201_13191_gb300/csrc/k_transport.cu", "paper_2201_13191_gb300/csrc/mc_device.cuh")
+
+
+def transport_source_hash():
+    """First 16 hex digits of the SHA-256 of the transport kernel's sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRANSPORT_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """Per-march-step DRAM and L2 bytes of k_transport from the ncu summary in
+    profiles/ (a line 'traffic-per-step: kernel=<hash> workload=<name>
+    dram_bytes=<x> l2_bytes=<y>'), or None when the summary was taken on other
+    sources than the current kernel's."""
+    path = os.path.join(ROOT, "profiles", f"k_transport_{workload}.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    want = transport_source_hash()
+    for line in lines:
+        if line.startswith("traffic-per-step:"):
+            kv = dict(x.split("=", 1) for x in line.split()[1:])
+            if kv.get("kernel") == want and kv.get("workload") == workload:
+                return float(kv["dram_bytes"]), float(kv["l2_bytes"])
+    return None
+
+
 def probe_library():
     """libmcprobe.so (include/mc_probe.h): the measurement kernels, built beside the product library."""
     import ctypes as C
@@ -494,6 +536,8 @@ def run_ours(args):
             steps += st["flight_steps"] + st["nee_steps"]
         return ms, steps, 3 * n_ang
 
+    clocks = Clocks(device_id(torch, local))
+    clocks.start()
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -502,8 +546,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    clocks = Clocks(device_id(torch, local))
-    clocks.start()
+    clocks.mark()
     t_kernel, steps_per, launches = [], [], 0
     barrier()
     torch.cuda.synchronize()
@@ -560,8 +603,14 @@ def run_ours(args):
     peak_tflops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
     mean_ms = float(np.mean(t_kernel))
     achieved = FLOPS_PER_STEP * float(np.mean(steps_per)) / (mean_ms / 1e3) / 1e12
+    rec = recorded_traffic(args.workload)
+    traffic = None if rec is None else rec[0] * float(np.mean(steps_per))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops, "traffic": traffic,
+            "traffic_basis": None if rec is None else
+            f"ncu dram__bytes_read.sum + dram__bytes_write.sum of a 2e6-photon launch of the same kernel, "
+            f"{rec[0]:.4f} B per march step, scaled by the march steps of this launch; L2 bytes per step "
+            f"{rec[1]:.2f} (profiles/k_transport_{args.workload}.md)",
             "kernel": "k_transport", "steps_per_launch": float(np.mean(steps_per)),
             "kernel_ms": mean_ms, "steps_per_s": float(np.mean(steps_per)) / (mean_ms / 1e3),
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
@@ -569,6 +618,10 @@ def run_ours(args):
     roof["memory"] = memory_roofline(torch, props, vol["mat"].shape,
                                      packed_words(vol["mat"].shape, args.voxel_layout, props), roof["steps_per_s"],
                                      stream)
+    if rec is not None:
+        # bytes the kernel moves from L2 per march step (ncu), against the algorithmic 3
+        roof["memory"]["l2_bytes_per_step"] = rec[1]
+        roof["memory"]["l2_traffic_over_algorithmic"] = rec[1] / 3.0
 
     # the second half of the metric: seconds per projection at <= 2% scatter
     # error for plain MC, Savitzky-Golay smoothing and the learned denoiser
@@ -1089,20 +1142,22 @@ def run_correct_eval(args):
 
 
 def run_vr_eval(args):
-    """Variance reduction of the expected-value point-detector scoring against
-    the paper's sampled-type scoring on the bench workload: transport time,
-    relative L2 noise of the scatter image (batch estimate) and the figure of
-    merit 1 / (noise^2 x time) of each mode."""
+    """Variance reduction of the point-detector scoring on the bench workload:
+    transport time, relative L2 noise of the scatter image (batch estimate) and
+    the figure of merit 1 / (noise^2 x time) of the paper's sampled-type scoring
+    and of expected-value scoring; then, on a coarse panel of the same extent
+    (--vr-panel pixels a side, the size of the correction's simulation grids),
+    the same two and forced detection (every pixel scored once per interaction)
+    alone and with expected-value scoring."""
     import torch
 
     import paper_2201_13191_gb300 as mcx
 
     mcx.build()
     tp, wl = make_inputs(tempfile.mkdtemp(prefix="mcvr"), args.photons or 1e7, args.workload)
-    N = wl["n_photons"]
-    res = {}
-    for mode in (0, 1):
-        ctx = mcx.Context(0, n_batches=20, nee_mode=mode)
+
+    def measure(wl, N, **opt):
+        ctx = mcx.Context(0, n_batches=20, **opt)
         ctx.load_tables(tp)
         ctx.setup(wl)
         ms, noise = [], []
@@ -1116,14 +1171,30 @@ def run_vr_eval(args):
                 noise.append(float(torch.sqrt(var.sum()) / torch.linalg.norm(img)))
         t = float(np.mean(ms)) / 1e3
         n2 = float(np.mean(np.square(noise)))
-        res[mode] = {"transport_s": t, "histories_per_s": N / t, "rel_l2_noise": float(np.sqrt(n2)),
-                     "figure_of_merit": 1.0 / (n2 * t)}
+        ctx.close()
+        return {"transport_s": t, "histories_per_s": N / t, "rel_l2_noise": float(np.sqrt(n2)),
+                "figure_of_merit": 1.0 / (n2 * t)}
+
+    N = wl["n_photons"]
+    res = {mode: measure(wl, N, nee_mode=mode) for mode in (0, 1)}
+    g = wl["geometry"]
+    P = args.vr_panel
+    coarse = dict(wl, geometry=dict(g, nu=P, nv=P, pu=g["pu"] * g["nu"] / P, pv=g["pv"] * g["nv"] / P))
+    Nc = int(args.vr_photons)
+    modes = {"paper": dict(nee_mode=0), "expected_value": dict(nee_mode=1),
+             "forced_detection": dict(forced_detection=1), "forced_detection_expected_value":
+             dict(forced_detection=1, nee_mode=1)}
+    cres = {name: measure(coarse, Nc, **opt) for name, opt in modes.items()}
+    for name in cres:
+        cres[name]["fom_gain"] = cres[name]["figure_of_merit"] / cres["paper"]["figure_of_merit"]
     line = {
         "metric": "figure of merit 1/(relative L2 noise^2 x transport time) of the scatter image",
         "unit": "1/s", "higher_is_better": True,
-        "config": {"workload": args.workload, "photons": N, "batches": 20, "steps": args.steps},
+        "config": {"workload": args.workload, "photons": N, "batches": 20, "steps": args.steps,
+                   "coarse_panel": f"{P}x{P} over the same extent", "coarse_photons": Nc},
         "paper_scoring": res[0], "expected_value_scoring": res[1],
         "fom_gain": res[1]["figure_of_merit"] / res[0]["figure_of_merit"],
+        "coarse_panel": cres,
     }
     print(json.dumps(line), flush=True)
 

@@ -367,12 +367,11 @@ class Context:
             with open(cache) as f:
                 saved = json.load(f).get(cache_key)
             if saved:
-                extra = {}
+                opt = dict(block_size=saved["block_size"], blocks_per_sm=saved["blocks_per_sm"],
+                           tally_mode=saved["tally_mode"], rr_threshold=saved.get("rr_threshold", 0.0))
                 if saved.get("tile_u", 0) > 0:
-                    extra = dict(tally_mode=4, tile_u=saved["tile_u"], tile_v=saved["tile_v"])
-                self.set_options(block_size=saved["block_size"], blocks_per_sm=saved["blocks_per_sm"],
-                                 tally_mode=saved["tally_mode"], rr_threshold=saved.get("rr_threshold", 0.0),
-                                 **extra)
+                    opt.update(tally_mode=4, tile_u=saved["tile_u"], tile_v=saved["tile_v"])
+                self.set_options(**opt)
                 return saved
         a = np.ascontiguousarray(np.atleast_1d(angles), dtype=np.float32)
         t = Tuning()

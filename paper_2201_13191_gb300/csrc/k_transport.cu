@@ -583,7 +583,18 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 }
 
 #ifndef MC_MIN_BLOCKS
-#define MC_MIN_BLOCKS 3
+#define MC_MIN_BLOCKS 2
+#endif
+// Flights through a linear-layout volume sum each group's optical depth
+// branch-free before looking for the interaction step (1), or test every step
+// (0); both give the same interaction points.
+#ifndef MC_FLIGHT_GROUP
+#define MC_FLIGHT_GROUP 1
+#endif
+// Flights per lane and iteration with the per-warp phases (the block-wide
+// phases of the combined tallies take one).
+#ifndef MC_FLIGHTS_PER_ITER
+#define MC_FLIGHTS_PER_ITER 1
 #endif
 // Pseudo-particle jobs are handed out longest records first: records are
 // bucketed by the chord from the interaction point to the volume boundary
@@ -647,6 +658,7 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
   __shared__ int s_bucket[kBuckets + 1];
   __shared__ TileChunk s_tc;
   const bool tiled = COMBINE && P.tally_mode == TALLY_TILED;
+  constexpr int kFlights = COMBINE ? 1 : MC_FLIGHTS_PER_ITER;
   const int nm = P.tab.n_mat, ns = P.tab.n_stage;
   const int nb = P.spec.n_bins;
   const int B = blockDim.x;
@@ -750,203 +762,224 @@ __global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const Transpor
 
   for (;;) {
     if (tiled && s_tc.done) break;
-    // ---- flight phase: one free flight per live photon
-    bool fresh = false, has_rec = false;
-    if (tiled) {
-      if (!alive) {
-        const unsigned long long j = atomicAdd(&s_tc.j, 1ull);
-        if (j < s_tc.j_end) {
-          a = s_tc.a;
-          h = s_tc.first + (unsigned long long)P.n_tiles * j;
-          fresh = true;
+    // ---- flight phase: one free flight per live photon; with the per-warp
+    // phases a lane whose photon leaves without a record (escape, absorption)
+    // starts the next history in the same iteration, up to kFlights flights
+    bool has_rec = false;
+    for (int fl = 0; fl < kFlights; ++fl) {
+      bool fresh = false;
+      if (tiled) {
+        if (!alive) {
+          const unsigned long long j = atomicAdd(&s_tc.j, 1ull);
+          if (j < s_tc.j_end) {
+            a = s_tc.a;
+            h = s_tc.first + (unsigned long long)P.n_tiles * j;
+            fresh = true;
+          }
         }
+      } else if (!alive && next < total) {
+        a = (int)(next / P.h_count);
+        h = P.h_begin + (next - (unsigned long long)a * P.h_count);
+        next += stride;
+        fresh = true;
       }
-    } else if (!alive && next < total) {
-      a = (int)(next / P.h_count);
-      h = P.h_begin + (next - (unsigned long long)a * P.h_count);
-      next += stride;
-      fresh = true;
-    }
-    if (fresh) {
-      int lo = 0, hi = nb - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pre[mid] <= h) lo = mid;
-        else hi = mid - 1;
+      if (fresh) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_pre[mid] <= h) lo = mid;
+          else hi = mid - 1;
+        }
+        E = s_E[lo];
+        g.init(h, (uint32_t)a, seed);
+        sincosf(__ldg(P.angles + a), &sb, &cb);
+        const float ua = g.u(), ub = g.u();
+        // toward a uniform point Q of the panel: D = Q - s = -SDD n + u e_u + v e_z
+        // (n = (cos b, sin b, 0), e_u = (-sin b, cos b, 0)), d^2 = SDD^2 + u^2 + v^2
+        const float u = (ua * (float)G.nu - 0.5f * (float)G.nu) * G.pu;
+        const float v = (ub * (float)G.nv - 0.5f * (float)G.nv) * G.pv;
+        const float r2 = fmaf(u, u, v * v);
+        const float d2 = fmaf(G.sdd, G.sdd, r2);
+        const float d = sqrtf(d2);
+        w = make_float3(fmaf(-G.sdd, cb, -u * sb) / d, fmaf(-G.sdd, sb, u * cb) / d, v / d);
+        W = s_wb[lo] * A_det * (G.sdd / d) / (4.f * kPi * d2);
+        if constexpr (LAYOUT == GEO_MESH) {
+          // the bodies' crossings are collected along the half-line from the source
+          x = make_float3(G.sod * cb, G.sod * sb, 0.f);
+          t_start = 0.f;
+        } else {
+          // the first flight runs from the ray's point nearest the isocentre,
+          // o = (SOD / d^2) ((u^2 + v^2) n + SDD (u e_u + v e_z)), with the source at
+          // t = -SOD SDD / d: its midpoints carry rounding of the volume's size, not
+          // of the source distance
+          const float k = G.sod / d2;
+          x = make_float3(k * fmaf(r2, cb, -G.sdd * (u * sb)), k * fmaf(r2, sb, G.sdd * (u * cb)), k * (G.sdd * v));
+          t_start = -G.sod * G.sdd / d;
+        }
+        order = 0;
+        alive = true;
+        ++C.hist;
       }
-      E = s_E[lo];
-      g.init(h, (uint32_t)a, seed);
-      sincosf(__ldg(P.angles + a), &sb, &cb);
-      const float ua = g.u(), ub = g.u();
-      // toward a uniform point Q of the panel: D = Q - s = -SDD n + u e_u + v e_z
-      // (n = (cos b, sin b, 0), e_u = (-sin b, cos b, 0)), d^2 = SDD^2 + u^2 + v^2
-      const float u = (ua * (float)G.nu - 0.5f * (float)G.nu) * G.pu;
-      const float v = (ub * (float)G.nv - 0.5f * (float)G.nv) * G.pv;
-      const float r2 = fmaf(u, u, v * v);
-      const float d2 = fmaf(G.sdd, G.sdd, r2);
-      const float d = sqrtf(d2);
-      w = make_float3(fmaf(-G.sdd, cb, -u * sb) / d, fmaf(-G.sdd, sb, u * cb) / d, v / d);
-      W = s_wb[lo] * A_det * (G.sdd / d) / (4.f * kPi * d2);
-      if constexpr (LAYOUT == GEO_MESH) {
-        // the bodies' crossings are collected along the half-line from the source
-        x = make_float3(G.sod * cb, G.sod * sb, 0.f);
-        t_start = 0.f;
-      } else {
-        // the first flight runs from the ray's point nearest the isocentre,
-        // o = (SOD / d^2) ((u^2 + v^2) n + SDD (u e_u + v e_z)), with the source at
-        // t = -SOD SDD / d: its midpoints carry rounding of the volume's size, not
-        // of the source distance
-        const float k = G.sod / d2;
-        x = make_float3(k * fmaf(r2, cb, -G.sdd * (u * sb)), k * fmaf(r2, sb, G.sdd * (u * cb)), k * (G.sdd * v));
-        t_start = -G.sod * G.sdd / d;
-      }
-      order = 0;
-      alive = true;
-      ++C.hist;
-    }
-    if (alive) {
-      const float tau_star = -logf(g.u());
-      float ta, tb;
-      bool hit = false;
-      float tint = 0.f;
-      int mint = 0;
-      if constexpr (LAYOUT == GEO_MESH) {
-        fill_mu(T, E, my_mu, B);
-        hit = mesh::mesh_flight(P.mesh, x, w, tau_star, my_mu, B, tint, mint, C.flight_steps);
-        (void)ta;
-        (void)tb;
-      } else if (clip_box(V, x, w, t_start, __int_as_float(0x7f800000), ta, tb)) {
-        fill_mu(T, E, my_mu, B);
-        const float L = tb - ta;
-        const int n = step_count(L, P.step);
-        const float hh = L / (float)n;
-        VoxRay vr;
-        vr.set(V, x, w);
-        const float3 hv = make_float3(hh * vr.vw.x, hh * vr.vw.y, hh * vr.vw.z);
-        float tau = 0.f, mu_m = 0.f;
-        int cur = -1, k = n;
-        // the step whose optical depth reaches tau* holds the interaction,
-        // placed inside it by a linear solve
-        auto consume = [&](const uint32_t(&wd)[kLook], int k0, bool tail) {
-#pragma unroll
-          for (int u = 0; u < kLook; ++u) {
-            if (!hit && (!tail || k0 + u < n)) {
-              const int m = vox_mat(wd[u]);
-              if (m != cur) {
-                cur = m;
-                mu_m = my_mu[m * B];
-              }
-              const float mu = mu_m * vox_rho(wd[u]);
-              if (fmaf(mu, hh, tau) >= tau_star) {
-                tint = fmaf((float)(k0 + u), hh, ta) + (tau_star - tau) / mu;
-                mint = cur;
-                hit = true;
-                k = k0 + u;
-              } else {
-                tau = fmaf(mu, hh, tau);
+      if (alive) {
+        const float tau_star = -logf(g.u());
+        float ta, tb;
+        bool hit = false;
+        float tint = 0.f;
+        int mint = 0;
+        if constexpr (LAYOUT == GEO_MESH) {
+          fill_mu(T, E, my_mu, B);
+          hit = mesh::mesh_flight(P.mesh, x, w, tau_star, my_mu, B, tint, mint, C.flight_steps);
+          (void)ta;
+          (void)tb;
+        } else if (clip_box(V, x, w, t_start, __int_as_float(0x7f800000), ta, tb)) {
+          fill_mu(T, E, my_mu, B);
+          const float L = tb - ta;
+          const int n = step_count(L, P.step);
+          const float hh = L / (float)n;
+          VoxRay vr;
+          vr.set(V, x, w);
+          const float3 hv = make_float3(hh * vr.vw.x, hh * vr.vw.y, hh * vr.vw.z);
+          float tau = 0.f, mu_m = 0.f;
+          int cur = -1, k = n;
+          // the step whose optical depth reaches tau* holds the interaction,
+          // placed inside it by a linear solve
+          auto consume = [&](const uint32_t(&wd)[kLook], int k0, bool tail) {
+  #pragma unroll
+            for (int u = 0; u < kLook; ++u) {
+              if (!hit && (!tail || k0 + u < n)) {
+                const int m = vox_mat(wd[u]);
+                if (m != cur) {
+                  cur = m;
+                  mu_m = my_mu[m * B];
+                }
+                const float mu = mu_m * vox_rho(wd[u]);
+                if (fmaf(mu, hh, tau) >= tau_star) {
+                  tint = fmaf((float)(k0 + u), hh, ta) + (tau_star - tau) / mu;
+                  mint = cur;
+                  hit = true;
+                  k = k0 + u;
+                } else {
+                  tau = fmaf(mu, hh, tau);
+                }
               }
             }
+          };
+          // volume in L2 (linear layout): a group's optical depth is summed
+          // branch-free, with the same per-step products and sums as above; the
+          // depth never decreases, so only the group whose end reaches tau* is
+          // walked again step by step (consume) to place the interaction
+          auto group_reaches = [&](const uint32_t(&wd)[kLook], int k0, bool tail) -> bool {
+            float t = tau;
+  #pragma unroll
+            for (int u = 0; u < kLook; ++u) {
+              const float tn = fmaf(my_mu[vox_mat(wd[u]) * B] * vox_rho(wd[u]), hh, t);
+              t = (!tail || k0 + u < n) ? tn : t;
+            }
+            if (t >= tau_star) return true;
+            tau = t;
+            return false;
+          };
+          int k0 = 0;
+          for (; k0 + kLook <= n && !hit; k0 += kLook) {
+            uint32_t wd[kLook];
+            gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
+            if (LAYOUT != VOX_LIN || !MC_FLIGHT_GROUP || group_reaches(wd, k0, false)) consume(wd, k0, false);
           }
-        };
-        int k0 = 0;
-        for (; k0 + kLook <= n && !hit; k0 += kLook) {
-          uint32_t wd[kLook];
-          gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
-          consume(wd, k0, false);
+          if (k0 < n && !hit) {
+            uint32_t wd[kLook];
+            gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
+            if (LAYOUT != VOX_LIN || !MC_FLIGHT_GROUP || group_reaches(wd, k0, true)) consume(wd, k0, true);
+          }
+          C.flight_steps += (unsigned long long)(hit ? k + 1 : n);
         }
-        if (k0 < n && !hit) {
-          uint32_t wd[kLook];
-          gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
-          consume(wd, k0, true);
-        }
-        C.flight_steps += (unsigned long long)(hit ? k + 1 : n);
-      }
-      if (!hit) {
-        ++C.escape;
-        alive = false;
-      } else {
-        x = make_float3(fmaf(tint, w.x, x.x), fmaf(tint, w.y, x.y), fmaf(tint, w.z, x.z));
-        t_start = 0.f;
-        int ti;
-        float tf;
-        T.locate(E, ti, tf);
-        const float pe = T.at(TAB_PE, mint, ti, tf), in = T.at(TAB_IN, mint, ti, tf),
-                    co = T.at(TAB_CO, mint, ti, tf);
-        const float ut = g.u() * (pe + in + co);
-        const int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
-        if (type == 0) ++C.photo;
-        else if (type == 1) ++C.compton;
-        else ++C.rayleigh;
-        // absorption sites score only in expected-value mode
-        if (type == 0 && !EV) {
+        if (!hit) {
+          ++C.escape;
           alive = false;
         } else {
-          // queue the interaction; its pseudo-particles use the next counter blocks, one each
-          g.align();
-          // block-wide queue (combined tallies) or the lane's own slot (per-warp phases)
-          int r;
-          if constexpr (COMBINE) {
-            r = atomicAdd(&s_nrec, 1);
+          x = make_float3(fmaf(tint, w.x, x.x), fmaf(tint, w.y, x.y), fmaf(tint, w.z, x.z));
+          t_start = 0.f;
+          int ti;
+          float tf;
+          T.locate(E, ti, tf);
+          const float pe = T.at(TAB_PE, mint, ti, tf), in = T.at(TAB_IN, mint, ti, tf),
+                      co = T.at(TAB_CO, mint, ti, tf);
+          const float ut = g.u() * (pe + in + co);
+          const int type = ut < pe ? 0 : (ut < pe + in ? 1 : 2);
+          if (type == 0) ++C.photo;
+          else if (type == 1) ++C.compton;
+          else ++C.rayleigh;
+          // absorption sites score only in expected-value mode
+          if (type == 0 && !EV) {
+            alive = false;
           } else {
-            r = threadIdx.x;
-            has_rec = true;
-          }
-          R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
-          R.wx[r] = w.x; R.wy[r] = w.y; R.wz[r] = w.z;
-          R.E[r] = E; R.W[r] = W; R.cb[r] = cb; R.sb[r] = sb;
-          R.norm[r] = type == 1 ? 1.f / (T.bound ? T.at(TAB_IINC, mint, ti, tf) : T.kn_norm(ti, tf))
-                                : 1.f / T.at(TAB_ICOH, mint, ti, tf);
-          R.tm[r] = (type << 8) | mint;
-          R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
-          R.k0[r] = g.ctr.x;
-          g.ctr.x += (uint32_t)pseudo_count();
-          {
-            // length key: chord toward the panel centre
-            const float rr0 = G.sod - G.sdd;
-            const float3 toc = make_float3(rr0 * cb - x.x, rr0 * sb - x.y, -x.z);
-            const float il = rsqrtf(dot3(toc, toc));
-            float ca, cbb;
-            R.len[r] = clip_box(V, x, make_float3(toc.x * il, toc.y * il, toc.z * il), 0.f,
-                                __int_as_float(0x7f800000), ca, cbb) ? cbb : 0.f;
-          }
-          // new direction (an absorption ends the photon)
-          if (type == 0) alive = false;
-        }
-        if (alive) {
-          bool fail = false;
-          float ct, Enew = E;
-          if (type == 1) {
-            const float alpha = E / T.mec2;
-            float rk = kahn(g, alpha, fail);
-            ct = 1.f - (rk - 1.f) / alpha;
-            if (T.bound) {
-              // scattering function: accept Kahn's angle with probability S_mol(x) / S_mol(inf)
-              const float K = (E * T.inv_hc) * (E * T.inv_hc);
-              const float smax = T.smol_max(mint);
-              for (int it = 0; it < 100000 && !fail; ++it) {
-                if (g.u() * smax <= T.smol(mint, 0.5f * K * (1.f - ct))) break;
-                rk = kahn(g, alpha, fail);
-                ct = 1.f - (rk - 1.f) / alpha;
-                if (it == 99999) fail = true;
-              }
+            // queue the interaction; its pseudo-particles use the next counter blocks, one each
+            g.align();
+            // block-wide queue (combined tallies) or the lane's own slot (per-warp phases)
+            int r;
+            if constexpr (COMBINE) {
+              r = atomicAdd(&s_nrec, 1);
+            } else {
+              r = threadIdx.x;
+              has_rec = true;
             }
-            Enew = DOP ? E * sample_doppler(g, T, mint, E, ct, fail) : E / rk;
-          } else {
-            ct = rayleigh(g, T, mint, E, fail);
+            R.X[r] = x.x; R.Y[r] = x.y; R.Z[r] = x.z;
+            R.wx[r] = w.x; R.wy[r] = w.y; R.wz[r] = w.z;
+            R.E[r] = E; R.W[r] = W; R.cb[r] = cb; R.sb[r] = sb;
+            R.norm[r] = type == 1 ? 1.f / (T.bound ? T.at(TAB_IINC, mint, ti, tf) : T.kn_norm(ti, tf))
+                                  : 1.f / T.at(TAB_ICOH, mint, ti, tf);
+            R.tm[r] = (type << 8) | mint;
+            R.hlo[r] = (uint32_t)h; R.hhi[r] = (uint32_t)(h >> 32); R.ang[r] = (uint32_t)a;
+            R.k0[r] = g.ctr.x;
+            g.ctr.x += (uint32_t)pseudo_count();
+            {
+              // length key: chord toward the panel centre
+              const float rr0 = G.sod - G.sdd;
+              const float3 toc = make_float3(rr0 * cb - x.x, rr0 * sb - x.y, -x.z);
+              const float il = rsqrtf(dot3(toc, toc));
+              float ca, cbb;
+              R.len[r] = clip_box(V, x, make_float3(toc.x * il, toc.y * il, toc.z * il), 0.f,
+                                  __int_as_float(0x7f800000), ca, cbb) ? cbb : 0.f;
+            }
+            // new direction (an absorption ends the photon)
+            if (type == 0) alive = false;
           }
-          const float phi = 2.f * kPi * g.u();
-          if (fail) ++C.fail;
-          w = rotate(w, ct, phi);
-          E = Enew;
-          ++order;
-          if (E < 1.f) {
-            alive = false;
-          } else if (order >= P.max_order) {
-            ++C.limit;
-            alive = false;
+          if (alive) {
+            bool fail = false;
+            float ct, Enew = E;
+            if (type == 1) {
+              const float alpha = E / T.mec2;
+              float rk = kahn(g, alpha, fail);
+              ct = 1.f - (rk - 1.f) / alpha;
+              if (T.bound) {
+                // scattering function: accept Kahn's angle with probability S_mol(x) / S_mol(inf)
+                const float K = (E * T.inv_hc) * (E * T.inv_hc);
+                const float smax = T.smol_max(mint);
+                for (int it = 0; it < 100000 && !fail; ++it) {
+                  if (g.u() * smax <= T.smol(mint, 0.5f * K * (1.f - ct))) break;
+                  rk = kahn(g, alpha, fail);
+                  ct = 1.f - (rk - 1.f) / alpha;
+                  if (it == 99999) fail = true;
+                }
+              }
+              Enew = DOP ? E * sample_doppler(g, T, mint, E, ct, fail) : E / rk;
+            } else {
+              ct = rayleigh(g, T, mint, E, fail);
+            }
+            const float phi = 2.f * kPi * g.u();
+            if (fail) ++C.fail;
+            w = rotate(w, ct, phi);
+            E = Enew;
+            ++order;
+            if (E < 1.f) {
+              alive = false;
+            } else if (order >= P.max_order) {
+              ++C.limit;
+              alive = false;
+            }
           }
         }
       }
+      if (has_rec || !(alive || next < total)) break;
     }
     if constexpr (!COMBINE) {
       // ---- pseudo-particle phase, per warp (no block barrier): the warp marches

@@ -45,7 +45,9 @@ def test_forced_detection_same_seed(gpu, oracle_lib, table_path, tables, nee_mod
     n_pp = st["nee_rays"] / max(1.0, st["compton"] + st["rayleigh"] + (st["photo"] if nee_mode else 0))
     for k, unit in (("compton", 1), ("rayleigh", 1), ("photo", 1), ("nee_rays", n_pp)):
         assert abs(st[k] - r["stats"][k]) <= max(3e-4 * r["stats"][k], 8 * unit), k
-    assert st["nee_rays"] > 100 * (st["compton"] + st["rayleigh"])  # every pixel (of the tile) per interaction
+    # every pixel of the panel (256), or of the history's tile (8 x 6, or 8 x 4 at the far edge), per interaction
+    per = st["nee_rays"] / (st["compton"] + st["rayleigh"] + (st["photo"] if nee_mode else 0))
+    assert (32 <= per <= 48) if tiles else abs(per - 256) < 1e-9, per
 
 
 def test_forced_detection_limits(gpu, table_path, tables):
