@@ -73,7 +73,14 @@ __device__ __forceinline__ uint32_t wg_off(int row, int k) {
 // store bias + optional ReLU, BF16 or FP32.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 8;
-constexpr int kSmemBudget = 225 * 1024;
+constexpr int kSmemBudget = 225 * 1024;  // the most one CTA may take
+// Shared memory the planner lets one forward CTA take: the whole budget (one
+// CTA per SM, the deepest ring) or less, so that several CTAs share an SM and
+// one's pipeline fill and epilogue overlap another's MMAs.
+#ifndef MC_CONV_PLAN_KB
+#define MC_CONV_PLAN_KB 225
+#endif
+constexpr int kPlanBudget = MC_CONV_PLAN_KB * 1024;
 
 struct FwdArgs {
   const __nv_bfloat16* wm;  // packed weights [cin/8][9][co_total][8]
@@ -447,7 +454,17 @@ uint32_t halo_bytes_for(int CC, int rbox, int wp) {
   return ((uint32_t)rbox * (uint32_t)wp * (uint32_t)(2 * CC) + 1023u) & ~1023u;
 }
 
+bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a, int& grid_x, int& grid_y,
+                     int& smem);
+
+// The plan within the planning budget, or within the whole budget when no tile fits the smaller one.
 bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int& grid_y, int& smem) {
+  return plan_fwd_budget(p, N, sms, kPlanBudget, a, grid_x, grid_y, smem) ||
+         plan_fwd_budget(p, N, sms, kSmemBudget, a, grid_x, grid_y, smem);
+}
+
+bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a, int& grid_x, int& grid_y,
+                     int& smem) {
   a.ws = p.w < 128 ? p.w : 128;
   a.strips = (p.w + a.ws - 1) / a.ws;
   a.wp = a.ws + 2;
@@ -468,7 +485,7 @@ bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int&
       const uint32_t halo = halo_bytes_for(CC, rbox, a.wp);
       const uint32_t stage = ((halo + (uint32_t)CC * 9u * N * 2u) + 1023u) & ~1023u;
       const int chunks = p.cin / CC;
-      int stages = (int)((kSmemBudget - 1024) / stage);
+      int stages = (int)((budget - 1024) / stage);
       if (stages > kMaxStages) stages = kMaxStages;
       if (stages > chunks) stages = chunks;
       if (stages < 1 || (stages < 2 && chunks > 1)) continue;
