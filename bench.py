@@ -373,15 +373,15 @@ def transport_source_hash():
 
 
 def recorded_traffic(workload):
-    """Per-march-step DRAM and L2 bytes of k_transport from the ncu summary in
-    profiles/ (a line 'traffic-per-step: kernel=<hash> workload=<name>
+    """Per-march-step DRAM and L2 bytes of k_transport from the ncu summaries
+    profiles/k_transport_<workload>*.md (a line 'traffic-per-step: kernel=<hash> workload=<name>
     dram_bytes=<x> l2_bytes=<y>'), or None when the summary was taken on other
     sources than the current kernel's."""
-    path = os.path.join(ROOT, "profiles", f"k_transport_{workload}.md")
-    try:
-        lines = open(path).read().splitlines()
-    except OSError:
-        return None
+    import glob
+
+    lines = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"k_transport_{workload}*.md"))):
+        lines += open(path).read().splitlines()
     want = transport_source_hash()
     for line in lines:
         if line.startswith("traffic-per-step:"):
@@ -611,7 +611,7 @@ def run_ours(args):
             "traffic_basis": None if rec is None else
             f"ncu dram__bytes_read.sum + dram__bytes_write.sum of a 2e6-photon launch of the same kernel, "
             f"{rec[0]:.4f} B per march step, scaled by the march steps of this launch; L2 bytes per step "
-            f"{rec[1]:.2f} (profiles/k_transport_{args.workload}.md)",
+            f"{rec[1]:.2f} (profiles/k_transport_{args.workload}*.md)",
             "kernel": "k_transport", "steps_per_launch": float(np.mean(steps_per)),
             "kernel_ms": mean_ms, "steps_per_s": float(np.mean(steps_per)) / (mean_ms / 1e3),
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",

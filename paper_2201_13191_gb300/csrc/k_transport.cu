@@ -99,13 +99,6 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 #endif
 constexpr int kLook = MC_LOOKAHEAD;
 
-// With MC_DEDUP a midpoint in the same voxel as the previous one issues no
-// load: the lane takes the previous word once all the group's loads are in
-// flight (fewer L1 requests when the step is shorter than the voxel).
-#ifndef MC_DEDUP
-#define MC_DEDUP 0
-#endif
-
 template <int LAYOUT>
 __device__ __forceinline__ void gather_group(const VolumeView& V, const VoxRay& r, int k0, float h, float ta,
                                              float3 hv, uint32_t (&wd)[kLook]) {
@@ -117,18 +110,7 @@ __device__ __forceinline__ void gather_group(const VolumeView& V, const VoxRay& 
     idx[u] = u == 0 ? r.voxel_p<LAYOUT>(V, bx, by, bz)
                     : r.voxel_p<LAYOUT>(V, fmaf((float)u, hv.x, bx), fmaf((float)u, hv.y, by), fmaf((float)u, hv.z, bz));
 #pragma unroll
-  for (int u = 0; u < kLook; ++u) {
-    if (MC_DEDUP && u > 0) {
-      wd[u] = 0u;
-      if (idx[u] != idx[u - 1]) wd[u] = __ldg(V.vox + idx[u]);
-    } else {
-      wd[u] = __ldg(V.vox + idx[u]);
-    }
-  }
-  if (MC_DEDUP) {
-#pragma unroll
-    for (int u = 1; u < kLook; ++u) wd[u] = idx[u] == idx[u - 1] ? wd[u - 1] : wd[u];
-  }
+  for (int u = 0; u < kLook; ++u) wd[u] = __ldg(V.vox + idx[u]);
 }
 
 // Adds the group's steps to the optical-depth sum acc (attenuation per unit
