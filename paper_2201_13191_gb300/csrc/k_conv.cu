@@ -78,7 +78,7 @@ constexpr int kSmemBudget = 225 * 1024;  // the most one CTA may take
 // CTA per SM, the deepest ring) or less, so that several CTAs share an SM and
 // one's pipeline fill and epilogue overlap another's MMAs.
 #ifndef MC_CONV_PLAN_KB
-#define MC_CONV_PLAN_KB 225
+#define MC_CONV_PLAN_KB 110
 #endif
 constexpr int kPlanBudget = MC_CONV_PLAN_KB * 1024;
 
@@ -101,7 +101,21 @@ __device__ __forceinline__ uint32_t tmem_cols(int n) {
   return c;
 }
 
-template <int N>
+// Tap folding (FOLD, for C_out tiles with 3N <= 256).  The three taps of one
+// kernel row (dy, dx = -1, 0, +1) share one MMA: the A operand is the halo seen
+// from the row shift dy*wp - 1 alone and B holds the three taps' weights side by
+// side (N_mma = 3N, contiguous in the packed [tap][co] order), so accumulator
+// row r collects, in column block dx, the contributions that output position
+// r - 1 - dx ... needs; the epilogue adds block -1 of row r, block 0 of row
+// r + 1 and block +1 of row r + 2.  That is 3 instead of 9 MMAs per k-step,
+// each three times wider (narrow-N MMAs are bound by their A operand reads),
+// and 126 instead of 128 output positions per accumulator.
+#ifndef MC_CONV_FOLD
+#define MC_CONV_FOLD 1
+#endif
+constexpr int kFoldRows = 126;
+
+template <int N, bool FOLD>
 __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_constant__ CUtensorMap xmap, const FwdArgs a) {
   extern __shared__ unsigned char dyn_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
@@ -116,12 +130,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
   const int strip = tile % a.strips;
   const int img = tile / a.strips;
   const int nb = blockIdx.y * N;  // first output channel of this CTA (within the launch's cout)
-  const int Mt = 128 * a.A;
+  constexpr int NA = FOLD ? 3 * N : N;         // accumulator columns
+  constexpr int RA = FOLD ? kFoldRows : 128;   // output positions per accumulator
+  const int Mt = RA * a.A;
   const int q0 = a.wp + 1 + t * Mt;           // first position: row 1, column 1 of the padded strip
   const int vr_lo = (q0 - a.wp - 1) / a.wp;   // first halo row (padded-strip row index)
   const int o0 = q0 - vr_lo * a.wp;           // halo index of q0
   const int n_chunks = a.cin / a.CC;
-  const uint32_t ncols = tmem_cols(a.A * N);
+  const uint32_t ncols = tmem_cols(a.A * NA);
 
   if (warp == 0) tc::tmem_alloc(&tmem_holder, ncols);
   if (tid == 0) {
@@ -179,8 +195,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      const uint32_t idesc = tc::idesc_bf16(128, N);
+      const uint32_t idesc = tc::idesc_bf16(128, NA);
       const uint32_t lbo_b = 9u * N * 16u;
+      constexpr int kGroups = FOLD ? 3 : 9;  // MMAs per k-step and accumulator: kernel rows or taps
       for (int st = 0; st < n_chunks; ++st) {
         const int slot = st % a.stages;
         if (!tc::mbar_wait(&full[slot], (uint32_t)(st / a.stages) & 1u)) {
@@ -190,17 +207,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
         tc::fence_after();
         const uint32_t hb = tc::saddr(sm + (size_t)slot * a.stage_bytes);
         const uint32_t wb = hb + a.halo_bytes;
-        for (int tap = 0; tap < 9; ++tap) {
-          const int shift = (tap / 3 - 1) * a.wp + (tap % 3 - 1);
+        for (int g = 0; g < kGroups; ++g) {
+          // first tap of the group and the row shift of its A operand
+          const int tap = FOLD ? 3 * g : g;
+          const int shift = FOLD ? (g - 1) * a.wp - 1 : (tap / 3 - 1) * a.wp + (tap % 3 - 1);
           for (int ks = 0; ks < a.CC / 16; ++ks) {
             const uint64_t db = tc::sdesc(wb + (uint32_t)((2 * ks * 9 + tap) * N) * 16u, lbo_b, 128);
             for (int acc = 0; acc < a.A; ++acc) {
               // rows of 2 CC bytes, 8-row groups 8 rb apart; k-step = 32 bytes within the row.  The
               // tensor core applies the swizzle on absolute shared-memory address bits, like the TMA
               // that wrote the tile, so a start shifted by any number of rows needs no phase field.
-              const uint32_t sa = hb + (uint32_t)(o0 + 128 * acc + shift) * (uint32_t)a.rb + (uint32_t)ks * 32u;
+              const uint32_t sa = hb + (uint32_t)(o0 + RA * acc + shift) * (uint32_t)a.rb + (uint32_t)ks * 32u;
               const uint64_t da = tc::sdesc_swz(sa, 8u * (uint32_t)a.rb, a.rb);
-              tc::mma_bf16(tmem + (uint32_t)(acc * N), da, db, idesc, (st | tap | ks) ? 1u : 0u);
+              tc::mma_bf16(tmem + (uint32_t)(acc * NA), da, db, idesc, (st | g | ks) ? 1u : 0u);
             }
           }
         }
@@ -212,20 +231,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_fwd(const __grid_consta
   }
   bool ok = tc::mbar_wait(&done, 0);
   tc::fence_after();
-  ok = ok && !abort_flag;
+  // one decision for the whole CTA: the folded epilogue synchronises its threads
+  ok = __syncthreads_and(ok && !abort_flag) != 0;
   if (!ok && tid == 0) atomicOr(a.err, 1);
   if (ok) {
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // exchange rows of the folded epilogue: the ring is idle once `done` has completed
+    constexpr int kX = 20;  // floats per row (16 used; 80-byte rows keep float4 reads conflict-free)
+    float* xch = reinterpret_cast<float*>(sm);
     for (int acc = 0; acc < a.A; ++acc) {
-      const int q = q0 + 128 * acc + tid;
+      const int q = q0 + RA * acc + tid;
       const int vr = q / a.wp, vc = q - vr * a.wp;
       const int y = vr - 1, x = strip * a.ws + vc - 1;
-      const bool valid = vr >= 1 && vr <= a.h && vc >= 1 && vc <= a.ws && x < a.w;
+      const bool valid = (!FOLD || tid < kFoldRows) && vr >= 1 && vr <= a.h && vc >= 1 && vc <= a.ws && x < a.w;
       const long long pix = ((long long)img * a.h + y) * a.w + x;
 #pragma unroll 1
       for (int c0 = 0; c0 < N; c0 += 8) {
         float v[8];
-        tc::tmem_ld8(lane_base + (uint32_t)(acc * N + c0), v);
+        tc::tmem_ld8(lane_base + (uint32_t)(acc * NA + c0), v);
+        if (FOLD) {
+          float v0[8], vp[8];
+          tc::tmem_ld8(lane_base + (uint32_t)(acc * NA + N + c0), v0);
+          tc::tmem_ld8(lane_base + (uint32_t)(acc * NA + 2 * N + c0), vp);
+          __syncthreads();  // the previous chunk's reads of xch are done
+          float4* mine = reinterpret_cast<float4*>(xch + tid * kX);
+          mine[0] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+          mine[1] = make_float4(v0[4], v0[5], v0[6], v0[7]);
+          mine[2] = make_float4(vp[0], vp[1], vp[2], vp[3]);
+          mine[3] = make_float4(vp[4], vp[5], vp[6], vp[7]);
+          __syncthreads();
+          if (tid < kFoldRows) {
+            const float4* r1 = reinterpret_cast<const float4*>(xch + (tid + 1) * kX);
+            const float4* r2 = reinterpret_cast<const float4*>(xch + (tid + 2) * kX);
+            const float4 a0 = r1[0], a1 = r1[1], b0 = r2[2], b1 = r2[3];
+            v[0] += a0.x + b0.x; v[1] += a0.y + b0.y; v[2] += a0.z + b0.z; v[3] += a0.w + b0.w;
+            v[4] += a1.x + b1.x; v[5] += a1.y + b1.y; v[6] += a1.z + b1.z; v[7] += a1.w + b1.w;
+          }
+        }
         const int co = nb + c0;
         if (valid && co < a.cout) {
 #pragma unroll
@@ -454,25 +496,34 @@ uint32_t halo_bytes_for(int CC, int rbox, int wp) {
   return ((uint32_t)rbox * (uint32_t)wp * (uint32_t)(2 * CC) + 1023u) & ~1023u;
 }
 
-bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a, int& grid_x, int& grid_y,
-                     int& smem);
+bool plan_fwd_budget(const ConvParams& p, int N, bool fold, int sms, int budget, FwdArgs& a, int& grid_x,
+                     int& grid_y, int& smem);
 
 // The plan within the planning budget, or within the whole budget when no tile fits the smaller one.
-bool plan_fwd(const ConvParams& p, int N, int sms, FwdArgs& a, int& grid_x, int& grid_y, int& smem) {
-  return plan_fwd_budget(p, N, sms, kPlanBudget, a, grid_x, grid_y, smem) ||
-         plan_fwd_budget(p, N, sms, kSmemBudget, a, grid_x, grid_y, smem);
+bool plan_fwd(const ConvParams& p, int N, bool fold, int sms, FwdArgs& a, int& grid_x, int& grid_y, int& smem) {
+  return plan_fwd_budget(p, N, fold, sms, kPlanBudget, a, grid_x, grid_y, smem) ||
+         plan_fwd_budget(p, N, fold, sms, kSmemBudget, a, grid_x, grid_y, smem);
 }
 
-bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a, int& grid_x, int& grid_y,
-                     int& smem) {
+int tmem_cols_host(int n) {
+  int c = 32;
+  while (c < n) c <<= 1;
+  return c;
+}
+
+bool plan_fwd_budget(const ConvParams& p, int N, bool fold, int sms, int budget, FwdArgs& a, int& grid_x,
+                     int& grid_y, int& smem) {
   a.ws = p.w < 128 ? p.w : 128;
   a.strips = (p.w + a.ws - 1) / a.ws;
   a.wp = a.ws + 2;
   grid_y = (p.cout + N - 1) / N;
+  const int NA = fold ? 3 * N : N;             // accumulator columns
+  const int RA = fold ? kFoldRows : 128;       // output positions per accumulator
+  const int min_bytes = 128 * 20 * 4 + 1024;   // the folded epilogue's exchange rows
   double best_cost = -1.0;
   for (int A = 8; A >= 1; A >>= 1) {
-    if (A * N > 512) continue;
-    const int Mt = 128 * A;
+    if (A * NA > 512) continue;
+    const int Mt = RA * A;
     const int rbox = (Mt + 2 * a.wp + 1) / a.wp + 2;
     if (rbox > 256) continue;
     const int tiles = ((p.h - 1) * a.wp + a.ws + Mt - 1) / Mt;
@@ -498,9 +549,10 @@ bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a
       }
     }
     if (bestScore < 0) continue;
-    const int bytes = (int)(bestStage * bestStages) + 1024;
+    int bytes = (int)(bestStage * bestStages) + 1024;
+    if (fold && bytes < min_bytes) bytes = min_bytes;
     int per_sm = (228 * 1024) / (bytes + 1024);
-    const int by_tmem = 512 / (int)(A * N <= 32 ? 32 : A * N);
+    const int by_tmem = 512 / tmem_cols_host(A * NA);
     if (per_sm > by_tmem) per_sm = by_tmem;
     if (per_sm < 1) per_sm = 1;
     const long long slots = (long long)sms * per_sm;
@@ -523,15 +575,32 @@ bool plan_fwd_budget(const ConvParams& p, int N, int sms, int budget, FwdArgs& a
   return best_cost >= 0;
 }
 
+template <int N, bool FOLD>
+cudaError_t launch_fwd_kernel(const CUtensorMap& map, const FwdArgs& a, int gx, int gy, int smem, cudaStream_t s) {
+  static unsigned long long smem_set = 0;  // devices on which the attribute was raised
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(smem_set & bit)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_conv3x3_fwd<N, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 1024);
+    if (e != cudaSuccess) return e;
+    smem_set |= bit;
+  }
+  k_conv3x3_fwd<N, FOLD><<<dim3((unsigned)gx, (unsigned)gy), kThreads, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
   int dev0 = 0, sms = 0;
   cudaGetDevice(&dev0);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev0);
   if (sms < 1) sms = 1;
+  constexpr bool fold = MC_CONV_FOLD && N == 16;  // measured: a gain at N = 16 only
   FwdArgs a{};
   int gx = 0, gy = 0, smem = 0;
-  if (!plan_fwd(p, N, sms, a, gx, gy, smem)) return cudaErrorInvalidValue;
+  if (!plan_fwd(p, N, fold, sms, a, gx, gy, smem)) return cudaErrorInvalidValue;
   a.wm = p.wt;
   a.bias = p.bias;
   a.y = p.y;
@@ -559,18 +628,10 @@ cudaError_t launch_fwd_n(const ConvParams& p, cudaStream_t s) {
           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  static unsigned long long smem_set = 0;  // devices on which the attribute was raised
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(smem_set & bit)) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_conv3x3_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 1024);
-    if (e != cudaSuccess) return e;
-    smem_set |= bit;
-  }
-  k_conv3x3_fwd<N><<<dim3((unsigned)gx, (unsigned)gy), kThreads, smem, s>>>(map, a);
-  return cudaGetLastError();
+  if constexpr (fold)
+    return launch_fwd_kernel<N, true>(map, a, gx, gy, smem, s);
+  else
+    return launch_fwd_kernel<N, false>(map, a, gx, gy, smem, s);
 }
 
 template <int N>
