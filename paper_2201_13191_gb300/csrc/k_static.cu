@@ -220,7 +220,7 @@ extern "C" int mc_project_scatter_static(mc_ctx* ctx, const float* angles_rad, i
   const int smem = transport_smem_bytes(tv, nb, block);
   int per_sm = opt.blocks_per_sm;
   if (per_sm == 0) {
-    e = transport_occupancy(block, smem, &per_sm);
+    e = transport_occupancy(block, smem, &per_sm, false, vv.layout);
     if (e != cudaSuccess) return static_cuda_fail(ctx, e, "occupancy query");
     per_sm = per_sm > 0 ? per_sm : 1;
   }

@@ -404,8 +404,9 @@ struct Records {
 // reach this point together (the active mask) and share an offset are combined
 // by a shuffle sum; the lowest lane of each group does the one add.
 // COMBINE = false: one FP64 atomic add per pseudo-particle, no other code
-// (measured fastest on every workload: the tally is one add per ~200 march
-// steps).  COMBINE = true: TALLY_WARP or TALLY_SHARED as selected at run time.
+// (the fastest unstratified tally on every workload measured: the tally is one
+// add per ~200 march steps).  COMBINE = true: TALLY_WARP, TALLY_SHARED or
+// TALLY_TILED as selected at run time.
 template <bool COMBINE>
 __device__ __forceinline__ void tally_add(const TransportParams& P, float* s_img, size_t off, float v);
 
@@ -585,6 +586,11 @@ __device__ __forceinline__ void pseudo_particle(const TransportParams& P, const 
 #ifndef MC_MIN_BLOCKS
 #define MC_MIN_BLOCKS 2
 #endif
+// The same for the brick layout (volumes in HBM, where more warps in flight hide
+// the longer gathers).
+#ifndef MC_MIN_BLOCKS_BRICK
+#define MC_MIN_BLOCKS_BRICK MC_MIN_BLOCKS
+#endif
 // Flights through a linear-layout volume sum each group's optical depth
 // branch-free before looking for the interaction step (1), or test every step
 // (0); both give the same interaction points.
@@ -651,7 +657,8 @@ __device__ void tile_fetch(const TransportParams& P, uint2 key, TileChunk& c) {
 }
 
 template <int LAYOUT, bool COMBINE, bool EV, bool DOP>
-__global__ void __launch_bounds__(256, MC_MIN_BLOCKS) k_transport(const TransportParams P) {
+__global__ void __launch_bounds__(256, LAYOUT == VOX_BRICK ? MC_MIN_BLOCKS_BRICK : MC_MIN_BLOCKS)
+    k_transport(const TransportParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ int s_nrec, s_job;
@@ -1150,8 +1157,10 @@ cudaError_t launch_one(const TransportParams& p, int grid, int block, int smem, 
 }
 }  // namespace
 
-cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh) {
-  auto* k = mesh ? k_transport<GEO_MESH, false, false, false> : k_transport<VOX_LIN, false, false, false>;
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh, int layout) {
+  auto* k = mesh                    ? k_transport<GEO_MESH, false, false, false>
+            : layout == VOX_BRICK ? k_transport<VOX_BRICK, false, false, false>
+                                  : k_transport<VOX_LIN, false, false, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);

@@ -491,7 +491,8 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     } else if (ctx->opt.tally_mode == MC_TALLY_WARP) {
       tp.tally_mode = TALLY_WARP;
     } else {
-      // automatic and global: plain FP64 adds, measured fastest even on an 8 x 8 panel
+      // automatic and global: plain FP64 adds, the fastest of the unstratified tallies (measured down to
+      // an 8 x 8 panel); the tile-stratified tally is chosen explicitly or by the autotuner
       tp.tally_mode = TALLY_GLOBAL;
     }
     if (tp.forced) {
@@ -504,7 +505,7 @@ int project_impl(mc_ctx* ctx, const float* angles, int n_angles, uint64_t N, uin
     const int smem = transport_smem_bytes(tp.tab, sv.n_bins, block, transport_shared_pixels(tp));
     int per_sm = ctx->opt.blocks_per_sm;
     if (per_sm == 0) {
-      CK(transport_occupancy(block, smem, &per_sm, ctx->mesh_mode), "occupancy query");
+      CK(transport_occupancy(block, smem, &per_sm, ctx->mesh_mode, ctx->layout), "occupancy query");
       per_sm = std::max(1, per_sm);
     }
     const unsigned long long work = (unsigned long long)n_angles * h_count;
@@ -1063,7 +1064,7 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   {
     const TableView tv = table_view(ctx);
     smem = transport_smem_bytes(tv, (int)ctx->S.size(), 256, 0);
-    e = transport_occupancy(256, smem, &max_per_sm);
+    e = transport_occupancy(256, smem, &max_per_sm, ctx->mesh_mode, ctx->layout);
     if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "occupancy query"));
   }
   double best_rate = -1;
@@ -1072,7 +1073,8 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   const int tallies[2] = {MC_TALLY_GLOBAL, MC_TALLY_WARP};
   for (int bi = 0; bi < 3; ++bi) {
     int occ = 1;
-    e = transport_occupancy(blocks[bi], transport_smem_bytes(table_view(ctx), (int)ctx->S.size(), blocks[bi], 0), &occ);
+    e = transport_occupancy(blocks[bi], transport_smem_bytes(table_view(ctx), (int)ctx->S.size(), blocks[bi], 0), &occ,
+                            ctx->mesh_mode, ctx->layout);
     if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "occupancy query"));
     for (int per = 1; per <= std::max(1, occ); ++per) {
       for (int ti = 0; ti < 2; ++ti) {
@@ -1208,7 +1210,7 @@ int mc_autotune(mc_ctx* ctx, const float* angles, int n_angles, uint64_t probe, 
   out->step_mm = best_step;
   out->block_size = best.block_size;
   out->blocks_per_sm = best.blocks_per_sm;
-  out->tally_mode = best.tally_mode;
+  out->tally_mode = ctx->opt.tally_mode;  // the tile-stratified tally when step 4 kept a tile shape
   out->histories_per_s = best_rate;
   out->step_error = best_err;
   (void)max_per_sm;

@@ -160,7 +160,7 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, cuda
 int transport_smem_bytes(const TableView& t, int n_bins, int block, int shared_pixels = 0);
 // FP32 pixels of the shared tally image the kernel keeps for these parameters
 int transport_shared_pixels(const TransportParams& p);
-cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh = false);
+cudaError_t transport_occupancy(int block, int smem, int* blocks_per_sm, bool mesh = false, int layout = VOX_LIN);
 cudaError_t launch_finalize(const double* tally, int n_batches, size_t n, float* out, float* var, cudaStream_t s);
 cudaError_t launch_primary(const PrimaryParams& p, cudaStream_t s);
 // Fraction of x-neighbour voxel pairs of a device material array whose materials differ (synchronises s).
