@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--per-angle", action="store_true", help="one mc_project call per angle instead of one batch")
     p.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-tiled-alt", action="store_true",
+                   help="skip the extra (untimed-for-value) run of the tile-stratified tally")
     p.add_argument("--detector", default="energy", choices=["energy", "panel"],
                    help="detector response: energy integrating (eta = E) or the flat-panel Gd2O2S model")
     p.add_argument("--autotune", action="store_true",
@@ -597,6 +599,26 @@ def run_ours(args):
             e2e_s = max_time(e2e_s, device="cuda")
         e2e_value = world * N * n_ang * e2e_steps / e2e_s
 
+    # the same projection with the tile-stratified tally (16x16 tiles: shared-memory
+    # tile images flushed into the FP64 image per chunk), outside the timed region:
+    # its kernel rate beside the headline's plain global tally
+    tiled_alt = None
+    if args.tally in ("auto", "global") and not args.per_angle and n_ang == 1 and not args.no_tiled_alt:
+        ctx.set_options(tally_mode=4, tile_u=16, tile_v=16)
+        for k in range(2):
+            ctx.project(angles, N, wl["step_mm"], seed + 200 + k, out=out, stream=stream)
+        tk = []
+        for k in range(3):
+            flush.zero_()
+            ctx.project(angles, N, wl["step_mm"], seed + 300 + k, out=out, stream=stream)
+            tk.append(ctx.last_stats()["transport_ms"])
+        torch.cuda.synchronize()
+        ctx.set_options(tally_mode=tally, tile_u=args.tile[0], tile_v=args.tile[1])
+        tiled_alt = {"tally": "tiled 16x16", "histories_per_s": N * n_ang / (float(np.mean(tk)) / 1e3),
+                     "transport_ms": float(np.mean(tk)), "reps": len(tk),
+                     "note": "transport kernel time (CUDA events), L2 flushed between reps; its noise per history "
+                             "and figure of merit against the global tally: profiles/tally_modes_ell256.md"}
+
     # roofline of the dominant kernel (transport): FP32 issue
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
@@ -661,6 +683,7 @@ def run_ours(args):
             "s_per_projection": el_ms / 1e3 / args.steps / n_ang,
             "s_per_projection_at_2pct": None if c4 is None else c4["s_per_projection_at_2pct"],
             "denoised_scatter": c4,
+            "tally_tiled_alt": tiled_alt,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -665,7 +665,12 @@ __global__ void __launch_bounds__(256, LAYOUT == VOX_BRICK ? MC_MIN_BLOCKS_BRICK
   __shared__ int s_bucket[kBuckets + 1];
   __shared__ TileChunk s_tc;
   const bool tiled = COMBINE && P.tally_mode == TALLY_TILED;
-  constexpr int kFlights = COMBINE ? 1 : MC_FLIGHTS_PER_ITER;
+  // Block-wide phases (a block queue of records, jobs sorted over the block)
+  // for the combined tallies, whose shared images need them, and for volumes
+  // in HBM (brick layout), where they were measured faster than per-warp
+  // phases; per-warp phases otherwise.
+  constexpr bool kBlockPhases = COMBINE || LAYOUT == VOX_BRICK;
+  constexpr int kFlights = kBlockPhases ? 1 : MC_FLIGHTS_PER_ITER;
   const int nm = P.tab.n_mat, ns = P.tab.n_stage;
   const int nb = P.spec.n_bins;
   const int B = blockDim.x;
@@ -921,9 +926,9 @@ __global__ void __launch_bounds__(256, LAYOUT == VOX_BRICK ? MC_MIN_BLOCKS_BRICK
           } else {
             // queue the interaction; its pseudo-particles use the next counter blocks, one each
             g.align();
-            // block-wide queue (combined tallies) or the lane's own slot (per-warp phases)
+            // the block-wide queue (block-wide phases) or the lane's own slot (per-warp phases)
             int r;
-            if constexpr (COMBINE) {
+            if constexpr (kBlockPhases) {
               r = atomicAdd(&s_nrec, 1);
             } else {
               r = threadIdx.x;
@@ -988,7 +993,7 @@ __global__ void __launch_bounds__(256, LAYOUT == VOX_BRICK ? MC_MIN_BLOCKS_BRICK
       }
       if (has_rec || !(alive || next < total)) break;
     }
-    if constexpr (!COMBINE) {
+    if constexpr (!kBlockPhases) {
       // ---- pseudo-particle phase, per warp (no block barrier): the warp marches
       // its own lanes' queued rays, records ranked by chord length, longest first
       const unsigned recmask = __ballot_sync(0xffffffffu, has_rec);
