@@ -366,7 +366,7 @@ typedef struct mc_tuning {
   float step_mm;
   int block_size;
   int blocks_per_sm;
-  int tally_mode;
+  int tally_mode;      /* the mode written into the options: MC_TALLY_TILED when step 4 kept a tile shape */
   double histories_per_s;
   double step_error;   /* relative L2 of the chosen step's primary vs step_min */
   float rr_threshold;  /* chosen Russian-roulette threshold (0: off) */
