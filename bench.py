@@ -232,14 +232,16 @@ def _oracle_blocks(orcs, wl, n_photons, blocks, block):
     from concurrent.futures import ThreadPoolExecutor
 
     def run(i):
+        steps = 0
         for b in blocks[i :: len(orcs)]:
-            orcs[i].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], int(b), int(min(b + block, n_photons)))
+            st = orcs[i].scatter(0.0, n_photons, wl["step_mm"], wl["seed"], int(b), int(min(b + block, n_photons)))
+            steps += st["stats"]["flight_steps"] + st["stats"]["nee_steps"]
+        return steps
 
     if len(orcs) == 1:
-        run(0)
-        return
+        return run(0)
     with ThreadPoolExecutor(len(orcs)) as ex:
-        list(ex.map(run, range(len(orcs))))
+        return sum(ex.map(run, range(len(orcs))))
 
 
 def spread_blocks(n_photons, n_blocks, block, phase=0.0):
@@ -275,14 +277,15 @@ def oracle_rate(tp, wl, n_photons, budget_s, threads=1):
     block = 512
     starts = spread_blocks(n_photons, max(threads, n_hist // block), block, 0.25)
     t0 = time.perf_counter()
-    _oracle_blocks(orcs, wl, n_photons, starts, block)
+    steps = _oracle_blocks(orcs, wl, n_photons, starts, block)
     dt = time.perf_counter() - t0
     done = sum(min(b + block, n_photons) - b for b in starts)
     rate = n_photons / (t_primary + n_photons * dt / done)
+    steps_per_s = steps / dt  # march steps per second of the sampled histories, all threads
     sample = (f"oracle, {threads} thread(s): primary image once, single thread ({t_primary:.2f} s) + {done} histories "
               f"in {len(starts)} blocks of {block} spread evenly over the {int(n_photons)}-photon run ({dt:.1f} s "
               "wall), extrapolated to one full projection")
-    return rate, sample, rate1
+    return rate, sample, rate1, steps_per_s
 
 
 def make_inputs(tables_dir, photons, workload=WORKLOAD):
@@ -377,7 +380,7 @@ def transport_source_hash():
 def recorded_traffic(workload):
     """Per-march-step DRAM and L2 bytes of k_transport from the ncu summaries
     profiles/k_transport_<workload>*.md (a line 'traffic-per-step: kernel=<hash> workload=<name>
-    dram_bytes=<x> l2_bytes=<y>'), or None when the summary was taken on other
+    dram_bytes=<x> l2_bytes=<y> [simt_lanes=<z>]'), or None when the summary was taken on other
     sources than the current kernel's."""
     import glob
 
@@ -389,7 +392,7 @@ def recorded_traffic(workload):
         if line.startswith("traffic-per-step:"):
             kv = dict(x.split("=", 1) for x in line.split()[1:])
             if kv.get("kernel") == want and kv.get("workload") == workload:
-                return float(kv["dram_bytes"]), float(kv["l2_bytes"])
+                return float(kv["dram_bytes"]), float(kv["l2_bytes"]), float(kv.get("simt_lanes", "nan"))
     return None
 
 
@@ -645,6 +648,9 @@ def run_ours(args):
         # bytes the kernel moves from L2 per march step (ncu), against the algorithmic 3
         roof["memory"]["l2_bytes_per_step"] = rec[1]
         roof["memory"]["l2_traffic_over_algorithmic"] = rec[1] / 3.0
+        if np.isfinite(rec[2]):
+            # branch efficiency: active lanes per warp instruction (ncu thread / warp instructions) of 32
+            roof["branch_efficiency"] = rec[2] / 32.0
 
     # the second half of the metric: seconds per projection at <= 2% scatter
     # error for plain MC, Savitzky-Golay smoothing and the learned denoiser
@@ -663,9 +669,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores, cpu_name = host_cpu()
-        rate, sample, rate1 = oracle_rate(tp, wl, N, args.cpu_seconds, threads=cores)
+        rate, sample, rate1, sps = oracle_rate(tp, wl, N, args.cpu_seconds, threads=cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "value_1_thread": rate1, "cpu": cpu_name}
+               "value_1_thread": rate1, "steps_per_s": sps, "cpu": cpu_name}
 
     if rank == 0:
         line = {

@@ -65,3 +65,34 @@ def test_tiled_mode_limits(gpu, table_path, tables):
     a = one.project([0.3], 200_000, 0.5, 3, primary=False)["scatter"].cpu().numpy()
     b = ref.project([0.3], 200_000, 0.5, 3, primary=False)["scatter"].cpu().numpy()
     np.testing.assert_allclose(a, b, rtol=2e-5, atol=1e-12)
+
+
+def test_tiled_full_size_ell256_16x16(gpu, oracle_lib, table_path, tables):
+    """The bench's tile-stratified side run (ell256: 256^3, 512^2, 1e8 photons, 16x16 tiles): histories from
+    the middle of the run, recomputed one by one on both sides, match history for history; a 4000-history
+    block agrees to a small fraction of its noise."""
+    wl = make_workload("ell256", tables)
+    N = wl["n_photons"]
+    c = _ctx(gpu, table_path, wl, tally_mode=4, tile_u=16, tile_v=16)
+    o = _orc(oracle_lib, table_path, wl)
+    o.set_tiles(16, 16)
+    h0 = 41_000_000
+    same, close, scat = 0, 0, 0
+    for h in range(h0, h0 + 200):
+        g = c.project_histories([0.0], N, h, 1, wl["step_mm"], wl["seed"])[0].cpu().numpy().astype(np.float64)
+        ref = o.scatter(0.0, N, wl["step_mm"], wl["seed"], h_begin=h, h_end=h + 1)["Is"]
+        if ref.sum() == 0 and g.sum() == 0:
+            continue
+        scat += 1
+        l1 = np.abs(g - ref).sum() / ref.sum()
+        same += l1 < 1e-4
+        close += l1 < 1e-2  # a midpoint within rounding of a voxel face may see the neighbouring voxel
+    assert scat >= 20, scat
+    assert same >= 0.8 * scat and close >= 0.95 * scat, (same, close, scat)
+    cnt = 4000
+    g = c.project_histories([0.0], N, h0, cnt, wl["step_mm"], wl["seed"])[0].cpu().numpy().astype(np.float64)
+    ref = o.scatter(0.0, N, wl["step_mm"], wl["seed"], h_begin=h0, h_end=h0 + cnt)["Is"]
+    parts = np.array([o.scatter(0.0, N, wl["step_mm"], wl["seed"] + 1, h_begin=h0 + b * cnt // 10,
+                                h_end=h0 + (b + 1) * cnt // 10)["Is"] for b in range(10)])
+    var = parts.var(axis=0, ddof=1) * 10
+    assert np.linalg.norm(g - ref) <= 0.2 * np.linalg.norm(np.sqrt(var))
