@@ -339,15 +339,17 @@ def run_reference(args):
 
     def one_step(k):
         starts = spread_blocks(N, n_blocks, block, (k * golden) % 1.0)
-        _oracle_blocks(orcs, wl, N, starts, block)
-        return sum(min(b + block, N) - b for b in starts)
+        steps = _oracle_blocks(orcs, wl, N, starts, block)
+        return sum(min(b + block, N) - b for b in starts), steps
 
     for k in range(args.warmup):
         one_step(k)
-    done = 0
+    done, marched = 0, 0
     t0 = time.perf_counter()
     for k in range(args.steps):
-        done += one_step(args.warmup + k)
+        d, m = one_step(args.warmup + k)
+        done += d
+        marched += m
     el = time.perf_counter() - t0
     value = done / el
     line = {
@@ -356,6 +358,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": bench_config(args, wl),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_name,
+                         "steps_per_s": marched / el,
                          "sample": f"per step {n_blocks} blocks of {block} scatter histories spread evenly over the "
                                    f"{N}-photon run (new phase each step), {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
