@@ -370,13 +370,16 @@ TRANSPORT_SOURCES = ("paper_2201_13191_gb300/csrc/k_transport.cu", "paper_2201_1
 
 
 def transport_source_hash():
-    """First 16 hex digits of the SHA-256 of the transport kernel's sources."""
+    """First 16 hex digits of the SHA-256 of the transport kernel's sources and its compiler flags."""
     import hashlib
+
+    from paper_2201_13191_gb300.build import FLAGS, SOURCE_FLAGS
 
     h = hashlib.sha256()
     for f in TRANSPORT_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
+    h.update(" ".join(FLAGS + SOURCE_FLAGS.get("k_transport.cu", [])).encode())
     return h.hexdigest()[:16]
 
 

@@ -24,6 +24,11 @@ SOURCES = ["mc_api.cu", "k_transport.cu", "k_primary.cu", "k_post.cu", "k_static
 PROBE_SOURCES = ["probe/k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+# Per translation unit: the transport takes division and square root in their
+# fast forms (within 2 ulp; denormals flushed): its per-ray set-up divides
+# several times (chord clipping, step length, pdf factors), and the IEEE forms
+# cost 7% of the kernel.  The primary image keeps IEEE division (its 1e-5 bar).
+SOURCE_FLAGS = {"k_transport.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc():
@@ -61,7 +66,7 @@ def _build(out, sources, header, force, verbose, extra):
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace("/", "_").replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *SOURCE_FLAGS.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
