@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t wg_off(int row, int k) {
 // ---------------------------------------------------------------------------
 // Forward (and input-gradient) convolution.
 //
-// Tiling.  The image is cut into column strips of width ws = min(w, 128); a
+// Tiling.  The image is cut into column strips of width ws = min(w, MC_CONV_WS); a
 // strip with its one-pixel border (the neighbouring strips' columns, or zeros
 // at the image edge) and a zero row above and below is the "padded strip", of
 // width wp = ws + 2, linearised row-major.  A CTA computes A x 128 consecutive
@@ -81,6 +81,12 @@ constexpr int kSmemBudget = 225 * 1024;  // the most one CTA may take
 #define MC_CONV_PLAN_KB 110
 #endif
 constexpr int kPlanBudget = MC_CONV_PLAN_KB * 1024;
+// Widest strip (columns) the forward tiles cut an image into: narrower strips
+// cut the halo rows a tile fetches (measured 301.6 / 307.9 / 312.3 TFLOP/s
+// FLOP-weighted at 128 / 64 / 32 over the denoiser's layers).
+#ifndef MC_CONV_WS
+#define MC_CONV_WS 32
+#endif
 
 struct FwdArgs {
   const __nv_bfloat16* wm;  // packed weights [cin/8][9][co_total][8]
@@ -513,7 +519,7 @@ int tmem_cols_host(int n) {
 
 bool plan_fwd_budget(const ConvParams& p, int N, bool fold, int sms, int budget, FwdArgs& a, int& grid_x,
                      int& grid_y, int& smem) {
-  a.ws = p.w < 128 ? p.w : 128;
+  a.ws = p.w < MC_CONV_WS ? p.w : MC_CONV_WS;
   a.strips = (p.w + a.ws - 1) / a.ws;
   a.wp = a.ws + 2;
   grid_y = (p.cout + N - 1) / N;

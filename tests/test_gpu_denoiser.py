@@ -23,7 +23,7 @@ def _bf(torch, a):
 
 
 @pytest.mark.parametrize("shape", [(2, 16, 24, 16, 32), (1, 10, 13, 32, 48), (1, 8, 8, 384, 128), (2, 9, 16, 64, 256),
-                                   (1, 4, 4, 16, 16)])
+                                   (1, 4, 4, 16, 16), (2, 7, 80, 32, 32), (1, 5, 150, 96, 16)])
 def test_conv3x3_forward_parity(gpu, shape):
     torch = pytest.importorskip("torch")
     n, h, w, cin, cout = shape
