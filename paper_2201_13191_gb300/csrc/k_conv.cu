@@ -81,6 +81,11 @@ constexpr int kSmemBudget = 225 * 1024;  // the most one CTA may take
 #define MC_CONV_PLAN_KB 110
 #endif
 constexpr int kPlanBudget = MC_CONV_PLAN_KB * 1024;
+// Output-channel tiles narrower than C_out when the grid would not cover the
+// SMs (1), or always C_out rounded up (0).
+#ifndef MC_CONV_SPLIT_N
+#define MC_CONV_SPLIT_N 1
+#endif
 // Widest strip (columns) the forward tiles cut an image into: narrower strips
 // cut the halo rows a tile fetches (measured 301.6 / 307.9 / 312.3 TFLOP/s
 // FLOP-weighted at 128 / 64 / 32 over the denoiser's layers).
@@ -659,11 +664,27 @@ cudaError_t launch_conv3x3_fwd(const ConvParams& p, cudaStream_t s) {
   if (p.cin % 16 || p.cout % 16 || p.cin < 16 || p.cout < 16 || p.co_total < p.co0 + p.cout || p.n < 1 || p.h < 1 ||
       p.w < 1 || ((uintptr_t)p.x & 15) || ((uintptr_t)p.wt & 15))
     return cudaErrorInvalidValue;
-  if (p.cout <= 16) return launch_fwd_n<16>(p, s);
-  if (p.cout <= 32) return launch_fwd_n<32>(p, s);
-  if (p.cout <= 64) return launch_fwd_n<64>(p, s);
-  if (p.cout <= 128) return launch_fwd_n<128>(p, s);
-  return launch_fwd_n<256>(p, s);
+  int N = p.cout <= 16 ? 16 : p.cout <= 32 ? 32 : p.cout <= 64 ? 64 : p.cout <= 128 ? 128 : 256;
+  if (MC_CONV_SPLIT_N) {
+    // small images: narrower output-channel tiles (more CTAs, each reading the same input tile) until the
+    // grid covers the SMs
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (N > 64) {
+      FwdArgs a{};
+      int gx = 0, gy = 0, smem = 0;
+      if (!plan_fwd(p, N, false, sms, a, gx, gy, smem) || (long long)gx * gy >= sms) break;
+      N >>= 1;
+    }
+  }
+  switch (N) {
+    case 16: return launch_fwd_n<16>(p, s);
+    case 32: return launch_fwd_n<32>(p, s);
+    case 64: return launch_fwd_n<64>(p, s);
+    case 128: return launch_fwd_n<128>(p, s);
+    default: return launch_fwd_n<256>(p, s);
+  }
 }
 
 cudaError_t launch_conv3x3_wgrad(const WgradParams& p, int splits, cudaStream_t s) {
