@@ -98,6 +98,13 @@ __device__ __forceinline__ void fill_mu(const SmemTables& T, float E, float* smu
 #define MC_LOOKAHEAD 8
 #endif
 constexpr int kLook = MC_LOOKAHEAD;
+// Brick layout (volumes in HBM): every group of a march masks its steps past
+// the end (1), or whole groups run unmasked and one tail group is masked (0,
+// the linear layout's form).  The single masked loop measured 28% faster for
+// bricks (ell512, 36 angles: 4880 -> 3503 ms), with the same steps.
+#ifndef MC_BRICK_NOSPLIT
+#define MC_BRICK_NOSPLIT 1
+#endif
 
 template <int LAYOUT>
 __device__ __forceinline__ void gather_group(const VolumeView& V, const VoxRay& r, int k0, float h, float ta,
@@ -159,6 +166,13 @@ __device__ __forceinline__ float march_tau(const VolumeView& V, float3 x, float3
   const float3 hv = make_float3(h * r.vw.x, h * r.vw.y, h * r.vw.z);
   float acc = 0.f, mu = 0.f;
   int cur = -1, k0 = 0;
+  if (LAYOUT == VOX_BRICK && MC_BRICK_NOSPLIT) {
+    for (; k0 < n; k0 += kLook) {
+      uint32_t wd[kLook];
+      gather_group<LAYOUT>(V, r, k0, h, ta, hv, wd);
+      tau_group<LAYOUT, true>(wd, k0, n, smu, stride, acc, cur, mu);
+    }
+  }
   for (; k0 + kLook <= n; k0 += kLook) {
     uint32_t wd[kLook];
     gather_group<LAYOUT>(V, r, k0, h, ta, hv, wd);
@@ -892,6 +906,13 @@ __global__ void __launch_bounds__(256, LAYOUT == VOX_BRICK ? MC_MIN_BLOCKS_BRICK
             return false;
           };
           int k0 = 0;
+          if (LAYOUT == VOX_BRICK && MC_BRICK_NOSPLIT) {
+            for (; k0 < n && !hit; k0 += kLook) {
+              uint32_t wd[kLook];
+              gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
+              consume(wd, k0, true);
+            }
+          }
           for (; k0 + kLook <= n && !hit; k0 += kLook) {
             uint32_t wd[kLook];
             gather_group<LAYOUT>(V, vr, k0, hh, ta, hv, wd);
